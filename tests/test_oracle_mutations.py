@@ -1,0 +1,83 @@
+"""Planted mistakes in a copy of the oracle must each fail a pin (CPU only).
+
+Each case compiles ``oracle/esd_oracle.c`` with one plausible slip (a dropped term, a
+wrong sign, a transposed operand, a wrong loop order), swaps it in for the real oracle
+library, and checks that a pin of ``test_oracle_pins`` fails on it. The committed oracle
+is never modified.
+"""
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+SRC = open(os.path.join(os.path.dirname(oracle.__file__), "esd_oracle.c")).read()
+
+MUTANTS = {
+    # the paper's literal sign of beta in Algorithm DPCG
+    "beta_sign": ("p[k] = z[k] + beta * p[k];", "p[k] = z[k] - beta * p[k];",
+                  lambda: pins.test_cg_terminates_in_k_steps(4)),
+    # Eq. x1 correction dropped: x = x_i instead of P x_i + W E^-1 W^T b
+    "no_final_correction": ("    tall_vec_acc(n, s->m, s->W, u, 1.0, x);\n  }\ndone:",
+                            "  }\ndone:", pins.test_deflation_with_exact_eigenvectors),
+    # P applied instead of P^T (W and AW swapped inside the projection)
+    "P_instead_of_PT": ("  tall_t_vec(s->n, s->m, s->W, v, f);\n  chol_solve(s->m, s->LE, f, u);\n"
+                        "  tall_vec_acc(s->n, s->m, s->AW, u, -1.0, v);",
+                        "  tall_t_vec(s->n, s->m, s->AW, v, f);\n  chol_solve(s->m, s->LE, f, u);\n"
+                        "  tall_vec_acc(s->n, s->m, s->W, u, -1.0, v);",
+                        pins.test_deflation_with_exact_eigenvectors),
+    # IC(0): the sum over the common pattern of rows i and k dropped
+    "ic0_no_update": ("          s -= Lva[pi] * Lva[pk];", "          (void)0;",
+                      pins.test_ic0_is_exact_cholesky_on_full_pattern),
+    # IC(0): the pivot uses a_ii instead of a_ii - sum l_ik^2
+    "ic0_pivot": ("    for (int a = Lrp[i]; a < row_end; ++a) d -= Lva[a] * Lva[a];", "",
+                  pins.test_ic0_is_exact_cholesky_on_full_pattern),
+    # forward substitution in the reverse colour order
+    "fwd_colour_order": ("  for (int c = 0; c < ncol; ++c)\n    for (int i = cp[c]; i < cp[c + 1]; ++i) {",
+                         "  for (int c = ncol - 1; c >= 0; --c)\n    for (int i = cp[c]; i < cp[c + 1]; ++i) {",
+                         lambda: pins.test_ic_apply_is_M_inverse("c1")),
+    # backward substitution with L instead of L^T (row i's own entries)
+    "bwd_transposed": ("      for (int a = Lrp[j]; a < e; ++a) t[Lci[a]] -= Lva[a] * z[j];",
+                       "      for (int a = Lrp[j]; a < e; ++a) t[j] -= Lva[a] * z[Lci[a]];",
+                       lambda: pins.test_ic_apply_is_M_inverse("small3d")),
+    # subspace correction subtracted instead of added (Eq. mc)
+    "sc_sign": ("    tall_vec_acc(n, s->m, s->W, u, 1.0, z);", "    tall_vec_acc(n, s->m, s->W, u, -1.0, z);",
+                pins.test_subspace_correction_shifts_small_eigenvalue_by_one),
+    # residual update with the wrong sign
+    "residual_sign": ("        r[k] -= alpha * q[k];", "        r[k] += alpha * q[k];",
+                      pins.test_iccg_solves_the_system),
+}
+
+
+@pytest.fixture
+def mutant(tmp_path, monkeypatch):
+    def make(name):
+        old, new, _ = MUTANTS[name]
+        assert SRC.count(old) == 1, f"mutation anchor for {name} not unique"
+        src = tmp_path / f"{name}.c"
+        src.write_text(SRC.replace(old, new))
+        so = tmp_path / f"{name}.so"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", str(so), str(src), "-lm"])
+        monkeypatch.setattr(oracle, "_lib", oracle.load(str(so)))
+    return make
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_is_caught(name, mutant):
+    mutant(name)
+    with pytest.raises((AssertionError, ArithmeticError, ValueError, np.linalg.LinAlgError)):
+        MUTANTS[name][2]()
+
+
+def test_lanczos_dropped_term_is_caught(monkeypatch):
+    """The Lanczos matrix without the beta/alpha diagonal term misses the closed form."""
+    def wrong(alpha, beta):
+        a = np.asarray(alpha, dtype=np.float64)
+        b = np.asarray(beta, dtype=np.float64)[: len(a) - 1]
+        return 1.0 / a, np.sqrt(b) / a[:-1]
+    monkeypatch.setattr(oracle, "lanczos_tridiagonal", wrong)
+    with pytest.raises(AssertionError):
+        pins.test_lanczos_1d_laplacian_closed_form()

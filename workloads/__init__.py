@@ -1,0 +1,305 @@
+"""Seeded synthetic workloads: the linear systems the solver and the oracle both consume.
+
+This module defines *problems*, not the method: it assembles the SPD matrix of a
+backward-Euler diffusion step (the sequence ``A x_t = b_t`` of Eq. ak2/ak3 with a fixed
+``A``), its multicolour ordering, the source vectors and the seeded coefficient fields.
+It holds none of the solver arithmetic (no CG, no preconditioner, no deflation); both the
+CUDA path and the CPU oracle import it, and neither imports the other.
+
+Readings of the workload descriptions (the paper is silent on them, it used SuiteSparse
+matrices, Section 5.1):
+
+* domain ``[0,1]^d`` with ``N`` cells per side, ``h = 1/N``, cell-centred finite volumes;
+* ``A = I/dt + K`` with ``(K x)_i = sum_faces T_f (x_i - x_j)``, ``T_f`` the harmonic mean
+  ``2 k_a k_b / (k_a + k_b) / h^2``; a Dirichlet (zero) boundary face adds ``2 k_i / h^2``;
+* the right-hand side of system ``t`` is ``b_t = x_{t-1} / dt + s`` with ``x_0 = 0``;
+* inclusions are placed by rejection sampling (no overlap, fully inside the domain);
+* the ordering is colour-major: all rows of colour 0, then colour 1, ...; inside a colour
+  the natural lexicographic order is kept. Colours are red-black ``(i+j) % 2`` in 2D and
+  ``(i%2) + 2(j%2) + 4(k%2)`` in 3D.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Optional
+
+import numpy as np
+import scipy.sparse as sp
+
+__all__ = [
+    "Problem", "fv_diffusion", "square_inclusions", "sphere_inclusions",
+    "gaussian_source", "smooth_gaussian_field", "config_c1", "config_c2", "config_c4",
+    "small_3d", "random_spd_dense", "laplacian_1d", "laplacian_2d", "csr_of_dense",
+    "random_rhs", "SEED_BASE",
+]
+
+SEED_BASE = 20220316
+
+
+@dataclasses.dataclass
+class Problem:
+    """One SPD matrix in colour-major CSR order plus what a sequence needs.
+
+    rowptr/colind are int32, val float64; columns are sorted inside each row and
+    ``colour_ptr[c]:colour_ptr[c+1]`` is the row range of colour ``c``. ``perm[new] = old``
+    maps the colour-major index to the natural lexicographic cell index.
+    """
+    n: int
+    rowptr: np.ndarray
+    colind: np.ndarray
+    val: np.ndarray
+    colour_ptr: np.ndarray
+    perm: np.ndarray
+    dt: float = 0.0
+    source: Optional[np.ndarray] = None
+    shape: tuple = ()
+    h: float = 1.0
+    coef: Optional[np.ndarray] = None  # per-cell coefficient, natural order
+    name: str = ""
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowptr[-1])
+
+    @property
+    def ncolours(self) -> int:
+        return len(self.colour_ptr) - 1
+
+    def scipy(self) -> sp.csr_matrix:
+        return sp.csr_matrix((self.val, self.colind, self.rowptr), shape=(self.n, self.n))
+
+
+def _colour_of(shape):
+    idx = np.indices(shape)  # axis order (x, y[, z]); x fastest in the natural numbering
+    if len(shape) == 2:
+        return ((idx[0] + idx[1]) % 2).astype(np.int64)
+    col = np.zeros(shape, dtype=np.int64)
+    for ax in range(len(shape)):
+        col += (idx[ax] % 2) << ax
+    return col
+
+
+def _natural_index(shape):
+    # x fastest: index = x + Nx*(y + Ny*z)
+    idx = np.indices(shape)
+    lin = np.zeros(shape, dtype=np.int64)
+    stride = 1
+    for ax in range(len(shape)):
+        lin += idx[ax] * stride
+        stride *= shape[ax]
+    return lin
+
+
+def fv_diffusion(coef: np.ndarray, h: float, dt: float, name: str = "") -> Problem:
+    """Assemble ``A = I/dt + K`` for cell-centred FV diffusion with harmonic-mean faces.
+
+    ``coef`` has shape ``(Nx, Ny[, Nz])`` (axis 0 = x, fastest in the natural numbering).
+    ``dt = inf`` gives the steady operator ``K``.
+    """
+    shape = coef.shape
+    d = len(shape)
+    n = int(np.prod(shape))
+    nat = _natural_index(shape)
+    rows, cols, vals = [], [], []
+    diag = np.full(shape, 0.0 if not np.isfinite(dt) else 1.0 / dt)
+    inv_h2 = 1.0 / (h * h)
+    for ax in range(d):
+        ka = np.take(coef, np.arange(shape[ax] - 1), axis=ax)
+        kb = np.take(coef, np.arange(1, shape[ax]), axis=ax)
+        t = 2.0 * ka * kb / (ka + kb) * inv_h2
+        ia = np.take(nat, np.arange(shape[ax] - 1), axis=ax).ravel()
+        ib = np.take(nat, np.arange(1, shape[ax]), axis=ax).ravel()
+        tf = t.ravel()
+        rows += [ia, ib]
+        cols += [ib, ia]
+        vals += [-tf, -tf]
+        # interior faces feed both diagonals
+        pad_lo = [(0, 0)] * d
+        pad_lo[ax] = (0, 1)
+        pad_hi = [(0, 0)] * d
+        pad_hi[ax] = (1, 0)
+        diag += np.pad(t, pad_lo) + np.pad(t, pad_hi)
+        # Dirichlet faces at both ends of this axis
+        lo = [slice(None)] * d
+        lo[ax] = slice(0, 1)
+        hi = [slice(None)] * d
+        hi[ax] = slice(shape[ax] - 1, shape[ax])
+        diag[tuple(lo)] += 2.0 * coef[tuple(lo)] * inv_h2
+        diag[tuple(hi)] += 2.0 * coef[tuple(hi)] * inv_h2
+    rows.append(nat.ravel())
+    cols.append(nat.ravel())
+    vals.append(diag.ravel())
+    r = np.concatenate(rows)
+    c = np.concatenate(cols)
+    v = np.concatenate(vals)
+    # colour-major permutation (stable: natural order inside a colour)
+    colour = _colour_of(shape).ravel()[np.argsort(nat.ravel())]  # colour by natural index
+    perm = np.argsort(colour, kind="stable").astype(np.int64)  # perm[new] = old
+    inv = np.empty(n, dtype=np.int64)
+    inv[perm] = np.arange(n)
+    ncol = int(colour.max()) + 1
+    counts = np.bincount(colour, minlength=ncol)
+    colour_ptr = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    A = sp.csr_matrix((v, (inv[r], inv[c])), shape=(n, n))
+    A.sum_duplicates()
+    A.sort_indices()
+    return Problem(n=n, rowptr=A.indptr.astype(np.int32), colind=A.indices.astype(np.int32),
+                   val=A.data.astype(np.float64), colour_ptr=colour_ptr, perm=perm, dt=dt,
+                   shape=tuple(shape), h=h, coef=coef, name=name)
+
+
+def square_inclusions(N: int, count: int, size: int, value: float, rng) -> np.ndarray:
+    """Background 1 with ``count`` non-overlapping ``size x size`` squares of ``value``."""
+    coef = np.ones((N, N))
+    placed = []
+    while len(placed) < count:
+        x0, y0 = rng.integers(0, N - size + 1, size=2)
+        if any(abs(x0 - a) < size and abs(y0 - b) < size for a, b in placed):
+            continue
+        placed.append((x0, y0))
+        coef[x0:x0 + size, y0:y0 + size] = value
+    return coef
+
+
+def sphere_inclusions(N: int, count: int, rmin: float, rmax: float, value: float, rng) -> np.ndarray:
+    """Background 1 with ``count`` non-overlapping balls (radius in cells, fully inside)."""
+    coef = np.ones((N, N, N))
+    centres = []
+    ctr = np.indices((N, N, N)).astype(np.float64) + 0.5
+    tries = 0
+    while len(centres) < count:
+        tries += 1
+        if tries > 100000:
+            raise RuntimeError("could not place inclusions")
+        r = rng.uniform(rmin, rmax)
+        c = rng.uniform(r, N - r, size=3)
+        if any(np.linalg.norm(c - c2) < r + r2 for c2, r2 in centres):
+            continue
+        centres.append((c, r))
+        lo = np.maximum(np.floor(c - r).astype(int), 0)
+        hi = np.minimum(np.ceil(c + r).astype(int) + 1, N)
+        sub = tuple(slice(lo[a], hi[a]) for a in range(3))
+        d2 = sum((ctr[a][sub] - c[a]) ** 2 for a in range(3))
+        coef[sub][d2 <= r * r] = value
+    return coef
+
+
+def gaussian_source(shape, sigma: float = 0.1, centre: float = 0.5) -> np.ndarray:
+    """Fixed spatial Gaussian bump on cell centres, natural order."""
+    N = shape[0]
+    x = (np.indices(shape) + 0.5) / N
+    d2 = sum((x[a] - centre) ** 2 for a in range(len(shape)))
+    return np.exp(-d2 / (2.0 * sigma * sigma))
+
+
+def smooth_gaussian_field(shape, corr_cells: float, rng) -> np.ndarray:
+    """White noise convolved with a Gaussian of std ``corr_cells`` cells, unit variance."""
+    from scipy.ndimage import gaussian_filter
+    w = rng.standard_normal(shape)
+    f = gaussian_filter(w, sigma=corr_cells, mode="wrap")
+    f -= f.mean()
+    return f / f.std()
+
+
+def _finish(p: Problem, src_nat: np.ndarray) -> Problem:
+    p.source = np.ascontiguousarray(src_nat.ravel(order="F")[p.perm])
+    return p
+
+
+def config_c1(seed: int = SEED_BASE + 0) -> Problem:
+    """2D 64x64 5-point FV, 4 seeded 6x6 inclusions of 1e3, red-black, dt = 1e-2,
+    source uniform in [0,1) drawn once per sequence."""
+    rng = np.random.default_rng(seed)
+    N = 64
+    coef = square_inclusions(N, 4, 6, 1e3, rng)
+    p = fv_diffusion(coef, 1.0 / N, 1e-2, name="fv5_64x64_redblack")
+    return _finish(p, rng.uniform(0.0, 1.0, size=(N, N)))
+
+
+def config_c2(N: int = 128, seed: int = SEED_BASE + 1, count: int = 16, rmin: float = 4.0,
+              rmax: float = 8.0, value: float = 1e5, dt: float = 1e-3) -> Problem:
+    """3D 7-point FV on N^3, ``count`` balls of radius rmin..rmax cells with coefficient
+    ``value``, 8-colour ordering, dt = 1e-3, Gaussian source (centre 0.5, sigma 0.1)."""
+    rng = np.random.default_rng(seed)
+    coef = sphere_inclusions(N, count, rmin, rmax, value, rng)
+    p = fv_diffusion(coef, 1.0 / N, dt, name=f"fv7_{N}cube_8colour")
+    return _finish(p, gaussian_source((N, N, N)))
+
+
+def config_c4(N: int = 128, seed: int = SEED_BASE + 3, corr: float = 4.0):
+    """3D 7-point steady FV with k = exp(theta), theta ~ N(0,1) smoothed over ``corr``
+    cells (renormalised to unit variance). Returns (problem, theta, x_target)."""
+    rng = np.random.default_rng(seed)
+    theta = smooth_gaussian_field((N, N, N), corr, rng)
+    p = fv_diffusion(np.exp(theta), 1.0 / N, np.inf, name=f"fv7_{N}cube_lognormal")
+    p = _finish(p, gaussian_source((N, N, N)))
+    x_target = rng.standard_normal(p.n) * 1e-3
+    return p, theta, x_target
+
+
+def small_3d(N: int, seed: int, count: int = 2, rmin: float = 1.5, rmax: float = 2.5,
+             value: float = 1e3, dt: float = 1e-3) -> Problem:
+    """A reduced C2-like problem for parity tests (odd N gives ragged colour sizes)."""
+    rng = np.random.default_rng(seed)
+    if N < 7:  # too small for non-overlapping balls: one small inclusion at most
+        count, rmin, rmax = min(count, 1), min(rmin, N / 4), min(rmax, N / 4)
+    coef = sphere_inclusions(N, count, rmin, rmax, value, rng) if count else np.ones((N, N, N))
+    p = fv_diffusion(coef, 1.0 / N, dt, name=f"fv7_{N}cube")
+    return _finish(p, gaussian_source((N, N, N)))
+
+
+def random_rhs(n: int, seed: int) -> np.ndarray:
+    return np.random.default_rng(seed).uniform(0.0, 1.0, size=n)
+
+
+# ---- tiny dense-defined test matrices (for the pins) ----
+
+def random_spd_dense(eigs: np.ndarray, seed: int) -> np.ndarray:
+    """``Q diag(eigs) Q^T`` with a seeded random orthogonal Q."""
+    rng = np.random.default_rng(seed)
+    q, _ = np.linalg.qr(rng.standard_normal((len(eigs), len(eigs))))
+    a = (q * eigs) @ q.T
+    return 0.5 * (a + a.T)
+
+
+def csr_of_dense(a: np.ndarray, ncolours: int = 1) -> Problem:
+    """Dense SPD matrix as a CSR problem with a single colour (or the given count of
+    equal contiguous colour blocks, valid only when the blocks have no internal edges)."""
+    n = a.shape[0]
+    m = sp.csr_matrix(a)
+    m.sort_indices()
+    cp = np.linspace(0, n, ncolours + 1).astype(np.int32)
+    return Problem(n=n, rowptr=m.indptr.astype(np.int32), colind=m.indices.astype(np.int32),
+                   val=m.data.astype(np.float64), colour_ptr=cp, perm=np.arange(n))
+
+
+def laplacian_1d(n: int) -> Problem:
+    """tridiag(-1, 2, -1) of order n, red-black ordered (odd points first)."""
+    a = sp.diags([-np.ones(n - 1), 2 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1]).tocsr()
+    colour = np.arange(n) % 2
+    perm = np.argsort(colour, kind="stable")
+    inv = np.empty(n, dtype=np.int64)
+    inv[perm] = np.arange(n)
+    ap = a[perm][:, perm].tocsr()
+    ap.sort_indices()
+    counts = np.bincount(colour, minlength=2)
+    cp = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    return Problem(n=n, rowptr=ap.indptr.astype(np.int32), colind=ap.indices.astype(np.int32),
+                   val=ap.data.astype(np.float64), colour_ptr=cp, perm=perm, name="lap1d")
+
+
+def laplacian_2d(N: int) -> Problem:
+    """5-point Laplacian 4,-1 on an N x N grid (unit spacing), red-black ordered."""
+    coef = np.ones((N, N))
+    p = fv_diffusion(coef, 1.0, np.inf, name="lap2d")
+    # fv_diffusion with h=1, k=1 gives interior faces 1 and boundary faces 2: rescale to the
+    # textbook stencil by rebuilding the diagonal as 4 on every row.
+    A = p.scipy().tolil()
+    for i in range(p.n):
+        A[i, i] = 4.0
+    A = A.tocsr()
+    A.sort_indices()
+    p.rowptr = A.indptr.astype(np.int32)
+    p.colind = A.indices.astype(np.int32)
+    p.val = A.data.astype(np.float64)
+    return p
