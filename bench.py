@@ -1,0 +1,496 @@
+#!/usr/bin/env python3
+"""Benchmark of the hot path on the 128^3 heterogeneous-diffusion sequence.
+
+Workload (the configuration the headline metric is quoted on): 3D 7-point finite-volume
+diffusion on a 128^3 grid (n = 2,097,152, nnz = 14,581,760), background coefficient 1 and 16
+seeded balls of radius 4-8 cells with coefficient 1e5, Dirichlet boundaries, 8-colour
+ordering, FP64 CSR; a backward-Euler sequence of 20 systems b_t = x_{t-1}/dt + Gaussian
+source (dt = 1e-3, x_0 = 0); IC(0)-PCG to relative residual 1e-8; W from m = 16 error
+vectors sampled (method A) during system 1; systems 2..20 deflated.
+
+One step = one whole sequence: IC(0) factorisation, system 1 with sampling, the W build
+(CholeskyQR2, AW, E, E^-1), the Lanczos condition estimate, systems 2..20 in the selected
+mode, with the backward-Euler right-hand sides formed on the device. value = systems solved
+per second (all ranks). Inputs are resident in HBM when the timed region starts; the
+working set (~1.3 GB) is larger than L2, so no flush is needed between steps.
+
+--impl reference times the CPU oracle (the FP64 C restatement of the method) on the same
+workload, a bounded number of iterations per step, extrapolated to solves per second.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "time-to-1e-8 per system & solves/sec; HBM GB/s vs plain FP64 PCG on GB300"
+UNIT = "solves/s"
+L2_BYTES = 129e6
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="esdcg", choices=["esdcg", "reference"])
+    ap.add_argument("--mode", default="deflation", choices=["plain", "deflation", "sc"])
+    ap.add_argument("--grid", type=int, default=128)
+    ap.add_argument("--systems", type=int, default=20)
+    ap.add_argument("--m", type=int, default=16)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e, comparison modes and CPU baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(args):
+    import workloads as wl
+    if args.grid == 128:
+        p = wl.config_c2()
+    else:
+        r = args.grid / 128.0
+        p = wl.config_c2(N=args.grid, rmin=4 * r, rmax=8 * r)
+    return p
+
+
+def workload_name(args, p):
+    return (f"fv7_{args.grid}cube_16balls_1e5_dt1e-3: {args.systems}-system backward-Euler sequence, "
+            f"IC(0)-PCG to {args.tol:g}, W from m={args.m} sampled error vectors, {args.mode}")
+
+
+def level_stats(p):
+    """Rows and strict-lower / strict-upper entries per colour (for per-kernel bytes)."""
+    A = p.scipy().tocoo()
+    col_of = np.searchsorted(p.colour_ptr, np.arange(p.n), side="right") - 1
+    rows = np.diff(p.colour_ptr)
+    low = np.bincount(col_of[A.row[A.col < A.row]], minlength=p.ncolours)
+    up = np.bincount(col_of[A.row[A.col > A.row]], minlength=p.ncolours)
+    return rows, low, up
+
+
+# ---------------------------------------------------------------- clocks
+
+class Clocks:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.lines = []
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(gpu_index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def gpu_arm(args):
+    import torch
+    import paper_2203_08498_gb300 as esd
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    p = workload(args)
+    n, nnz = p.n, p.nnz
+    mode = {"plain": esd.PLAIN, "deflation": esd.DEFLATION, "sc": esd.SUBSPACE_CORRECTION}[args.mode]
+    A = esd.Matrix.from_problem(p)
+    A.factor_ic0()
+    S = esd.Solver(A, maxit_cap=20000, sample_cap=max(args.m, 2))
+    src = torch.from_numpy(p.source).to(dev)
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    b = torch.empty_like(x)
+    inv_dt = 1.0 / p.dt
+    info = A.info()
+
+    def sequence(md, S=S, A=A, x=x, b=b, src=src):
+        A.factor_ic0()
+        x.zero_()
+        its, stats = [], {}
+        for t in range(args.systems):
+            S.backward_euler_rhs(x, src, inv_dt, b)
+            if t == 0:
+                S.set_mode(esd.PLAIN)
+                st, it, rr = S.solve(b, x, args.tol, 20000, args.m if md != esd.PLAIN else 0)
+                stats["cond"] = S.estimate_cond()
+                if md != esd.PLAIN:
+                    stats["m_kept"] = S.sample_and_build_W()
+                    S.set_mode(md)
+            else:
+                st, it, rr = S.solve(b, x, args.tol, 20000, 0)
+            if st != esd.OK:
+                raise RuntimeError(f"solve {t} returned {st}")
+            its.append(it)
+        return its, stats
+
+    def timed(md, steps, warm):
+        for _ in range(warm):
+            sequence(md)
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record()
+        out = []
+        for _ in range(steps):
+            out.append(sequence(md))
+        e1.record()
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        ms = e0.elapsed_time(e1)
+        if ws > 1:
+            tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            ms = float(tt.item())
+        return ms, wall, out
+
+    clocks = Clocks(local)
+    ms, wall, runs = timed(mode, args.steps, args.warmup)
+    clk = clocks.stop()
+    its, stats = runs[-1]
+    systems_total = args.systems * args.steps * ws
+    value = systems_total / (ms / 1e3)
+    ms_step = ms / args.steps
+
+    # kernel launches inside the timed region (counted from the launch sequences)
+    nf = info["fwd_levels"] - 1
+    nb = max(info["bwd_levels"] - 1, 1)
+    body = 2 + nf + nb
+    defl = 1 if mode == esd.DEFLATION else 0
+    per_solve_fixed = (1 + 2 * defl + 1 + nf + nb) + (1 + 2 * defl + 1)
+    launches = 0
+    for it_list, st_ in runs:
+        launches += info["fwd_levels"] + 1  # factorisation
+        launches += args.systems  # right-hand sides
+        launches += sum(per_solve_fixed + body * k for k in it_list)
+        launches += 1  # condition estimate
+        if mode != esd.PLAIN:
+            launches += 1 + 8 + args.m  # errors, Gram/small/tall kernels, A W columns
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args, p), "grid": args.grid, "n": n, "nnz": nnz,
+                   "systems": args.systems, "m": args.m, "mode": args.mode, "tol": args.tol,
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (matrix, factor and vectors ~1.3 GB > 129 MB)"},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "iterations": its,
+        "time_to_tol_ms_per_system": ms_step / args.systems,
+        "cond_estimate_system1": {"lmin": stats["cond"][0], "lmax": stats["cond"][1],
+                                  "kappa": stats["cond"][2]},
+    }
+    if rank != 0 or args.no_extras:
+        return result, None
+
+    # roofline of the dominant kernel: live per-kernel CUDA-event times of the same kernels
+    S.set_mode(mode)
+    xs = x.clone()
+    prof = S.profile_iterations(b, xs, reps=20)
+    peaks = read_peaks()
+    result["roofline"], result["kernel_times_ms"] = roofline(prof, p, args, mode, esd, peaks)
+
+    # per-iteration time in each mode through the graphs (from the timed sequences)
+    modes = {}
+    iter_time = {}
+    for name, md in (("plain", esd.PLAIN), ("deflation", esd.DEFLATION), ("sc", esd.SUBSPACE_CORRECTION)):
+        if md == mode:
+            its_m, ms_m = its, ms_step
+        else:
+            ms_m, _, r = timed(md, 1, 1)
+            its_m = r[-1][0]
+        modes[name] = {"iterations": its_m, "ms_per_sequence": ms_m, "solves_per_s": args.systems / (ms_m / 1e3),
+                       "mean_iters_2_to_T": float(np.mean(its_m[1:]))}
+    result["modes"] = modes
+    # time per iteration and model bandwidth per mode (single solves of system 2)
+    result["iteration"] = iteration_roofline(S, esd, p, args, x, b, src, peaks)
+
+    # end to end through the C ABI with host buffers
+    result["e2e"] = e2e(esd, p, args, torch)
+    return result, modes
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return {"hbm_gbs": d["hbm_gbs"], "src": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (CUDA cores and tensor), nominal
+
+
+def kernel_model(name, p, args, mode, esd, lv):
+    """Algorithmic bytes and FP64 FMAs of one launch (per-kernel model)."""
+    n, nnz = p.n, p.nnz
+    m = args.m if mode != esd.PLAIN else 0
+    rows, low, up = lv
+    if name == "spmv_pq":
+        mb = m if mode == esd.DEFLATION else 0
+        return 12 * nnz + 20 * n + 8 * mb * n, nnz + n + mb * n
+    if name == "update":
+        dm = m if mode == esd.DEFLATION else 0
+        sm = m if mode == esd.SUBSPACE_CORRECTION else 0
+        n0 = int(rows[0])  # forward level 0 (colour 0): y = r / l_ii
+        return 48 * n + 8 * (dm + sm) * n + 16 * n0, 3 * n + (dm + sm) * n + 2 * n0
+    return None, None
+
+
+def roofline(prof, p, args, mode, esd, peaks):
+    lv = level_stats(p)
+    times = {nm: t for nm, t in prof}
+    cand = [(t, nm) for nm, t in prof if nm in ("spmv_pq", "update")]
+    t_ms, name = max(cand)
+    by, fmas = kernel_model(name, p, args, mode, esd, lv)
+    sec = t_ms / 1e3
+    gbs = by / sec / 1e9
+    tflops = 2 * fmas / sec / 1e12
+    f_hbm = gbs / peaks["hbm_gbs"]
+    f_alu = tflops / FP64_NOMINAL_TFLOPS
+    traffic = read_traffic(name)
+    if f_alu > f_hbm:
+        roof = {"bound": "alu", "achieved": tflops, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": f_alu, "traffic": traffic, "kernel": name,
+                "peak_src": "nominal FP64 (152 SMs x 2 FP64 FMA/clk x 2.07 GHz)",
+                "hbm": {"achieved": gbs, "peak": peaks["hbm_gbs"], "frac": f_hbm, "peak_src": peaks["src"]}}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": f_hbm,
+                "traffic": traffic, "kernel": name, "peak_src": peaks["src"],
+                "alu": {"achieved": tflops, "peak": FP64_NOMINAL_TFLOPS, "frac": f_alu}}
+    roof["bytes_per_launch"] = by
+    roof["ms_per_launch"] = t_ms
+    return roof, times
+
+
+def read_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary of this kernel, if any."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_128cube_traffic.txt")
+    try:
+        for ln in open(path):
+            if ln.startswith("traffic_bytes_per_launch:"):
+                return float(ln.split(":")[1])
+    except OSError:
+        pass
+    return None
+
+
+def iteration_roofline(S, esd, p, args, x, b, src, peaks):
+    """Time per iteration of each mode (graph launches of system 2) against the paper's
+    per-iteration byte model (Eq. ticcg / tsciccg generalised)."""
+    import torch
+    out = {}
+    n, nnz = p.n, p.nnz
+    m = args.m
+    for name, md in (("plain", esd.PLAIN), ("deflation", esd.DEFLATION), ("sc", esd.SUBSPACE_CORRECTION)):
+        S.set_mode(md)
+        x0 = torch.zeros_like(x)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, it, rr = S.solve(b, x0, args.tol, 20000, 0)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        model = 24 * nnz + 100 * n + (16 * m * n + 16 * n if md != esd.PLAIN else 0)
+        tpi = sec / max(it, 1)
+        out[name] = {"iters": it, "ms_per_iter": tpi * 1e3, "model_bytes_per_iter": model,
+                     "model_gbs": model / tpi / 1e9, "frac_of_hbm_peak": model / tpi / 1e9 / peaks["hbm_gbs"]}
+    return out
+
+
+def e2e(esd, p, args, torch):
+    """The same sequence through the C ABI with host buffers: CSR upload, factorisation and
+    per system the right-hand side and the solve with host b and x (copies inside)."""
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+    rp, ci, va = pin(p.rowptr.astype(np.int32)), pin(p.colind.astype(np.int32)), pin(p.val)
+    src_h = pin(p.source)
+    x_h = torch.zeros(p.n, dtype=torch.float64).pin_memory()
+    b_h = torch.zeros(p.n, dtype=torch.float64).pin_memory()
+    mode = {"plain": esd.PLAIN, "deflation": esd.DEFLATION, "sc": esd.SUBSPACE_CORRECTION}[args.mode]
+
+    def step():
+        A = esd.Matrix(rp, ci, va, p.colour_ptr)
+        A.factor_ic0()
+        S = esd.Solver(A, maxit_cap=20000, sample_cap=max(args.m, 2))
+        x_h.zero_()
+        for t in range(args.systems):
+            S.backward_euler_rhs(x_h, src_h, 1.0 / p.dt, b_h)
+            if t == 0:
+                S.solve(b_h, x_h, args.tol, 20000, args.m if mode != esd.PLAIN else 0)
+                S.estimate_cond()
+                if mode != esd.PLAIN:
+                    S.sample_and_build_W()
+                    S.set_mode(mode)
+            else:
+                S.solve(b_h, x_h, args.tol, 20000, 0)
+        S.close()
+        A.close()
+
+    step()  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    k = max(1, args.steps)
+    for _ in range(k):
+        step()
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    n = p.n
+    h2d = 4 * (n + 1) + 12 * p.nnz + args.systems * 32 * n
+    d2h = args.systems * 16 * n
+    return {"value": args.systems * k / sec, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": sec * 1e3 / k}
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def oracle_rates(p, args, iters_plain=20, iters_acc=20):
+    """Seconds per oracle iteration (plain ICCG and the accelerated mode), single thread."""
+    import oracle
+    ic = oracle.IC0(p)
+    rng = np.random.default_rng(0)
+    out = {}
+    t0 = time.perf_counter()
+    oracle.System(p, ic).solve(p.source, tol=1e-300, maxit=iters_plain, history=False)
+    out["plain"] = (time.perf_counter() - t0) / iters_plain
+    if args.mode != "plain":
+        Q, _ = np.linalg.qr(rng.standard_normal((p.n, args.m)))
+        aux = oracle.Aux.from_basis(p, Q)
+        md = oracle.DEFLATION if args.mode == "deflation" else oracle.SUBSPACE_CORRECTION
+        t0 = time.perf_counter()
+        oracle.System(p, ic, md, aux).solve(p.source, tol=1e-300, maxit=iters_acc, history=False)
+        out["acc"] = (time.perf_counter() - t0) / iters_acc
+    else:
+        out["acc"] = out["plain"]
+    return out
+
+
+def extrapolate(rates, its):
+    sec = rates["plain"] * its[0] + rates["acc"] * sum(its[1:])
+    return len(its) / sec
+
+
+def cpu_baseline(p, args, its):
+    r = oracle_rates(p, args)
+    return {"value": extrapolate(r, its), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"20 plain and 20 {args.mode} ICCG iterations of the {args.grid}^3 system (m={args.m}, "
+                       f"orthonormal W) on one host core, extrapolated with this run's iteration counts "
+                       f"per system"), "s_per_iter": r}
+
+
+def oracle_counts(args):
+    """The oracle's iteration counts for this sequence (written by oracle/sequence_counts.py)."""
+    path = os.path.join(ROOT, "oracle", "data", f"fv7_{args.grid}cube_{args.mode}_counts.json")
+    try:
+        its = json.load(open(path))["iterations"]
+        return its[: args.systems]
+    except (OSError, KeyError, ValueError):
+        raise SystemExit(f"missing {path}: run python -m oracle.sequence_counts {args.mode}")
+
+
+def reference_arm(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    p = workload(args)
+    its = oracle_counts(args)
+    vals = []
+    for s in range(args.warmup + args.steps):
+        r = oracle_rates(p, args, iters_plain=5, iters_acc=5)
+        if s >= args.warmup:
+            vals.append(extrapolate(r, its))
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args, p), "grid": args.grid, "n": p.n, "nnz": p.nnz},
+            "cpu_baseline": {"value": v, "unit": UNIT, "kind": "oracle", "cores": 1,
+                             "sample": "5 plain and 5 accelerated oracle iterations per step, extrapolated "
+                                       "with the oracle's own iteration counts of this sequence "
+                                       "(oracle/data, written by oracle/sequence_counts.py)"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    result, modes = gpu_arm(args)
+    if rank == 0:
+        if not args.no_extras and ws == 1:
+            result["cpu_baseline"] = cpu_baseline(workload(args), args, result["iterations"])
+        print(json.dumps(result), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * esdcg — deflated / subspace-corrected ICCG for a sequence of SPD systems with one matrix,
+ * the auxiliary matrix W built from error vectors sampled during an earlier solve
+ * (arXiv 2203.08498). One GPU (sm_103a); every numerical step runs in this library's CUDA
+ * kernels.
+ *
+ * Conventions for every entry point:
+ *   - Return value: ESD_OK (0) or a negative ESD_ERR_* code; esd_last_error() then returns
+ *     a message (library-owned, valid until the next failing call on the same thread).
+ *   - Vectors are arrays of n doubles. "Device or host" arguments may point to device memory
+ *     or to host memory (pinned or pageable); host data is staged through library buffers.
+ *   - The library never frees, keeps or aliases caller memory beyond the call: inputs are
+ *     copied in, outputs copied out.
+ *   - All work is ordered on the stream given to esd_create_matrix. Calls that return values
+ *     to the host (iteration counts, norms, estimates) synchronise that stream.
+ *   - Handles are not thread-safe; use one handle per host thread or serialise calls.
+ */
+#ifndef ESDCG_H
+#define ESDCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum esd_status {
+  ESD_OK = 0,
+  ESD_ERR_INVALID = -1,   /* bad argument, malformed CSR or colouring */
+  ESD_ERR_NOT_SPD = -2,   /* IC(0) pivot <= 0 after every allowed diagonal shift */
+  ESD_ERR_BREAKDOWN = -3, /* (p, Ap) <= 0 or (r, z) <= 0 or NaN during a solve */
+  ESD_ERR_MAXIT = -4,     /* tolerance not reached in maxit iterations (x holds the last iterate) */
+  ESD_ERR_STATE = -5,     /* call not valid in the current state (e.g. deflation without W) */
+  ESD_ERR_RANK = -6,      /* the sampled error vectors have rank 0 */
+  ESD_ERR_CHOL_E = -7,    /* E = W^T A W is not numerically positive definite */
+  ESD_ERR_CUDA = -8,      /* a CUDA runtime call failed */
+  ESD_ERR_NOMEM = -9,     /* device allocation failed */
+  ESD_ERR_INTERNAL = -10  /* an internal guard stopped the device loop (a library defect) */
+};
+
+enum esd_mode {
+  ESD_PLAIN = 0,                  /* PCG with M^{-1} */
+  ESD_DEFLATION = 1,              /* deflated PCG, Algorithm "Deflated PCG" */
+  ESD_SUBSPACE_CORRECTION = 2     /* PCG with M_sc^{-1} = M^{-1} + W E^{-1} W^T, Eq. mc */
+};
+
+enum esd_precond { ESD_PRECOND_NONE = 0, ESD_PRECOND_IC0 = 1 };
+
+enum esd_precision {
+  ESD_FP64 = 0,        /* every step in FP64 */
+  ESD_FP32_REFINE = 1  /* FP32 inner PCG inside an FP64 iterative refinement */
+};
+
+typedef struct esd_matrix esd_matrix;
+typedef struct esd_solver esd_solver;
+
+/* Message of the last failing call on this thread ("" if none). Library-owned. */
+const char* esd_last_error(void);
+
+/* ---------------------------------------------------------------- matrix */
+
+/*
+ * Create the library's copy of an SPD matrix A (the fixed matrix of the sequence
+ * A x_k = b_k, Eq. ak2/ak3) from CSR.
+ *   n           rows (= columns), 1 <= n < 2^31 - 64
+ *   nnz         entries, rowptr[n]
+ *   rowptr      n+1 int32, rowptr[0] = 0, non-decreasing         (device or host)
+ *   colind      nnz int32 in [0, n), strictly increasing per row  (device or host)
+ *   val         nnz doubles                                       (device or host)
+ *   colour_ptr  ncolours+1 int32: rows colour_ptr[c] .. colour_ptr[c+1]-1 form colour c;
+ *               colour_ptr[0] = 0, colour_ptr[ncolours] = n (host)
+ *   ncolours    1 .. 64; no two rows of one colour may be coupled (multicolour ordering)
+ *   flags       reserved, pass 0
+ *   stream      cudaStream_t on which all later work is ordered (0 = legacy default stream)
+ * Requirements checked on the device: sorted in-range columns, a diagonal entry in every
+ * row, a structurally symmetric pattern, no coupling inside a colour. Violations return
+ * ESD_ERR_INVALID. Only tril(A) enters the IC(0) factor; SpMV uses A as given.
+ * Layout: the rows are re-sliced into a sliced-ELL copy (32-row slices inside each colour).
+ */
+int esd_create_matrix(int32_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colind,
+                      const double* val, const int32_t* colour_ptr, int32_t ncolours,
+                      uint32_t flags, void* stream, esd_matrix** out);
+int esd_matrix_destroy(esd_matrix* A);
+
+/* Dimensions and the colour levels found at creation: a level is a set of colours with
+ * no coupling among them, so one launch serves it (forward / backward). */
+int esd_matrix_info(const esd_matrix* A, int32_t* n, int64_t* nnz, int32_t* ncolours,
+                    int32_t* fwd_levels, int32_t* bwd_levels);
+
+/*
+ * IC(0) factor M = L L^T on the pattern of tril(A), computed colour by colour in the
+ * given order (the paper's incomplete Cholesky preconditioner, Sections 4.4 and 5.3; the
+ * fill level is zero). If a pivot is not positive the factor is recomputed for
+ * A + s diag(A) with s = 1e-3, 2e-3, 4e-3, ... (at most max_tries attempts in total,
+ * the first with s = 0). shift_used (host, may be NULL) receives s.
+ * Errors: ESD_ERR_NOT_SPD when every attempt fails.
+ */
+int esd_factor_ic0(esd_matrix* A, int32_t max_tries, double* shift_used);
+
+/* y = A x (device or host arrays of n doubles). */
+int esd_matrix_spmv(esd_matrix* A, const double* x, double* y);
+
+/* z = (L L^T)^{-1} r by colour-ordered forward and backward substitution
+ * (requires esd_factor_ic0). */
+int esd_matrix_apply_ic(esd_matrix* A, const double* r, double* z);
+
+/*
+ * Gradient of a scalar loss with respect to the stored entries of A when x solves
+ * A x = b and lambda solves the adjoint system A lambda = dL/dx: dL/da_ij = -lambda_i x_j,
+ * written in the order of the CSR given at creation (grad has nnz entries).
+ */
+int esd_pattern_grad(esd_matrix* A, const double* lambda, const double* x, double* grad);
+
+/* ---------------------------------------------------------------- solver */
+
+typedef struct {
+  int32_t precond;     /* esd_precond */
+  int32_t maxit_cap;   /* capacity of the alpha/beta history; a solve's maxit <= this */
+  int32_t sample_cap;  /* slots reserved for sampled iterates (the paper's m), 0..64 */
+  int32_t lmax;        /* sampling method A parameter l_max (m^l_max > N_max); 0 = smallest valid */
+  double rank_tol;     /* rank rule for the sampled errors, e.g. 1e-12 */
+  int32_t precision;   /* esd_precision */
+  double inner_tol;    /* relative tolerance of each FP32 inner solve (ESD_FP32_REFINE) */
+  int32_t max_outer;   /* refinement steps allowed (ESD_FP32_REFINE) */
+} esd_params;
+
+/* Default parameters: IC(0), maxit_cap 20000, sample_cap 32, lmax 0, rank_tol 1e-12, FP64. */
+void esd_params_default(esd_params* p);
+
+int esd_solver_create(esd_matrix* A, const esd_params* params, esd_solver** out);
+int esd_solver_destroy(esd_solver* S);
+
+/* Select the iteration: ESD_PLAIN, ESD_DEFLATION or ESD_SUBSPACE_CORRECTION. The last two
+ * need W (esd_sample_and_build_W or esd_set_W), otherwise ESD_ERR_STATE. */
+int esd_set_mode(esd_solver* S, int32_t mode);
+
+/*
+ * Solve A x = b to ||b - A x||_2 <= tol ||b||_2 (the paper's criterion, Section 5.1).
+ *   b         n doubles (device or host), unchanged
+ *   x         n doubles (device or host): initial guess on entry, solution on exit
+ *   tol       relative tolerance > 0
+ *   maxit     1 .. maxit_cap
+ *   sample_m  0, or 1 .. sample_cap: store iterates by sampling method A (Appendix A) for
+ *             a following esd_sample_and_build_W. Not allowed in deflation mode (its
+ *             iterates live in the deflated space): ESD_ERR_STATE.
+ *   iters     (host, may be NULL) alpha steps taken
+ *   relres    (host, may be NULL) final ||r_i||/||b|| of the recursive residual; in
+ *             deflation mode r_i = P^T (b - A x_i), which equals the true residual of the
+ *             returned x (Eq. x1/x2)
+ * Plain / SC mode: PCG as in Algorithm "PCG with condition number estimation" without the
+ * power method. Deflation: Algorithm "Deflated PCG" with beta = +rho_{i+1}/rho_i and the
+ * final x = P x_i + W E^{-1} W^T b. b = 0 gives x = 0 and 0 iterations.
+ * The whole solve is one CUDA graph launch (a device-side while loop); the call
+ * synchronises once at the end to return iters and relres.
+ * Errors: ESD_ERR_MAXIT (x = last iterate), ESD_ERR_BREAKDOWN, ESD_ERR_STATE.
+ */
+int esd_solve(esd_solver* S, const double* b, double* x, double tol, int32_t maxit,
+              int32_t sample_m, int32_t* iters, double* relres);
+
+/* ||b - A x|| / ||b|| of the last solve, recomputed in FP64 from the returned x. */
+int esd_true_relres(esd_solver* S, double* relres);
+
+/*
+ * Build W from the iterates stored by the last sampling solve (Section 4.2):
+ * e_s = x - x~_s (Eq. ek) for every filled slot, columns normalised, the rank
+ * mbar = #{eig(G) > rank_tol max eig(G)} of G = Ehat^T Ehat, an orthonormal basis Q of
+ * their span (Eq. ekd; CholeskyQR2 when full rank, else SVQB then one CholeskyQR pass),
+ * then with theta = +inf W = Q, or with finite theta the Ritz vectors Q t_i of
+ * Q^T A Q t = lambda t with lambda < theta (Eq. Rayleigh-Ritz, bk). Also AW = A W,
+ * E = W^T A W and E^{-1}, all in FP64 on the device.
+ *   m_kept  (host, may be NULL) number of columns of W
+ * Errors: ESD_ERR_STATE (no sampled solve), ESD_ERR_RANK, ESD_ERR_CHOL_E.
+ */
+int esd_sample_and_build_W(esd_solver* S, double theta, int32_t* m_kept);
+
+/* Use a caller-supplied W (n x m column-major doubles, device or host, 1 <= m <= 64,
+ * columns linearly independent); AW, E and E^{-1} are built as above. */
+int esd_set_W(esd_solver* S, const double* W, int32_t m);
+
+/* Copy W, AW (n x m column-major) and E (m x m row-major) out; any pointer may be NULL. */
+int esd_get_W(esd_solver* S, double* W, double* AW, double* E, int32_t* m);
+
+/* Ritz values of the current W (eigenvalues of E when W is orthonormal), ascending. */
+int esd_ritz_values(esd_solver* S, double* out, int32_t cap, int32_t* count);
+
+/*
+ * Condition number estimate from the last solve: the extreme eigenvalues of the Lanczos
+ * tridiagonal matrix assembled from its CG coefficients, T_jj = 1/alpha_j +
+ * beta_{j-1}/alpha_{j-1}, T_{j,j+1} = sqrt(beta_j)/alpha_j. They estimate the spectrum
+ * of the (preconditioned, deflated) operator of that solve; kappa = lmax/lmin.
+ * ritz_min (may be NULL) receives the smallest Ritz value of W (the paper's lambda_min
+ * estimate, Section 5.4) or NaN when there is no W.
+ */
+int esd_estimate_cond(esd_solver* S, double* lmin, double* lmax, double* kappa, double* ritz_min);
+
+/* alpha_j and beta_j of the last solve (host arrays of cap entries). */
+int esd_get_history(esd_solver* S, double* alpha, double* beta, int32_t cap, int32_t* count);
+
+/* Sampled slots of the last sampling solve: iteration held by each slot (0 = empty). */
+int esd_get_samples(esd_solver* S, double* samples, int32_t* slot_iter, int32_t cap, int32_t* m);
+
+/*
+ * Measurement: run reps iterations of the current mode on A x = b starting from x, the same
+ * kernels the solve graph holds but launched one by one with CUDA events between them, and
+ * return each kernel's average device time in launch order (the tolerance is taken as 0, so
+ * the iterations do not stop early).
+ *   ms     host array of cap doubles: average milliseconds per kernel launch
+ *   names  host buffer of 32*cap chars (may be NULL): NUL-terminated kernel names, 32 bytes each
+ *   count  (host) kernels in one iteration
+ * x (device or host) receives the iterate after reps steps.
+ */
+int esd_profile_iterations(esd_solver* S, const double* b, double* x, int32_t reps, double* ms,
+                           char* names, int32_t cap, int32_t* count);
+
+/* b = x_prev * inv_dt + s, the backward-Euler right-hand side of the next system. */
+int esd_backward_euler_rhs(esd_solver* S, const double* x_prev, const double* s, double inv_dt,
+                           double* b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ESDCG_H */

@@ -32,11 +32,12 @@ PLAIN, DEFLATION, SUBSPACE_CORRECTION = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
-    """Compile the C oracle into ``oracle/_build`` (plain -O2, no vectorisation flags)."""
+    """Compile the C oracle into ``oracle/_build``: -O2 with floating-point contraction off,
+    so every product is rounded before it is added and x86 and Arm builds agree bit for bit."""
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 

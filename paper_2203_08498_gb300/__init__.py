@@ -1,0 +1,408 @@
+"""Python binding of ``libesdcg`` (include/esdcg.h): deflated / subspace-corrected ICCG for a
+sequence of SPD systems with one matrix, the auxiliary matrix built from sampled error
+vectors (arXiv 2203.08498).
+
+Argument marshalling only: every numerical step runs in the library's CUDA kernels. Arrays
+may be CUDA torch tensors, CPU torch tensors or NumPy arrays (host data is staged by the
+library). There is no fallback: without the compiled library every call raises.
+
+The functions keep the C names (``esd_create_matrix``, ``esd_solve`` ...); ``Matrix`` and
+``Solver`` own the handles.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+from . import _build
+
+__all__ = [
+    "lib", "EsdError", "Matrix", "Solver", "PLAIN", "DEFLATION", "SUBSPACE_CORRECTION",
+    "PRECOND_NONE", "PRECOND_IC0", "FP64", "FP32_REFINE", "EsdParams", "HEADER_SYMBOLS",
+    "esd_create_matrix", "esd_matrix_destroy", "esd_matrix_info", "esd_factor_ic0", "esd_matrix_spmv",
+    "esd_matrix_apply_ic", "esd_pattern_grad", "esd_params_default", "esd_solver_create",
+    "esd_solver_destroy", "esd_set_mode", "esd_solve", "esd_true_relres", "esd_sample_and_build_W",
+    "esd_set_W", "esd_get_W", "esd_ritz_values", "esd_estimate_cond", "esd_get_history",
+    "esd_get_samples", "esd_backward_euler_rhs", "esd_profile_iterations", "esd_last_error",
+]
+
+OK, ERR_INVALID, ERR_NOT_SPD, ERR_BREAKDOWN, ERR_MAXIT, ERR_STATE, ERR_RANK, ERR_CHOL_E, ERR_CUDA, ERR_NOMEM = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8, -9)
+ERR_INTERNAL = -10
+PLAIN, DEFLATION, SUBSPACE_CORRECTION = 0, 1, 2
+PRECOND_NONE, PRECOND_IC0 = 0, 1
+FP64, FP32_REFINE = 0, 1
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "esdcg.h")
+
+
+def _header_symbols():
+    import re
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(esd_[a-zA-Z0-9_]+)\s*\(", txt)))
+
+
+HEADER_SYMBOLS = _header_symbols()
+
+
+class EsdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class EsdParams(C.Structure):
+    _fields_ = [("precond", C.c_int32), ("maxit_cap", C.c_int32), ("sample_cap", C.c_int32),
+                ("lmax", C.c_int32), ("rank_tol", C.c_double), ("precision", C.c_int32),
+                ("inner_tol", C.c_double), ("max_outer", C.c_int32)]
+
+
+_lib = None
+
+
+def lib(build_if_missing: bool = True):
+    """Load the compiled library (building it in-tree when it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise EsdError(ERR_INVALID, f"libesdcg not built ({path})")
+        L = C.CDLL(path)
+        vp, i32, i64, f64, u32 = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_uint32
+        P = C.POINTER
+        sig = {
+            "esd_last_error": (C.c_char_p, []),
+            "esd_create_matrix": (i32, [i32, i64, vp, vp, vp, vp, i32, u32, vp, P(vp)]),
+            "esd_matrix_destroy": (i32, [vp]),
+            "esd_matrix_info": (i32, [vp, P(i32), P(i64), P(i32), P(i32), P(i32)]),
+            "esd_factor_ic0": (i32, [vp, i32, P(f64)]),
+            "esd_matrix_spmv": (i32, [vp, vp, vp]),
+            "esd_matrix_apply_ic": (i32, [vp, vp, vp]),
+            "esd_pattern_grad": (i32, [vp, vp, vp, vp]),
+            "esd_params_default": (None, [P(EsdParams)]),
+            "esd_solver_create": (i32, [vp, P(EsdParams), P(vp)]),
+            "esd_solver_destroy": (i32, [vp]),
+            "esd_set_mode": (i32, [vp, i32]),
+            "esd_solve": (i32, [vp, vp, vp, f64, i32, i32, P(i32), P(f64)]),
+            "esd_true_relres": (i32, [vp, P(f64)]),
+            "esd_sample_and_build_W": (i32, [vp, f64, P(i32)]),
+            "esd_set_W": (i32, [vp, vp, i32]),
+            "esd_get_W": (i32, [vp, vp, vp, vp, P(i32)]),
+            "esd_ritz_values": (i32, [vp, vp, i32, P(i32)]),
+            "esd_estimate_cond": (i32, [vp, P(f64), P(f64), P(f64), P(f64)]),
+            "esd_get_history": (i32, [vp, vp, vp, i32, P(i32)]),
+            "esd_get_samples": (i32, [vp, vp, vp, i32, P(i32)]),
+            "esd_backward_euler_rhs": (i32, [vp, vp, vp, f64, vp]),
+            "esd_profile_iterations": (i32, [vp, vp, vp, i32, vp, vp, i32, P(i32)]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def esd_last_error() -> str:
+    return lib().esd_last_error().decode()
+
+
+def _check(code, allow=()):
+    if code != OK and code not in allow:
+        raise EsdError(code, esd_last_error())
+    return code
+
+
+def _ptr(a):
+    """Device or host address of a torch tensor / NumPy array (contiguous)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        if not (a.flags["C_CONTIGUOUS"] or a.flags["F_CONTIGUOUS"]):
+            raise ValueError("array must be contiguous")
+        return C.c_void_p(a.ctypes.data)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _dtype_ok(a, kind):
+    if a is None:
+        return
+    if hasattr(a, "dtype") and hasattr(a, "data_ptr"):
+        import torch
+        want = {"f64": torch.float64, "i32": torch.int32}[kind]
+        if a.dtype != want:
+            raise TypeError(f"expected {want}, got {a.dtype}")
+    elif isinstance(a, np.ndarray):
+        want = {"f64": np.float64, "i32": np.int32}[kind]
+        if a.dtype != want:
+            raise TypeError(f"expected {want}, got {a.dtype}")
+
+
+def current_stream():
+    """torch's current CUDA stream handle when torch has CUDA, else 0 (legacy stream)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return 0
+
+
+# ---------------------------------------------------------------- C-named functions
+
+def esd_create_matrix(n, nnz, rowptr, colind, val, colour_ptr, ncolours, flags=0, stream=None):
+    _dtype_ok(rowptr, "i32"), _dtype_ok(colind, "i32"), _dtype_ok(val, "f64")
+    cp = np.ascontiguousarray(colour_ptr, dtype=np.int32)
+    out = C.c_void_p()
+    st = current_stream() if stream is None else stream
+    _check(lib().esd_create_matrix(n, nnz, _ptr(rowptr), _ptr(colind), _ptr(val), _ptr(cp), ncolours, flags,
+                                   C.c_void_p(st), C.byref(out)))
+    return out
+
+
+def esd_matrix_destroy(h):
+    return _check(lib().esd_matrix_destroy(h))
+
+
+def esd_matrix_info(h):
+    n, ncol, fl, bl = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+    nnz = C.c_int64()
+    _check(lib().esd_matrix_info(h, C.byref(n), C.byref(nnz), C.byref(ncol), C.byref(fl), C.byref(bl)))
+    return dict(n=n.value, nnz=nnz.value, ncolours=ncol.value, fwd_levels=fl.value, bwd_levels=bl.value)
+
+
+def esd_factor_ic0(h, max_tries=30):
+    s = C.c_double()
+    _check(lib().esd_factor_ic0(h, max_tries, C.byref(s)))
+    return s.value
+
+
+def esd_matrix_spmv(h, x, y):
+    _check(lib().esd_matrix_spmv(h, _ptr(x), _ptr(y)))
+
+
+def esd_matrix_apply_ic(h, r, z):
+    _check(lib().esd_matrix_apply_ic(h, _ptr(r), _ptr(z)))
+
+
+def esd_pattern_grad(h, lam, x, grad):
+    _check(lib().esd_pattern_grad(h, _ptr(lam), _ptr(x), _ptr(grad)))
+
+
+def esd_params_default():
+    p = EsdParams()
+    lib().esd_params_default(C.byref(p))
+    return p
+
+
+def esd_solver_create(mh, params=None):
+    out = C.c_void_p()
+    p = params if params is not None else esd_params_default()
+    _check(lib().esd_solver_create(mh, C.byref(p), C.byref(out)))
+    return out
+
+
+def esd_solver_destroy(h):
+    return _check(lib().esd_solver_destroy(h))
+
+
+def esd_set_mode(h, mode):
+    _check(lib().esd_set_mode(h, mode))
+
+
+def esd_solve(h, b, x, tol, maxit, sample_m=0):
+    """Returns (status, iters, relres); status OK or ERR_MAXIT (other errors raise)."""
+    it, rr = C.c_int32(), C.c_double()
+    st = _check(lib().esd_solve(h, _ptr(b), _ptr(x), tol, maxit, sample_m, C.byref(it), C.byref(rr)),
+                allow=(ERR_MAXIT,))
+    return st, it.value, rr.value
+
+
+def esd_true_relres(h):
+    v = C.c_double()
+    _check(lib().esd_true_relres(h, C.byref(v)))
+    return v.value
+
+
+def esd_sample_and_build_W(h, theta=math.inf):
+    m = C.c_int32()
+    _check(lib().esd_sample_and_build_W(h, theta, C.byref(m)))
+    return m.value
+
+
+def esd_set_W(h, W, m):
+    _check(lib().esd_set_W(h, _ptr(W), m))
+
+
+def esd_get_W(h, n, m_cap=64):
+    """Returns (W, AW, E) as NumPy arrays (n x m column-major, n x m, m x m)."""
+    m = C.c_int32()
+    W = np.zeros((n, m_cap), order="F")
+    AW = np.zeros((n, m_cap), order="F")
+    E = np.zeros(m_cap * m_cap)
+    _check(lib().esd_get_W(h, _ptr(W), _ptr(AW), _ptr(E), C.byref(m)))
+    k = m.value
+    return W[:, :k].copy(order="F"), AW[:, :k].copy(order="F"), E[: k * k].reshape(k, k)
+
+
+def esd_ritz_values(h, cap=64):
+    out = np.zeros(cap)
+    cnt = C.c_int32()
+    _check(lib().esd_ritz_values(h, _ptr(out), cap, C.byref(cnt)))
+    return out[: min(cnt.value, cap)]
+
+
+def esd_estimate_cond(h):
+    lo, hi, k, r = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+    _check(lib().esd_estimate_cond(h, C.byref(lo), C.byref(hi), C.byref(k), C.byref(r)))
+    return lo.value, hi.value, k.value, r.value
+
+
+def esd_get_history(h, cap):
+    a, b = np.zeros(cap), np.zeros(cap)
+    cnt = C.c_int32()
+    _check(lib().esd_get_history(h, _ptr(a), _ptr(b), cap, C.byref(cnt)))
+    k = min(cnt.value, cap)
+    return a[:k], b[: max(k - 1, 0)]
+
+
+def esd_get_samples(h, n, cap):
+    s = np.zeros((n, cap), order="F")
+    it = np.zeros(cap, dtype=np.int32)
+    m = C.c_int32()
+    _check(lib().esd_get_samples(h, _ptr(s), _ptr(it), cap, C.byref(m)))
+    k = min(m.value, cap)
+    return s[:, :k], it[:k]
+
+
+def esd_backward_euler_rhs(h, x_prev, s, inv_dt, b):
+    _check(lib().esd_backward_euler_rhs(h, _ptr(x_prev), _ptr(s), inv_dt, _ptr(b)))
+
+
+def esd_profile_iterations(h, b, x, reps, cap=64):
+    """Returns [(kernel name, average ms per launch)] for one iteration of the current mode."""
+    ms = np.zeros(cap)
+    names = C.create_string_buffer(32 * cap)
+    cnt = C.c_int32()
+    _check(lib().esd_profile_iterations(h, _ptr(b), _ptr(x), reps, _ptr(ms), names, cap, C.byref(cnt)))
+    k = min(cnt.value, cap)
+    raw = names.raw
+    return [(raw[32 * j: 32 * j + 32].split(b"\0")[0].decode(), float(ms[j])) for j in range(k)]
+
+
+# ---------------------------------------------------------------- handle owners
+
+class Matrix:
+    """Library copy of an SPD CSR matrix in colour-major order (``esd_create_matrix``)."""
+
+    def __init__(self, rowptr, colind, val, colour_ptr, stream=None):
+        n = len(rowptr) - 1
+        nnz = len(colind)
+        self.n, self.nnz = n, nnz
+        self._h = esd_create_matrix(n, nnz, rowptr, colind, val, colour_ptr, len(colour_ptr) - 1, 0, stream)
+        self.shift = None
+
+    @classmethod
+    def from_problem(cls, prob, stream=None):
+        return cls(np.ascontiguousarray(prob.rowptr, np.int32), np.ascontiguousarray(prob.colind, np.int32),
+                   np.ascontiguousarray(prob.val, np.float64), prob.colour_ptr, stream)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        return esd_matrix_info(self._h)
+
+    def factor_ic0(self, max_tries=30):
+        self.shift = esd_factor_ic0(self._h, max_tries)
+        return self.shift
+
+    def spmv(self, x, y):
+        esd_matrix_spmv(self._h, x, y)
+
+    def apply_ic(self, r, z):
+        esd_matrix_apply_ic(self._h, r, z)
+
+    def pattern_grad(self, lam, x, grad):
+        esd_pattern_grad(self._h, lam, x, grad)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            esd_matrix_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Solver:
+    """``esd_solver`` bound to a Matrix; keeps the matrix alive."""
+
+    def __init__(self, matrix: Matrix, precond=PRECOND_IC0, maxit_cap=20000, sample_cap=32, lmax=0,
+                 rank_tol=1e-12, precision=FP64, inner_tol=1e-4, max_outer=30):
+        p = esd_params_default()
+        p.precond, p.maxit_cap, p.sample_cap, p.lmax = precond, maxit_cap, sample_cap, lmax
+        p.rank_tol, p.precision, p.inner_tol, p.max_outer = rank_tol, precision, inner_tol, max_outer
+        self.matrix = matrix
+        self.maxit_cap = maxit_cap
+        self._h = esd_solver_create(matrix.handle, p)
+
+    def set_mode(self, mode):
+        esd_set_mode(self._h, mode)
+
+    def solve(self, b, x, tol=1e-8, maxit=None, sample_m=0):
+        return esd_solve(self._h, b, x, tol, maxit or self.maxit_cap, sample_m)
+
+    def true_relres(self):
+        return esd_true_relres(self._h)
+
+    def sample_and_build_W(self, theta=math.inf):
+        return esd_sample_and_build_W(self._h, theta)
+
+    def set_W(self, W):
+        W = np.asfortranarray(W, dtype=np.float64) if isinstance(W, np.ndarray) else W
+        esd_set_W(self._h, W, W.shape[1])
+
+    def get_W(self):
+        return esd_get_W(self._h, self.matrix.n)
+
+    def ritz_values(self):
+        return esd_ritz_values(self._h)
+
+    def estimate_cond(self):
+        return esd_estimate_cond(self._h)
+
+    def history(self):
+        return esd_get_history(self._h, self.maxit_cap)
+
+    def samples(self, cap=64):
+        return esd_get_samples(self._h, self.matrix.n, cap)
+
+    def profile_iterations(self, b, x, reps=20):
+        return esd_profile_iterations(self._h, b, x, reps)
+
+    def backward_euler_rhs(self, x_prev, s, inv_dt, b):
+        esd_backward_euler_rhs(self._h, x_prev, s, inv_dt, b)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            esd_solver_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,219 @@
+// Shared definitions of the CUDA path: sliced-ELL matrix views, the device-resident solver
+// state, the grid-wide deterministic reductions and the error plumbing.
+//
+// Matrix layout (HBM): rows are grouped by colour; each colour is cut into slices of 32
+// consecutive rows. A slice stores its entries column-major (entry k of lane l at
+// off + 32*k + l), so the 32 threads of a warp, one per row, read consecutive words.
+// Rows shorter than the slice width are padded with (column n, value 0); every vector the
+// kernels gather from carries a sentinel element n that is always 0, so padding adds an
+// exact zero. The same slicing serves A, the strict lower factor L and its transpose U.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+
+#include "../../include/esdcg.h"
+
+namespace esd {
+
+constexpr int kSlice = 32;      // rows per slice (one warp, one row per lane)
+constexpr int kBlock = 512;     // threads per block of the streaming kernels
+constexpr int kMaxM = 64;       // maximum number of columns of W
+constexpr int kMaxRanges = 16;  // slice ranges one launch may cover
+constexpr int kMaxColours = 64;
+
+// A set of slice ranges processed by one launch (the colours of one level).
+struct SliceSet {
+  int nr;                       // number of ranges
+  int begin[kMaxRanges];        // first slice of each range
+  int cum[kMaxRanges + 1];      // prefix sums of range lengths (cum[0] = 0)
+  unsigned fwd0;                // bit r: rows of range r have no earlier neighbour
+  unsigned bwd0;                // bit r: rows of range r have no later neighbour
+  __host__ __device__ int total() const { return cum[nr]; }
+  // slice index of the g-th slice of the set, and the range it belongs to
+  __device__ __forceinline__ int slice(int g, int* range) const {
+    int r = 0;
+#pragma unroll 1
+    while (r + 1 < nr && g >= cum[r + 1]) ++r;
+    *range = r;
+    return begin[r] + (g - cum[r]);
+  }
+};
+
+// meta per slice: x = entry offset, y = width, z = first row, w = rows in the slice
+template <typename T>
+struct SellView {
+  const int4* meta;
+  const int* col;
+  const T* val;
+};
+
+// Device-resident scalar state of one solve. All Krylov scalars stay here; the host reads
+// it back once per solve.
+struct State {
+  double bb;        // ||b||^2
+  double rr;        // ||r||^2 of the recursive (deflated) residual
+  double tol2bb;    // tol^2 ||b||^2
+  double rho;       // (r, z) of the current iteration
+  double rho_prev;  // (r, z) of the previous iteration
+  double rho_acc;   // running sum of y_i^2 over the forward levels
+  double pq;        // (p, A p)
+  double pap;       // (p, P^T A p) in deflation, = pq otherwise
+  double alpha, beta;
+  double fu;        // f^T E^{-1} f of the subspace correction
+  double true_rr;   // ||b - A x||^2 recomputed after the solve
+  double scal0, scal1;  // scratch for auxiliary kernels
+  int iter;         // alpha steps taken
+  int maxit;
+  int conv;         // 1 once the loop must stop (converged, maxit or breakdown)
+  int status;       // ESD_OK / ESD_ERR_MAXIT / ESD_ERR_BREAKDOWN
+  int zero_rhs;
+  int samp_m;       // sampling method A: number of slots in use (0 = off)
+  int lmax;
+  int h;            // the interval h of sampling method A
+  int pend_slot;    // slot to receive x at the next update (-1 = none)
+  int pend_iter;
+  int guard;        // loop bodies started; a second, reduction-free bound on the loop
+  int pad1;
+  int slot_iter[kMaxM];
+  double y[kMaxM];  // deflation: E^{-1} (AW)^T p
+  double u[kMaxM];  // subspace correction / projection: E^{-1} f
+  unsigned int ticket[8];
+};
+
+enum Ticket { kTkSpmv = 0, kTkUpdate = 1, kTkSweep = 2, kTkAux = 3, kTkAux2 = 4 };
+
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define ESD_CUDA(call)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      throw ::esd::Error(ESD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define ESD_CHECK(cond, code, msg)                   \
+  do {                                               \
+    if (!(cond)) throw ::esd::Error((code), (msg));  \
+  } while (0)
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+// Sum of P values held by each lane of a warp: a butterfly that halves the values a lane
+// holds at each exchange, so 32 values cost 31 additions per lane instead of 5 x 32.
+// On return v[0] of lane l holds the warp total of value index warp_sum_index<P>(l).
+template <int P, typename T>
+__device__ __forceinline__ void warp_sum_multi(T (&v)[P]) {
+  static_assert((P & (P - 1)) == 0 && P <= 32, "P must be a power of two <= 32");
+  const int lane = lane_id();
+  int h = P / 2;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    if (h >= 1) {
+      const bool upper = (lane & o) != 0;
+#pragma unroll
+      for (int k = 0; k < (P / 2 > 0 ? P / 2 : 1); ++k) {
+        if (k < h) {
+          T send = upper ? v[k] : v[k + h];
+          T keep = upper ? v[k + h] : v[k];
+          v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+      }
+      h >>= 1;
+    } else {
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+    }
+  }
+}
+
+template <int P>
+__device__ __forceinline__ int warp_sum_index(int lane) {
+  int idx = 0, h = P / 2;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    if (h >= 1) {
+      if (lane & o) idx += h;
+      h >>= 1;
+    }
+  }
+  return idx;
+}
+
+__host__ __device__ constexpr int pow2_ceil(int x) { return x <= 1 ? 1 : (x <= 2 ? 2 : (x <= 4 ? 4 : (x <= 8 ? 8 : (x <= 16 ? 16 : 32)))); }
+
+// Block-wide sum of R values per thread (R <= 64). The block totals end up in red[0..R).
+// red must hold 32 * (blockDim/32) ... at least (blockDim/32) * R entries of shared memory.
+template <int R, typename T>
+__device__ __forceinline__ void block_sum_multi(const T (&in)[R], T* red) {
+  constexpr int C = R > 32 ? 32 : R;  // chunk size
+  constexpr int P = pow2_ceil(C);
+  const int lane = lane_id(), warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+#pragma unroll
+  for (int c0 = 0; c0 < R; c0 += C) {
+    T v[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) v[k] = (k < C && c0 + k < R) ? in[c0 + k] : T(0);
+    warp_sum_multi<P>(v);
+    const int idx = warp_sum_index<P>(lane);
+    // lanes holding the same index carry the same total; the lowest such lane writes it
+    if (idx < C && c0 + idx < R && (lane & ((32 / P) - 1)) == 0) red[warp * R + c0 + idx] = v[0];
+  }
+  __syncthreads();
+  if (threadIdx.x < R) {
+    T s = 0;
+    for (int w = 0; w < nwarp; ++w) s += red[w * R + threadIdx.x];
+    red[(nwarp)*R + threadIdx.x] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < R) red[threadIdx.x] = red[nwarp * R + threadIdx.x];
+  __syncthreads();
+}
+
+// Grid-wide deterministic sum: every block stores its R block totals into
+// partials[j * gridDim.x + blockIdx.x]; the last block to arrive adds them up in a fixed
+// order and returns true with the totals in red[0..R). No block ever waits for another.
+template <int R, typename T>
+__device__ __forceinline__ bool grid_sum_multi(const T (&in)[R], T* red, T* partials,
+                                               unsigned int* ticket) {
+  __shared__ bool s_last;
+  block_sum_multi<R>(in, red);
+  const int G = gridDim.x;
+  if (threadIdx.x < R) partials[threadIdx.x * G + blockIdx.x] = red[threadIdx.x];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = atomicAdd(ticket, 1u);
+    s_last = (t == (unsigned)G - 1);
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  T acc[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    T s = 0;
+    for (int b = threadIdx.x; b < G; b += blockDim.x) s += __ldcg(&partials[j * G + b]);
+    acc[j] = s;
+  }
+  block_sum_multi<R>(acc, red);
+  if (threadIdx.x == 0) *ticket = 0u;  // ready for the next launch
+  return true;
+}
+
+// u = Einv f for the small dense (padded) M x M inverse stored row-major; one warp.
+__device__ __forceinline__ void small_matvec_warp(const double* Einv, int M, const double* f,
+                                                  double* u) {
+  for (int i = lane_id(); i < M; i += 32) {
+    double s = 0.0;
+    for (int k = 0; k < M; ++k) s += Einv[i * M + k] * f[k];
+    u[i] = s;
+  }
+}
+
+}  // namespace esd

@@ -1,0 +1,116 @@
+// Host-side objects behind the C handles: device buffers, the sliced matrix with its IC(0)
+// factor, and the solver with its captured CUDA graphs.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "esd_common.cuh"
+
+namespace esd {
+
+// Owning device allocation.
+class DevBuf {
+ public:
+  DevBuf() = default;
+  explicit DevBuf(size_t bytes) { alloc(bytes); }
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p_(o.p_), bytes_(o.bytes_) { o.p_ = nullptr; o.bytes_ = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) { release(); p_ = o.p_; bytes_ = o.bytes_; o.p_ = nullptr; o.bytes_ = 0; }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void alloc(size_t bytes);
+  void release();
+  template <typename T> T* as() const { return static_cast<T*>(p_); }
+  void* get() const { return p_; }
+  size_t bytes() const { return bytes_; }
+
+ private:
+  void* p_ = nullptr;
+  size_t bytes_ = 0;
+};
+
+// Sliced-ELL storage of one matrix part (A, strict L or strict U), double and optional float.
+struct Sell {
+  DevBuf meta;   // int4 per slice
+  DevBuf col;    // int per entry (padded)
+  DevBuf val;    // double per entry
+  DevBuf val32;  // float per entry (FP32 inner solves)
+  long long entries = 0;
+  template <typename T> SellView<T> view() const;
+};
+
+template <> inline SellView<double> Sell::view<double>() const {
+  return {meta.as<int4>(), col.as<int>(), val.as<double>()};
+}
+template <> inline SellView<float> Sell::view<float>() const {
+  return {meta.as<int4>(), col.as<int>(), val32.as<float>()};
+}
+
+// Scratch for the grid-wide reductions of one stream of launches.
+struct Scratch {
+  DevBuf partials;  // double, kMaxGridBlocks * kMaxRed
+  DevBuf state;     // State
+};
+
+constexpr int kMaxRed = 2 * kMaxM + 8;
+
+int grid_blocks(int work_slices);  // blocks for a launch over this many slices
+int max_grid_blocks();
+
+}  // namespace esd
+
+struct esd_matrix {
+  int n = 0;
+  long long nnz = 0;
+  int ncol = 0;
+  std::vector<int> cp;             // colour pointer (host)
+  cudaStream_t stream = nullptr;
+  int nslices = 0;
+  std::vector<int> colour_first_slice;
+  std::vector<int> fwd_level, bwd_level;
+  // launch groups
+  esd::SliceSet all;                       // every slice
+  std::vector<esd::SliceSet> fwd_sets;     // forward levels >= 1 (level 0 is fused in the update)
+  std::vector<esd::SliceSet> bwd_sets;     // backward levels >= 1 (+ elementwise ranges)
+  std::vector<esd::SliceSet> fwd_all_sets; // all forward levels incl. level 0 (factor, apply)
+  std::vector<esd::SliceSet> bwd_all_sets; // all backward levels incl. level 0 (apply)
+  std::vector<esd::SliceSet> bwd0_sets;    // colours without later neighbours
+  esd::Sell A, L, U;
+  esd::DevBuf slice_flags;   // uint8 per slice: bit0 fwd level 0, bit1 bwd level 0
+  esd::DevBuf rowpos;        // int per row: slice*32 + lane
+  esd::DevBuf diagpos;       // int per row: CSR index of the diagonal entry
+  esd::DevBuf umap;          // int per U entry: index of the L entry holding l_ji (-1 = pad)
+  esd::DevBuf csr_rowptr, csr_colind, csr_val;  // the CSR as given (int, int, double)
+  esd::DevBuf ldiag;         // double: l_ii
+  esd::DevBuf inv_d;         // double: 1/l_ii (n+1, sentinel 0)
+  esd::DevBuf inv_d32;       // float copy
+  esd::DevBuf err;           // int[4] validation / factor error words
+  esd::DevBuf tmp;           // 3 x (n+1) doubles for host-pointer staging
+  esd::Scratch scratch;
+  bool factored = false;
+  int factor_version = 0;
+  int fp32_version = -1;
+  double shift = 0.0;
+  size_t vec_stride() const { return ((size_t)n + 1 + 31) / 32 * 32; }  // doubles per vector
+  void ensure_fp32();
+};
+
+namespace esd {
+// Helpers shared by the translation units.
+void copy_in(const void* src, void* dst_dev, size_t bytes, cudaStream_t s);   // device or host src
+void copy_out(const void* src_dev, void* dst, size_t bytes, cudaStream_t s);  // device or host dst
+bool is_device_ptr(const void* p);
+void set_last_error(const std::string& msg);
+
+// Kernel launchers used across files (defined in esd_iter.cu).
+void launch_spmv(const esd_matrix* A, const double* x, double* y, cudaStream_t s);
+void launch_apply_ic(const esd_matrix* A, const double* r, double* z, double* work, cudaStream_t s);
+}  // namespace esd

@@ -1,0 +1,69 @@
+// Launchers of the Krylov-iteration kernels. One IterCtx describes the buffers of one
+// precision (double for the FP64 solver, float for the FP32 inner solver of the refinement).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "esd_internal.h"
+
+namespace esd {
+
+template <typename T>
+struct IterCtx {
+  const esd_matrix* A = nullptr;
+  SellView<T> Av{}, Lv{}, Uv{};
+  const T* inv_d = nullptr;
+  T* b = nullptr;   // right-hand side
+  T* x = nullptr;   // iterate
+  T* r = nullptr;   // residual (deflated residual in deflation mode)
+  T* p = nullptr;   // search direction
+  T* q = nullptr;   // A p
+  T* Y = nullptr;   // forward then backward substitution values (y, then L^-T y)
+  const T* W = nullptr;   // n x M column-major, stride ld
+  const T* AW = nullptr;  // n x M column-major, stride ld
+  size_t ld = 0;          // vector stride in elements
+  const double* Einv = nullptr;  // M x M row-major (zero-padded)
+  int M = 0;              // padded number of W columns (0, 8, 16, 24, 32, 64)
+  T* samples = nullptr;   // sample slots, stride ld
+  double* ahist = nullptr;
+  double* bhist = nullptr;
+  void* partials = nullptr;
+  State* st = nullptr;
+  const unsigned char* sflags = nullptr;
+  unsigned long long cond = 0;  // graph conditional handle (0 = none)
+  int mode = ESD_PLAIN;
+  int pre = ESD_PRECOND_IC0;
+};
+
+// Optional event marks between the kernels of a launch sequence (profiling): mark() records
+// an event after each kernel, labelled with the kernel's name.
+struct KernelMarks {
+  std::vector<cudaEvent_t> ev;
+  std::vector<std::string> names;
+  void mark(cudaStream_t s, const char* name) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    cudaEventRecord(e, s);
+    ev.push_back(e);
+    names.push_back(name);
+  }
+  ~KernelMarks() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+};
+
+// Solve pieces, each a short sequence of kernel launches on stream s.
+template <typename T> void launch_init(const IterCtx<T>& c, cudaStream_t s);       // r0, z0, p0
+template <typename T>
+void launch_iteration(const IterCtx<T>& c, cudaStream_t s, KernelMarks* marks = nullptr);  // one PCG step
+template <typename T> void launch_finish(const IterCtx<T>& c, cudaStream_t s);     // flush, correction
+// ||b - A x||^2 into st->true_rr
+void launch_true_residual(const IterCtx<double>& c, cudaStream_t s);
+// y = A X for an n x m block (column-major, stride ld), m columns
+void launch_spmm(const esd_matrix* A, const double* X, double* Y, size_t ld, int m, cudaStream_t s);
+// b = x * a + s_vec
+void launch_axpby(int n, const double* x, double a, const double* sv, double* b, cudaStream_t s);
+int pad_m(int m);  // the compiled column count >= m
+
+}  // namespace esd

@@ -1,0 +1,610 @@
+// Matrix set-up: CSR validation, colour levels, the sliced-ELL copies of A, L and U, and
+// the IC(0) factorisation computed colour level by colour level on the device.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+#include "esd_internal.h"
+
+namespace esd {
+
+// ------------------------------------------------------------------ buffers and errors
+
+void DevBuf::alloc(size_t bytes) {
+  release();
+  if (bytes == 0) return;
+  cudaError_t e = cudaMalloc(&p_, bytes);
+  if (e != cudaSuccess) {
+    p_ = nullptr;
+    (void)cudaGetLastError();
+    throw Error(ESD_ERR_NOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
+                                   cudaGetErrorString(e));
+  }
+  bytes_ = bytes;
+}
+
+void DevBuf::release() {
+  if (p_) cudaFree(p_);
+  p_ = nullptr;
+  bytes_ = 0;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void copy_in(const void* src, void* dst_dev, size_t bytes, cudaStream_t s) {
+  if (bytes) ESD_CUDA(cudaMemcpyAsync(dst_dev, src, bytes, cudaMemcpyDefault, s));
+}
+
+void copy_out(const void* src_dev, void* dst, size_t bytes, cudaStream_t s) {
+  if (bytes) ESD_CUDA(cudaMemcpyAsync(dst, src_dev, bytes, cudaMemcpyDefault, s));
+}
+
+static thread_local std::string g_last_error;
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+static int g_sms = 0;
+static int sm_count() {
+  if (g_sms == 0) {
+    int dev = 0;
+    ESD_CUDA(cudaGetDevice(&dev));
+    ESD_CUDA(cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  return g_sms;
+}
+int max_grid_blocks() { return sm_count() * 4; }
+int grid_blocks(int work_slices) {
+  int need = (work_slices * kSlice + kBlock - 1) / kBlock;
+  return std::max(1, std::min(need, max_grid_blocks()));
+}
+
+// ------------------------------------------------------------------ kernels
+
+__device__ __forceinline__ int colour_of(int i, const int* cp, int ncol) {
+  int lo = 0, hi = ncol;  // cp[lo] <= i < cp[hi]
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (cp[mid] <= i) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int find_col(const int* ci, int b, int e, int key) {
+  while (b < e) {
+    int mid = (b + e) >> 1;
+    int v = ci[mid];
+    if (v == key) return mid;
+    if (v < key) b = mid + 1; else e = mid;
+  }
+  return -1;
+}
+
+enum ValidBits { kBadRowptr = 1, kBadCol = 2, kUnsorted = 4, kNoDiag = 8, kSameColour = 16, kNotSym = 32 };
+
+// Every index is checked before it is used, so malformed input sets error bits instead of
+// reading out of bounds.
+__global__ void k_validate(int n, long long nnz, const int* rp, const int* ci, const int* cp,
+                           int ncol, int* diagpos, unsigned* adj, int* err) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int b = rp[i], e = rp[i + 1];
+  unsigned bad = 0;
+  if (b < 0 || e < b || (long long)e > nnz) { bad |= kBadRowptr; b = 0; e = 0; }
+  int ci_row = colour_of(i, cp, ncol);
+  int dpos = -1, prev = -1;
+  for (int k = b; k < e; ++k) {
+    int j = ci[k];
+    if (j < 0 || j >= n) { bad |= kBadCol; continue; }
+    if (j <= prev) bad |= kUnsorted;
+    prev = j;
+    if (j == i) { dpos = k; continue; }
+    int cj = colour_of(j, cp, ncol);
+    if (cj == ci_row) bad |= kSameColour;
+    atomicOr(&adj[ci_row * ncol + cj], 1u);
+    // structural symmetry: (j, i) must exist
+    int jb = rp[j], je = rp[j + 1];
+    if (jb < 0 || je < jb || (long long)je > nnz || find_col(ci, jb, je, i) < 0) bad |= kNotSym;
+  }
+  if (dpos < 0) bad |= kNoDiag;
+  diagpos[i] = dpos < 0 ? b : dpos;
+  if (bad) {
+    atomicOr(&err[0], (int)bad);
+    atomicMin(&err[1], i);
+  }
+}
+
+__global__ void k_rowpos(int n, const int* cp, const int* first_slice, int ncol, int* rowpos) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c = colour_of(i, cp, ncol);
+  int off = i - cp[c];
+  rowpos[i] = (first_slice[c] + off / kSlice) * kSlice + off % kSlice;
+}
+
+__global__ void k_slice_widths(int nslices, const int2* rows, const int* rp, const int* diagpos,
+                               int* wA, int* wL, int* wU) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  int s = g >> 5, lane = g & 31;
+  if (s >= nslices) return;
+  int2 r = rows[s];
+  int la = 0, ll = 0, lu = 0;
+  if (lane < r.y) {
+    int i = r.x + lane;
+    la = rp[i + 1] - rp[i];
+    ll = diagpos[i] - rp[i];
+    lu = rp[i + 1] - diagpos[i] - 1;
+  }
+  la = __reduce_max_sync(0xffffffffu, la);
+  ll = __reduce_max_sync(0xffffffffu, ll);
+  lu = __reduce_max_sync(0xffffffffu, lu);
+  if (lane == 0) { wA[s] = la; wL[s] = ll; wU[s] = lu; }
+}
+
+__global__ void k_fill(int nslices, int n, const int4* mA, const int4* mL, const int4* mU,
+                       const int* rp, const int* ci, const double* va, const int* diagpos,
+                       const int* rowpos, int* colA, double* valA, int* colL, double* valL,
+                       int* colU, int* umap) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  int s = g >> 5, lane = g & 31;
+  if (s >= nslices) return;
+  int4 a = mA[s], l = mL[s], u = mU[s];
+  bool valid = lane < a.w;
+  int i = a.z + lane;
+  int b = valid ? rp[i] : 0, e = valid ? rp[i + 1] : 0, d = valid ? diagpos[i] : 0;
+  for (int k = 0; k < a.y; ++k) {
+    bool has = valid && b + k < e;
+    colA[a.x + k * kSlice + lane] = has ? ci[b + k] : n;
+    valA[a.x + k * kSlice + lane] = has ? va[b + k] : 0.0;
+  }
+  for (int k = 0; k < l.y; ++k) {
+    bool has = valid && b + k < d;
+    colL[l.x + k * kSlice + lane] = has ? ci[b + k] : n;
+    valL[l.x + k * kSlice + lane] = has ? va[b + k] : 0.0;
+  }
+  for (int k = 0; k < u.y; ++k) {
+    bool has = valid && d + 1 + k < e;
+    int j = has ? ci[d + 1 + k] : n;
+    int m = -1;
+    if (has) {
+      int q = find_col(ci, rp[j], rp[j + 1], i);  // (j, i) exists: checked in validation
+      int apos = q - rp[j];                       // position among row j's lower entries
+      int pj = rowpos[j];
+      m = mL[pj >> 5].x + apos * kSlice + (pj & 31);
+    }
+    colU[u.x + k * kSlice + lane] = j;
+    umap[u.x + k * kSlice + lane] = m;
+  }
+}
+
+// One colour level of IC(0): every row i of the level computes, in column order,
+//   l_ik = (a_ik - sum_{j<k} l_ij l_kj) / l_kk       (sum over the common pattern)
+//   l_ii = sqrt(a_ii (1 + shift) - sum_k l_ik^2),
+// reading rows k of earlier levels, which are final.
+__global__ void k_ic0_level(SliceSet set, int n, const int4* mL, const int* colL, double* valL,
+                            const int* rowpos, const int* rp, const int* diagpos,
+                            const double* csr_val, double shift, double* ldiag, int* err) {
+  const int lane = lane_id();
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int g = gw; g < set.total(); g += nw) {
+    int r;
+    const int s = set.slice(g, &r);
+    const int4 md = mL[s];
+    if (lane >= md.w) continue;
+    const int i = md.z + lane;
+    const int off = md.x;
+    double sumsq = 0.0;
+    for (int a = 0; a < md.y; ++a) {
+      const int k = colL[off + a * kSlice + lane];
+      if (k >= n) break;
+      double sacc = csr_val[rp[i] + a];
+      const int pk = rowpos[k];
+      const int4 mk = mL[pk >> 5];
+      const int lk = pk & 31;
+      int ai = 0, bk = 0;
+      while (ai < a && bk < mk.y) {
+        const int ji = colL[off + ai * kSlice + lane];
+        const int jk = colL[mk.x + bk * kSlice + lk];
+        if (jk >= n) break;
+        if (ji == jk) {
+          sacc -= valL[off + ai * kSlice + lane] * valL[mk.x + bk * kSlice + lk];
+          ++ai;
+          ++bk;
+        } else if (ji < jk) {
+          ++ai;
+        } else {
+          ++bk;
+        }
+      }
+      const double lik = sacc / ldiag[k];
+      valL[off + a * kSlice + lane] = lik;
+      sumsq += lik * lik;
+    }
+    double dpiv = csr_val[diagpos[i]] * (1.0 + shift) - sumsq;
+    if (!(dpiv > 0.0)) {
+      atomicOr(&err[2], 1);
+      atomicMin(&err[3], i);
+      dpiv = 1.0;
+    }
+    ldiag[i] = sqrt(dpiv);
+  }
+}
+
+__global__ void k_ic0_finish(int n, const double* ldiag, double* inv_d, long long nU,
+                             const int* umap, const double* valL, double* valU) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = t; i < n; i += stride) inv_d[i] = 1.0 / ldiag[i];
+  if (t == 0) inv_d[n] = 0.0;
+  for (long long e = t; e < nU; e += stride) {
+    int m = umap[e];
+    valU[e] = m >= 0 ? valL[m] : 0.0;
+  }
+}
+
+__global__ void k_to_float(long long cnt, const double* a, float* b) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = t; i < cnt; i += stride) b[i] = (float)a[i];
+}
+
+static void to_float(const DevBuf& src, DevBuf& dst, long long cnt, cudaStream_t s) {
+  if (dst.bytes() < (size_t)cnt * sizeof(float)) dst.alloc((size_t)cnt * sizeof(float));
+  if (cnt == 0) return;
+  k_to_float<<<max_grid_blocks(), kBlock, 0, s>>>(cnt, src.as<double>(), dst.as<float>());
+  ESD_CUDA(cudaGetLastError());
+}
+
+}  // namespace esd
+
+using namespace esd;
+
+void esd_matrix::ensure_fp32() {
+  if (fp32_version == factor_version && A.val32.get()) return;
+  to_float(A.val, A.val32, A.entries, stream);
+  if (factored) {
+    to_float(L.val, L.val32, L.entries, stream);
+    to_float(U.val, U.val32, U.entries, stream);
+    to_float(inv_d, inv_d32, (long long)vec_stride(), stream);
+  }
+  fp32_version = factor_version;
+}
+
+// ------------------------------------------------------------------ creation
+
+static void build_level_sets(esd_matrix* M, const std::vector<unsigned>& adj) {
+  const int C = M->ncol;
+  M->fwd_level.assign(C, 0);
+  M->bwd_level.assign(C, 0);
+  for (int c = 0; c < C; ++c) {
+    int lv = -1;
+    for (int d = 0; d < c; ++d)
+      if (adj[c * C + d] || adj[d * C + c]) lv = std::max(lv, M->fwd_level[d]);
+    M->fwd_level[c] = lv + 1;
+  }
+  for (int c = C - 1; c >= 0; --c) {
+    int lv = -1;
+    for (int d = c + 1; d < C; ++d)
+      if (adj[c * C + d] || adj[d * C + c]) lv = std::max(lv, M->bwd_level[d]);
+    M->bwd_level[c] = lv + 1;
+  }
+  auto nsl = [&](int c) { return M->colour_first_slice[c + 1] - M->colour_first_slice[c]; };
+  // Ranges: maximal runs of consecutive colours that share the same flags; a set holds at
+  // most kMaxRanges ranges (further ranges open a new launch of the same level).
+  struct Range { int c0, c1; unsigned f0, b0, elem; };
+  auto make_sets = [&](const std::vector<Range>& rs) {
+    std::vector<SliceSet> out;
+    SliceSet cur{};
+    auto flush = [&]() { if (cur.nr) { out.push_back(cur); cur = SliceSet{}; } };
+    for (const Range& r : rs) {
+      int len = 0;
+      for (int c = r.c0; c <= r.c1; ++c) len += nsl(c);
+      if (len == 0) continue;
+      if (cur.nr == kMaxRanges) flush();
+      cur.begin[cur.nr] = M->colour_first_slice[r.c0];
+      cur.cum[cur.nr + 1] = cur.cum[cur.nr] + len;
+      if (r.f0) cur.fwd0 |= 1u << cur.nr;
+      if (r.b0) cur.bwd0 |= 1u << cur.nr;
+      (void)r.elem;
+      ++cur.nr;
+    }
+    flush();
+    return out;
+  };
+  auto ranges_of = [&](const std::vector<int>& cols, bool elem) {
+    std::vector<Range> rs;
+    for (int c : cols) {
+      unsigned f0 = M->fwd_level[c] == 0, b0 = M->bwd_level[c] == 0;
+      if (!rs.empty() && rs.back().c1 == c - 1 && rs.back().f0 == f0 && rs.back().b0 == b0)
+        rs.back().c1 = c;
+      else
+        rs.push_back({c, c, f0, b0, elem ? 1u : 0u});
+    }
+    return rs;
+  };
+  int maxf = *std::max_element(M->fwd_level.begin(), M->fwd_level.end());
+  int maxb = *std::max_element(M->bwd_level.begin(), M->bwd_level.end());
+  M->fwd_sets.clear();
+  M->bwd_sets.clear();
+  M->fwd_all_sets.clear();
+  for (int lv = 0; lv <= maxf; ++lv) {
+    std::vector<int> cols;
+    for (int c = 0; c < C; ++c)
+      if (M->fwd_level[c] == lv) cols.push_back(c);
+    auto sets = make_sets(ranges_of(cols, false));
+    for (auto& s : sets) {
+      M->fwd_all_sets.push_back(s);
+      if (lv >= 1) M->fwd_sets.push_back(s);
+    }
+  }
+  M->bwd_all_sets.clear();
+  M->bwd0_sets.clear();
+  for (int lv = 0; lv <= maxb; ++lv) {
+    std::vector<int> cols;
+    for (int c = 0; c < C; ++c)
+      if (M->bwd_level[c] == lv) cols.push_back(c);
+    auto sets = make_sets(ranges_of(cols, false));
+    for (auto& s : sets) {
+      M->bwd_all_sets.push_back(s);
+      if (lv >= 1) M->bwd_sets.push_back(s); else M->bwd0_sets.push_back(s);
+    }
+  }
+  // the "all slices" set
+  SliceSet all{};
+  all.nr = 1;
+  all.begin[0] = 0;
+  all.cum[1] = M->nslices;
+  M->all = all;
+}
+
+extern "C" {
+
+const char* esd_last_error(void) { return g_last_error.c_str(); }
+
+int esd_create_matrix(int32_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colind,
+                      const double* val, const int32_t* colour_ptr, int32_t ncolours,
+                      uint32_t flags, void* stream, esd_matrix** out) {
+  try {
+    ESD_CHECK(out != nullptr, ESD_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    ESD_CHECK(n >= 1 && n < INT32_MAX - 64, ESD_ERR_INVALID, "n out of range");
+    ESD_CHECK(nnz >= n && nnz < (int64_t)INT32_MAX, ESD_ERR_INVALID, "nnz out of range");
+    ESD_CHECK(rowptr && colind && val && colour_ptr, ESD_ERR_INVALID, "NULL array");
+    ESD_CHECK(ncolours >= 1 && ncolours <= kMaxColours, ESD_ERR_INVALID, "ncolours must be 1..64");
+    ESD_CHECK(flags == 0, ESD_ERR_INVALID, "flags must be 0");
+    std::unique_ptr<esd_matrix> M(new esd_matrix());
+    M->n = n;
+    M->nnz = nnz;
+    M->ncol = ncolours;
+    M->stream = (cudaStream_t)stream;
+    cudaStream_t s = M->stream;
+    M->cp.assign(colour_ptr, colour_ptr + ncolours + 1);
+    ESD_CHECK(M->cp[0] == 0 && M->cp[ncolours] == n, ESD_ERR_INVALID, "colour_ptr must span 0..n");
+    for (int c = 0; c < ncolours; ++c)
+      ESD_CHECK(M->cp[c + 1] >= M->cp[c], ESD_ERR_INVALID, "colour_ptr must be non-decreasing");
+
+    // the CSR as given
+    M->csr_rowptr.alloc(sizeof(int) * (n + 1));
+    M->csr_colind.alloc(sizeof(int) * nnz);
+    M->csr_val.alloc(sizeof(double) * nnz);
+    copy_in(rowptr, M->csr_rowptr.get(), sizeof(int) * (n + 1), s);
+    copy_in(colind, M->csr_colind.get(), sizeof(int) * nnz, s);
+    copy_in(val, M->csr_val.get(), sizeof(double) * nnz, s);
+    int ends[2];
+    ESD_CUDA(cudaMemcpyAsync(&ends[0], M->csr_rowptr.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, s));
+    ESD_CUDA(cudaMemcpyAsync(&ends[1], M->csr_rowptr.as<int>() + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ESD_CUDA(cudaStreamSynchronize(s));
+    ESD_CHECK(ends[0] == 0 && ends[1] == nnz, ESD_ERR_INVALID, "rowptr[0] must be 0 and rowptr[n] = nnz");
+
+    // validation + colour adjacency
+    DevBuf dcp(sizeof(int) * (ncolours + 1)), adj(sizeof(unsigned) * ncolours * ncolours),
+        diagpos(sizeof(int) * n);
+    M->err.alloc(sizeof(int) * 4);
+    int err_init[4] = {0, INT32_MAX, 0, INT32_MAX};
+    ESD_CUDA(cudaMemcpyAsync(dcp.get(), M->cp.data(), sizeof(int) * (ncolours + 1), cudaMemcpyHostToDevice, s));
+    ESD_CUDA(cudaMemsetAsync(adj.get(), 0, adj.bytes(), s));
+    ESD_CUDA(cudaMemcpyAsync(M->err.get(), err_init, sizeof(err_init), cudaMemcpyHostToDevice, s));
+    k_validate<<<(n + 255) / 256, 256, 0, s>>>(n, nnz, M->csr_rowptr.as<int>(), M->csr_colind.as<int>(),
+                                               dcp.as<int>(), ncolours, diagpos.as<int>(),
+                                               adj.as<unsigned>(), M->err.as<int>());
+    ESD_CUDA(cudaGetLastError());
+    int herr[4];
+    std::vector<unsigned> hadj(ncolours * ncolours);
+    ESD_CUDA(cudaMemcpyAsync(herr, M->err.get(), sizeof(herr), cudaMemcpyDeviceToHost, s));
+    ESD_CUDA(cudaMemcpyAsync(hadj.data(), adj.get(), adj.bytes(), cudaMemcpyDeviceToHost, s));
+    ESD_CUDA(cudaStreamSynchronize(s));
+    if (herr[0]) {
+      std::string why;
+      if (herr[0] & kBadRowptr) why += " decreasing rowptr;";
+      if (herr[0] & kBadCol) why += " column index out of range;";
+      if (herr[0] & kUnsorted) why += " columns not strictly increasing;";
+      if (herr[0] & kNoDiag) why += " missing diagonal entry;";
+      if (herr[0] & kSameColour) why += " two rows of one colour are coupled;";
+      if (herr[0] & kNotSym) why += " pattern not structurally symmetric;";
+      throw Error(ESD_ERR_INVALID, "invalid matrix (first bad row " + std::to_string(herr[1]) + "):" + why);
+    }
+
+    // slices: 32-row slices inside each colour
+    M->colour_first_slice.assign(ncolours + 1, 0);
+    std::vector<int2> rows;
+    for (int c = 0; c < ncolours; ++c) {
+      M->colour_first_slice[c] = (int)rows.size();
+      for (int r0 = M->cp[c]; r0 < M->cp[c + 1]; r0 += kSlice)
+        rows.push_back(make_int2(r0, std::min(kSlice, M->cp[c + 1] - r0)));
+    }
+    M->colour_first_slice[ncolours] = (int)rows.size();
+    M->nslices = (int)rows.size();
+    const int NS = M->nslices;
+    DevBuf drows(sizeof(int2) * NS), wA(sizeof(int) * NS), wL(sizeof(int) * NS), wU(sizeof(int) * NS),
+        dfirst(sizeof(int) * (ncolours + 1));
+    ESD_CUDA(cudaMemcpyAsync(drows.get(), rows.data(), drows.bytes(), cudaMemcpyHostToDevice, s));
+    ESD_CUDA(cudaMemcpyAsync(dfirst.get(), M->colour_first_slice.data(), dfirst.bytes(), cudaMemcpyHostToDevice, s));
+    M->rowpos.alloc(sizeof(int) * n);
+    k_rowpos<<<(n + 255) / 256, 256, 0, s>>>(n, dcp.as<int>(), dfirst.as<int>(), ncolours, M->rowpos.as<int>());
+    k_slice_widths<<<(NS * 32 + 255) / 256, 256, 0, s>>>(NS, drows.as<int2>(), M->csr_rowptr.as<int>(),
+                                                         diagpos.as<int>(), wA.as<int>(), wL.as<int>(),
+                                                         wU.as<int>());
+    ESD_CUDA(cudaGetLastError());
+    std::vector<int> hwA(NS), hwL(NS), hwU(NS);
+    ESD_CUDA(cudaMemcpyAsync(hwA.data(), wA.get(), wA.bytes(), cudaMemcpyDeviceToHost, s));
+    ESD_CUDA(cudaMemcpyAsync(hwL.data(), wL.get(), wL.bytes(), cudaMemcpyDeviceToHost, s));
+    ESD_CUDA(cudaMemcpyAsync(hwU.data(), wU.get(), wU.bytes(), cudaMemcpyDeviceToHost, s));
+    ESD_CUDA(cudaStreamSynchronize(s));
+
+    auto build_meta = [&](const std::vector<int>& w, Sell& part) {
+      std::vector<int4> meta(NS);
+      long long off = 0;
+      for (int i = 0; i < NS; ++i) {
+        meta[i] = make_int4((int)off, w[i], rows[i].x, rows[i].y);
+        off += (long long)w[i] * kSlice;
+        ESD_CHECK(off < (long long)INT32_MAX, ESD_ERR_INVALID, "matrix too large for 32-bit slice offsets");
+      }
+      part.entries = off;
+      part.meta.alloc(sizeof(int4) * NS);
+      ESD_CUDA(cudaMemcpyAsync(part.meta.get(), meta.data(), part.meta.bytes(), cudaMemcpyHostToDevice, s));
+      part.col.alloc(sizeof(int) * std::max(off, 1LL));
+      part.val.alloc(sizeof(double) * std::max(off, 1LL));
+      ESD_CUDA(cudaStreamSynchronize(s));  // meta is a stack vector
+    };
+    build_meta(hwA, M->A);
+    build_meta(hwL, M->L);
+    build_meta(hwU, M->U);
+    M->umap.alloc(sizeof(int) * std::max(M->U.entries, 1LL));
+    k_fill<<<(NS * 32 + 255) / 256, 256, 0, s>>>(
+        NS, n, M->A.meta.as<int4>(), M->L.meta.as<int4>(), M->U.meta.as<int4>(), M->csr_rowptr.as<int>(),
+        M->csr_colind.as<int>(), M->csr_val.as<double>(), diagpos.as<int>(), M->rowpos.as<int>(),
+        M->A.col.as<int>(), M->A.val.as<double>(), M->L.col.as<int>(), M->L.val.as<double>(),
+        M->U.col.as<int>(), M->umap.as<int>());
+    ESD_CUDA(cudaGetLastError());
+
+    // slice flags and launch sets
+    build_level_sets(M.get(), hadj);
+    std::vector<unsigned char> sflags(NS, 0);
+    for (int c = 0; c < ncolours; ++c)
+      for (int sl = M->colour_first_slice[c]; sl < M->colour_first_slice[c + 1]; ++sl)
+        sflags[sl] = (M->fwd_level[c] == 0 ? 1 : 0) | (M->bwd_level[c] == 0 ? 2 : 0);
+    M->slice_flags.alloc(NS);
+    ESD_CUDA(cudaMemcpyAsync(M->slice_flags.get(), sflags.data(), NS, cudaMemcpyHostToDevice, s));
+
+    M->ldiag.alloc(sizeof(double) * M->vec_stride());
+    M->inv_d.alloc(sizeof(double) * M->vec_stride());
+    ESD_CUDA(cudaMemsetAsync(M->inv_d.get(), 0, M->inv_d.bytes(), s));
+    M->tmp.alloc(sizeof(double) * M->vec_stride() * 3);
+    ESD_CUDA(cudaMemsetAsync(M->tmp.get(), 0, M->tmp.bytes(), s));
+    M->scratch.partials.alloc(sizeof(double) * (size_t)max_grid_blocks() * kMaxRed);
+    M->scratch.state.alloc(sizeof(State));
+    ESD_CUDA(cudaMemsetAsync(M->scratch.state.get(), 0, sizeof(State), s));
+    M->diagpos = std::move(diagpos);  // kept for the factorisation
+    ESD_CUDA(cudaStreamSynchronize(s));
+    *out = M.release();
+    return ESD_OK;
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.code;
+  } catch (const std::exception& e) {
+    set_last_error(e.what());
+    return ESD_ERR_INVALID;
+  }
+}
+
+int esd_matrix_destroy(esd_matrix* A) {
+  delete A;
+  return ESD_OK;
+}
+
+int esd_matrix_info(const esd_matrix* A, int32_t* n, int64_t* nnz, int32_t* ncolours,
+                    int32_t* fwd_levels, int32_t* bwd_levels) {
+  if (!A) { set_last_error("NULL matrix"); return ESD_ERR_INVALID; }
+  if (n) *n = A->n;
+  if (nnz) *nnz = A->nnz;
+  if (ncolours) *ncolours = A->ncol;
+  if (fwd_levels) *fwd_levels = 1 + *std::max_element(A->fwd_level.begin(), A->fwd_level.end());
+  if (bwd_levels) *bwd_levels = 1 + *std::max_element(A->bwd_level.begin(), A->bwd_level.end());
+  return ESD_OK;
+}
+
+int esd_factor_ic0(esd_matrix* A, int32_t max_tries, double* shift_used) {
+  try {
+    ESD_CHECK(A != nullptr, ESD_ERR_INVALID, "NULL matrix");
+    ESD_CHECK(max_tries >= 1, ESD_ERR_INVALID, "max_tries must be >= 1");
+    cudaStream_t s = A->stream;
+    const int* diagpos = A->diagpos.as<int>();
+    double shift = 0.0;
+    for (int t = 0; t < max_tries; ++t) {
+      int err_init[4] = {0, INT32_MAX, 0, INT32_MAX};
+      ESD_CUDA(cudaMemcpyAsync(A->err.get(), err_init, sizeof(err_init), cudaMemcpyHostToDevice, s));
+      for (const SliceSet& set : A->fwd_all_sets) {
+        k_ic0_level<<<grid_blocks(set.total()), kBlock, 0, s>>>(
+            set, A->n, A->L.meta.as<int4>(), A->L.col.as<int>(), A->L.val.as<double>(), A->rowpos.as<int>(),
+            A->csr_rowptr.as<int>(), diagpos, A->csr_val.as<double>(), shift, A->ldiag.as<double>(),
+            A->err.as<int>());
+        ESD_CUDA(cudaGetLastError());
+      }
+      int herr[4];
+      ESD_CUDA(cudaMemcpyAsync(herr, A->err.get(), sizeof(herr), cudaMemcpyDeviceToHost, s));
+      ESD_CUDA(cudaStreamSynchronize(s));
+      if (herr[2] == 0) {
+        k_ic0_finish<<<max_grid_blocks(), kBlock, 0, s>>>(A->n, A->ldiag.as<double>(), A->inv_d.as<double>(),
+                                                          A->U.entries, A->umap.as<int>(),
+                                                          A->L.val.as<double>(), A->U.val.as<double>());
+        ESD_CUDA(cudaGetLastError());
+        ESD_CUDA(cudaStreamSynchronize(s));
+        A->factored = true;
+        A->shift = shift;
+        A->factor_version++;
+        if (shift_used) *shift_used = shift;
+        return ESD_OK;
+      }
+      shift = (shift == 0.0) ? 1e-3 : 2.0 * shift;
+    }
+    A->factored = false;
+    throw Error(ESD_ERR_NOT_SPD, "IC(0) pivot not positive after " + std::to_string(max_tries) + " attempts");
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.code;
+  }
+}
+
+int esd_matrix_spmv(esd_matrix* A, const double* x, double* y) {
+  try {
+    ESD_CHECK(A && x && y, ESD_ERR_INVALID, "NULL argument");
+    cudaStream_t s = A->stream;
+    double* tx = A->tmp.as<double>();
+    double* ty = tx + A->vec_stride();
+    copy_in(x, tx, sizeof(double) * A->n, s);
+    launch_spmv(A, tx, ty, s);
+    copy_out(ty, y, sizeof(double) * A->n, s);
+    ESD_CUDA(cudaStreamSynchronize(s));
+    return ESD_OK;
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.code;
+  }
+}
+
+int esd_matrix_apply_ic(esd_matrix* A, const double* r, double* z) {
+  try {
+    ESD_CHECK(A && r && z, ESD_ERR_INVALID, "NULL argument");
+    ESD_CHECK(A->factored, ESD_ERR_STATE, "esd_factor_ic0 has not succeeded on this matrix");
+    cudaStream_t s = A->stream;
+    double* tr = A->tmp.as<double>();
+    double* tz = tr + A->vec_stride();
+    double* ty = tz + A->vec_stride();
+    copy_in(r, tr, sizeof(double) * A->n, s);
+    launch_apply_ic(A, tr, tz, ty, s);
+    copy_out(tz, z, sizeof(double) * A->n, s);
+    ESD_CUDA(cudaStreamSynchronize(s));
+    return ESD_OK;
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.code;
+  }
+}
+
+}  // extern "C"

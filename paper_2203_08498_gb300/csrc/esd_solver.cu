@@ -1,0 +1,598 @@
+// Solver runtime: device buffers, one CUDA graph per mode (the whole solve, with the PCG
+// loop as a device-side conditional while node), the auxiliary-matrix construction, the
+// Lanczos condition estimate and the C ABI of the solver.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <memory>
+#include <vector>
+
+#include "esd_dense.h"
+
+namespace esd {
+
+// ------------------------------------------------------------------ small kernels
+
+// Extreme eigenvalues of the CG Lanczos matrix T (diag 1/a_j + b_{j-1}/a_{j-1}, off-diagonal
+// sqrt(b_j)/a_j) by multisection on Sturm counts: every round the 256 threads count the
+// eigenvalues below 256 points of the current bracket.
+__device__ int sturm_count(const double* a, const double* b, int k, double x) {
+  int cnt = 0;
+  double q = 1.0;
+  const double pivmin = 1e-300;
+  for (int j = 0; j < k; ++j) {
+    double d = 1.0 / a[j];
+    double e2 = 0.0;
+    if (j > 0) {
+      d += b[j - 1] / a[j - 1];
+      const double e = sqrt(b[j - 1]) / a[j - 1];
+      e2 = e * e;
+    }
+    q = (j == 0) ? d - x : d - x - e2 / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+__global__ void k_lanczos_extremes(const double* a, const double* b, int k, double* out) {
+  __shared__ double lo_s, hi_s;
+  __shared__ int cnt_s[256];
+  // Gershgorin bracket
+  if (threadIdx.x == 0) {
+    double lo = 1e300, hi = -1e300;
+    for (int j = 0; j < k; ++j) {
+      double d = 1.0 / a[j];
+      if (j > 0) d += b[j - 1] / a[j - 1];
+      double r = 0.0;
+      if (j > 0) r += fabs(sqrt(b[j - 1]) / a[j - 1]);
+      if (j + 1 < k) r += fabs(sqrt(b[j]) / a[j]);
+      lo = fmin(lo, d - r);
+      hi = fmax(hi, d + r);
+    }
+    const double pad = 1e-12 * fmax(fabs(lo), fabs(hi)) + 1e-300;
+    lo_s = lo - pad;
+    hi_s = hi + pad;
+  }
+  __syncthreads();
+  const double glo = lo_s, ghi = hi_s;
+  for (int which = 0; which < 2; ++which) {
+    // which 0: smallest eigenvalue (count goes 0 -> >=1); 1: largest (count k-1 -> k)
+    double lo = glo, hi = ghi;
+    const int target = which == 0 ? 1 : k;
+    for (int round = 0; round < 12; ++round) {
+      const double x = lo + (hi - lo) * (threadIdx.x + 1) / 257.0;
+      cnt_s[threadIdx.x] = sturm_count(a, b, k, x);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        // first point whose count reaches the target
+        int t = 256;
+        for (int i = 0; i < 256; ++i)
+          if (cnt_s[i] >= target) { t = i; break; }
+        const double w = (hi - lo) / 257.0;
+        const double nlo = lo + w * t;
+        const double nhi = (t < 256) ? lo + w * (t + 1) : hi;
+        lo_s = nlo;
+        hi_s = nhi;
+      }
+      __syncthreads();
+      lo = lo_s;
+      hi = hi_s;
+      __syncthreads();
+      if (hi - lo <= 1e-15 * fmax(fabs(lo), fabs(hi))) break;
+    }
+    if (threadIdx.x == 0) out[which] = 0.5 * (lo + hi);
+    __syncthreads();
+  }
+}
+
+__global__ void k_pattern_grad(int n, const int* rp, const int* ci, const double* lam, const double* x,
+                               double* grad) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double li = lam[i];
+    for (int k = rp[i]; k < rp[i + 1]; ++k) grad[k] = -li * x[ci[k]];
+  }
+}
+
+}  // namespace esd
+
+using namespace esd;
+
+struct esd_solver {
+  esd_matrix* A = nullptr;
+  esd_params prm{};
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;   // private capture streams
+  cudaStream_t cap2 = nullptr;
+  int mode = ESD_PLAIN;
+  size_t ld = 0;
+  DevBuf vb, vx, vr, vp, vq, vY, samples;
+  DevBuf W, AW, E, Einv, ritz, ahist, bhist, state, partials, ext;
+  State* hst = nullptr;  // pinned host copy
+  int m = 0, M = 0;      // columns of W, padded count
+  int mbar = 0;
+  bool have_W = false;
+  int w_version = 0;
+  cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
+  int exec_version[3] = {-1, -1, -1};
+  int last_iters = 0, last_status = 0, last_sample_m = 0, last_maxit = 0;
+  double last_relres = 0.0, last_true = 0.0;
+  AuxBuild aux;
+
+  ~esd_solver() {
+    for (auto& e : exec)
+      if (e) cudaGraphExecDestroy(e);
+    if (cap) cudaStreamDestroy(cap);
+    if (cap2) cudaStreamDestroy(cap2);
+    if (hst) cudaFreeHost(hst);
+  }
+
+  IterCtx<double> ctx(int md) const {
+    IterCtx<double> c;
+    c.A = A;
+    c.Av = A->A.view<double>();
+    c.Lv = A->L.view<double>();
+    c.Uv = A->U.view<double>();
+    c.inv_d = A->inv_d.as<double>();
+    c.b = vb.as<double>();
+    c.x = vx.as<double>();
+    c.r = vr.as<double>();
+    c.p = vp.as<double>();
+    c.q = vq.as<double>();
+    c.Y = vY.as<double>();
+    c.ld = ld;
+    c.mode = md;
+    c.pre = prm.precond;
+    if (md != ESD_PLAIN) {
+      c.W = W.as<double>();
+      c.AW = AW.as<double>();
+      c.Einv = Einv.as<double>();
+      c.M = M;
+    }
+    c.samples = samples.get() ? samples.as<double>() : nullptr;
+    c.ahist = ahist.as<double>();
+    c.bhist = bhist.as<double>();
+    c.partials = partials.get();
+    c.st = state.as<State>();
+    c.sflags = A->slice_flags.as<unsigned char>();
+    return c;
+  }
+
+  void build_graph(int md) {
+    if (exec[md] && exec_version[md] == w_version) return;
+    if (exec[md]) {
+      cudaGraphExecDestroy(exec[md]);
+      exec[md] = nullptr;
+    }
+    cudaGraph_t g;
+    ESD_CUDA(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    ESD_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    IterCtx<double> c = ctx(md);
+    c.cond = (unsigned long long)h;
+    ESD_CUDA(cudaStreamBeginCaptureToGraph(cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    try {
+      launch_init<double>(c, cap);
+      cudaStreamCaptureStatus cs;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t nd = 0;
+      ESD_CUDA(cudaStreamGetCaptureInfo(cap, &cs, nullptr, nullptr, &deps, nullptr, &nd));
+      cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+      np.conditional.handle = h;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      cudaGraphNode_t wnode;
+      ESD_CUDA(cudaGraphAddNode(&wnode, g, deps, nullptr, nd, &np));
+      cudaGraph_t body = np.conditional.phGraph_out[0];
+      ESD_CUDA(cudaStreamUpdateCaptureDependencies(cap, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+      ESD_CUDA(cudaStreamBeginCaptureToGraph(cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+      try {
+        launch_iteration<double>(c, cap2);
+      } catch (...) {
+        cudaGraph_t dummy;
+        cudaStreamEndCapture(cap2, &dummy);
+        throw;
+      }
+      ESD_CUDA(cudaStreamEndCapture(cap2, &body));
+      launch_finish<double>(c, cap);
+      launch_true_residual(c, cap);
+    } catch (...) {
+      cudaGraph_t dummy;
+      cudaStreamEndCapture(cap, &dummy);
+      cudaGraphDestroy(g);
+      throw;
+    }
+    ESD_CUDA(cudaStreamEndCapture(cap, &g));
+    cudaGraphExec_t e;
+    cudaError_t err = cudaGraphInstantiate(&e, g, 0);
+    cudaGraphDestroy(g);
+    ESD_CUDA(err);
+    exec[md] = e;
+    exec_version[md] = w_version;
+  }
+};
+
+static int smallest_lmax(int m, int maxit) {
+  if (m < 2) return 0;
+  int l = 0;
+  long long p = 1;
+  while (p <= maxit) {
+    p *= m;
+    ++l;
+  }
+  return l;
+}
+
+#define ESD_API_BEGIN try {
+#define ESD_API_END                  \
+  }                                  \
+  catch (const Error& e) {           \
+    set_last_error(e.what());        \
+    return e.code;                   \
+  }                                  \
+  catch (const std::exception& e) {  \
+    set_last_error(e.what());        \
+    return ESD_ERR_INVALID;          \
+  }
+
+extern "C" {
+
+void esd_params_default(esd_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->precond = ESD_PRECOND_IC0;
+  p->maxit_cap = 20000;
+  p->sample_cap = 32;
+  p->lmax = 0;
+  p->rank_tol = 1e-12;
+  p->precision = ESD_FP64;
+  p->inner_tol = 1e-4;
+  p->max_outer = 30;
+}
+
+int esd_solver_create(esd_matrix* A, const esd_params* params, esd_solver** out) {
+  ESD_API_BEGIN
+  ESD_CHECK(A && out, ESD_ERR_INVALID, "NULL argument");
+  *out = nullptr;
+  esd_params p;
+  if (params) p = *params; else esd_params_default(&p);
+  ESD_CHECK(p.precond == ESD_PRECOND_NONE || p.precond == ESD_PRECOND_IC0, ESD_ERR_INVALID, "bad precond");
+  ESD_CHECK(p.maxit_cap >= 1, ESD_ERR_INVALID, "maxit_cap must be >= 1");
+  ESD_CHECK(p.sample_cap >= 0 && p.sample_cap <= kMaxM, ESD_ERR_INVALID, "sample_cap must be 0..64");
+  ESD_CHECK(p.precision == ESD_FP64, ESD_ERR_INVALID, "this build solves in FP64 only");
+  ESD_CHECK(p.precond == ESD_PRECOND_NONE || A->factored, ESD_ERR_STATE, "IC(0) preconditioner needs esd_factor_ic0");
+  std::unique_ptr<esd_solver> S(new esd_solver());
+  S->A = A;
+  S->prm = p;
+  S->stream = A->stream;
+  S->ld = A->vec_stride();
+  const size_t vbytes = sizeof(double) * S->ld;
+  for (DevBuf* b : {&S->vb, &S->vx, &S->vr, &S->vp, &S->vq, &S->vY}) {
+    b->alloc(vbytes);
+    ESD_CUDA(cudaMemsetAsync(b->get(), 0, vbytes, S->stream));
+  }
+  if (p.sample_cap > 0) {
+    S->samples.alloc(vbytes * p.sample_cap);
+    ESD_CUDA(cudaMemsetAsync(S->samples.get(), 0, S->samples.bytes(), S->stream));
+  }
+  S->ahist.alloc(sizeof(double) * p.maxit_cap);
+  S->bhist.alloc(sizeof(double) * p.maxit_cap);
+  S->state.alloc(sizeof(State));
+  ESD_CUDA(cudaMemsetAsync(S->state.get(), 0, sizeof(State), S->stream));
+  S->partials.alloc(sizeof(double) * (size_t)max_grid_blocks() * kMaxRed);
+  S->E.alloc(sizeof(double) * kMaxM * kMaxM);
+  S->Einv.alloc(sizeof(double) * kMaxM * kMaxM);
+  S->ritz.alloc(sizeof(double) * kMaxM);
+  S->ext.alloc(sizeof(double) * 4);
+  ESD_CUDA(cudaMallocHost(&S->hst, sizeof(State)));
+  std::memset(S->hst, 0, sizeof(State));
+  ESD_CUDA(cudaStreamCreateWithFlags(&S->cap, cudaStreamNonBlocking));
+  ESD_CUDA(cudaStreamCreateWithFlags(&S->cap2, cudaStreamNonBlocking));
+  ESD_CUDA(cudaStreamSynchronize(S->stream));
+  *out = S.release();
+  return ESD_OK;
+  ESD_API_END
+}
+
+int esd_solver_destroy(esd_solver* S) {
+  if (S) {
+    cudaStreamSynchronize(S->stream);
+    delete S;
+  }
+  return ESD_OK;
+}
+
+int esd_set_mode(esd_solver* S, int32_t mode) {
+  ESD_API_BEGIN
+  ESD_CHECK(S, ESD_ERR_INVALID, "NULL solver");
+  ESD_CHECK(mode == ESD_PLAIN || mode == ESD_DEFLATION || mode == ESD_SUBSPACE_CORRECTION, ESD_ERR_INVALID,
+            "unknown mode");
+  ESD_CHECK(mode == ESD_PLAIN || S->have_W, ESD_ERR_STATE, "deflation / subspace correction need W");
+  S->mode = mode;
+  return ESD_OK;
+  ESD_API_END
+}
+
+int esd_solve(esd_solver* S, const double* b, double* x, double tol, int32_t maxit, int32_t sample_m,
+              int32_t* iters, double* relres) {
+  ESD_API_BEGIN
+  ESD_CHECK(S && b && x, ESD_ERR_INVALID, "NULL argument");
+  ESD_CHECK(tol > 0.0 && std::isfinite(tol), ESD_ERR_INVALID, "tol must be positive");
+  ESD_CHECK(maxit >= 1 && maxit <= S->prm.maxit_cap, ESD_ERR_INVALID, "maxit must be 1..maxit_cap");
+  ESD_CHECK(sample_m >= 0 && sample_m <= S->prm.sample_cap, ESD_ERR_INVALID, "sample_m must be 0..sample_cap");
+  ESD_CHECK(sample_m == 0 || S->mode != ESD_DEFLATION, ESD_ERR_STATE,
+            "sampling is defined on plain / subspace-correction iterates, not in deflation mode");
+  ESD_CHECK(sample_m != 1, ESD_ERR_INVALID, "sampling method A needs m >= 2");
+  cudaStream_t s = S->stream;
+  const int n = S->A->n;
+  S->build_graph(S->mode);
+  copy_in(b, S->vb.get(), sizeof(double) * n, s);
+  copy_in(x, S->vx.get(), sizeof(double) * n, s);
+  State* h = S->hst;
+  std::memset(h, 0, sizeof(State));
+  h->scal0 = tol * tol;
+  h->maxit = maxit;
+  h->samp_m = sample_m;
+  h->lmax = S->prm.lmax > 0 ? S->prm.lmax : smallest_lmax(sample_m, maxit);
+  h->h = 1;
+  h->pend_slot = -1;
+  ESD_CUDA(cudaMemcpyAsync(S->state.get(), h, sizeof(State), cudaMemcpyHostToDevice, s));
+  ESD_CUDA(cudaGraphLaunch(S->exec[S->mode], s));
+  copy_out(S->vx.get(), x, sizeof(double) * n, s);
+  ESD_CUDA(cudaMemcpyAsync(h, S->state.get(), sizeof(State), cudaMemcpyDeviceToHost, s));
+  ESD_CUDA(cudaStreamSynchronize(s));
+  S->last_iters = h->iter;
+  S->last_status = h->status;
+  S->last_sample_m = sample_m;
+  S->last_maxit = maxit;
+  S->last_relres = h->bb > 0.0 ? std::sqrt(h->rr / h->bb) : 0.0;
+  S->last_true = h->bb > 0.0 ? std::sqrt(h->true_rr / h->bb) : 0.0;
+  if (iters) *iters = h->iter;
+  if (relres) *relres = S->last_relres;
+  if (h->status == ESD_ERR_MAXIT) {
+    set_last_error("tolerance not reached within maxit iterations");
+    return ESD_ERR_MAXIT;
+  }
+  if (h->status == ESD_ERR_INTERNAL) {
+    set_last_error("internal loop guard stopped the solve");
+    return ESD_ERR_INTERNAL;
+  }
+  if (h->status == ESD_ERR_BREAKDOWN) {
+    set_last_error("CG breakdown: (p, Ap) or (r, z) not positive");
+    return ESD_ERR_BREAKDOWN;
+  }
+  return ESD_OK;
+  ESD_API_END
+}
+
+int esd_true_relres(esd_solver* S, double* relres) {
+  if (!S || !relres) { set_last_error("NULL argument"); return ESD_ERR_INVALID; }
+  *relres = S->last_true;
+  return ESD_OK;
+}
+
+static void install_W(esd_solver* S, const double* X, int m, bool orth, double theta) {
+  const size_t ld = S->ld;
+  S->aux.ensure(S->A->n, ld);
+  const int mpad_max = kMaxM;
+  if (!S->W.get()) {
+    S->W.alloc(sizeof(double) * ld * mpad_max);
+    S->AW.alloc(sizeof(double) * ld * mpad_max);
+  }
+  int mbar = 0;
+  const int mkeep = build_aux(S->A, S->aux, X, m, orth, S->prm.rank_tol, theta, S->W.as<double>(),
+                              S->AW.as<double>(), S->E.as<double>(), S->Einv.as<double>(),
+                              S->ritz.as<double>(), &mbar, S->stream);
+  ESD_CUDA(cudaStreamSynchronize(S->stream));
+  S->m = mkeep;
+  S->M = pad_cols(mkeep);
+  S->mbar = mbar;
+  S->have_W = true;
+  S->w_version++;
+}
+
+int esd_sample_and_build_W(esd_solver* S, double theta, int32_t* m_kept) {
+  ESD_API_BEGIN
+  ESD_CHECK(S, ESD_ERR_INVALID, "NULL solver");
+  ESD_CHECK(S->last_sample_m > 0, ESD_ERR_STATE, "the last solve did not sample iterates");
+  ESD_CHECK(!(theta <= 0.0), ESD_ERR_INVALID, "theta must be positive (or +inf)");
+  std::vector<int> slots;
+  for (int k = 0; k < S->last_sample_m; ++k)
+    if (S->hst->slot_iter[k] > 0) slots.push_back(k);
+  ESD_CHECK(!slots.empty(), ESD_ERR_RANK, "no iterate was sampled (the solve stopped too early)");
+  const int m = (int)slots.size();
+  S->aux.ensure(S->A->n, S->ld);
+  DevBuf dslots(sizeof(int) * m);
+  ESD_CUDA(cudaMemcpyAsync(dslots.get(), slots.data(), sizeof(int) * m, cudaMemcpyHostToDevice, S->stream));
+  k_errors<<<max_grid_blocks(), kBlock, 0, S->stream>>>(S->A->n, S->vx.as<double>(), S->samples.as<double>(),
+                                                        S->ld, dslots.as<int>(), m, S->aux.work1.as<double>());
+  ESD_CUDA(cudaGetLastError());
+  install_W(S, S->aux.work1.as<double>(), m, true, theta);
+  if (m_kept) *m_kept = S->m;
+  return ESD_OK;
+  ESD_API_END
+}
+
+int esd_set_W(esd_solver* S, const double* W, int32_t m) {
+  ESD_API_BEGIN
+  ESD_CHECK(S && W, ESD_ERR_INVALID, "NULL argument");
+  ESD_CHECK(m >= 1 && m <= kMaxM, ESD_ERR_INVALID, "m must be 1..64");
+  S->aux.ensure(S->A->n, S->ld);
+  const int n = S->A->n;
+  for (int j = 0; j < m; ++j)
+    copy_in(W + (size_t)j * n, S->aux.work1.as<double>() + (size_t)j * S->ld, sizeof(double) * n, S->stream);
+  install_W(S, S->aux.work1.as<double>(), m, false, std::numeric_limits<double>::infinity());
+  return ESD_OK;
+  ESD_API_END
+}
+
+int esd_get_W(esd_solver* S, double* W, double* AW, double* E, int32_t* m) {
+  ESD_API_BEGIN
+  ESD_CHECK(S, ESD_ERR_INVALID, "NULL solver");
+  ESD_CHECK(S->have_W, ESD_ERR_STATE, "no W");
+  const int n = S->A->n;
+  for (int j = 0; j < S->m; ++j) {
+    if (W) copy_out(S->W.as<double>() + (size_t)j * S->ld, W + (size_t)j * n, sizeof(double) * n, S->stream);
+    if (AW) copy_out(S->AW.as<double>() + (size_t)j * S->ld, AW + (size_t)j * n, sizeof(double) * n, S->stream);
+  }
+  if (E) copy_out(S->E.get(), E, sizeof(double) * S->m * S->m, S->stream);
+  ESD_CUDA(cudaStreamSynchronize(S->stream));
+  if (m) *m = S->m;
+  return ESD_OK;
+  ESD_API_END
+}
+
+int esd_ritz_values(esd_solver* S, double* out, int32_t cap, int32_t* count) {
+  ESD_API_BEGIN
+  ESD_CHECK(S && out, ESD_ERR_INVALID, "NULL argument");
+  ESD_CHECK(S->have_W, ESD_ERR_STATE, "no W");
+  const int k = std::min<int>(cap, S->m);
+  ESD_CUDA(cudaMemcpyAsync(out, S->ritz.get(), sizeof(double) * k, cudaMemcpyDeviceToHost, S->stream));
+  ESD_CUDA(cudaStreamSynchronize(S->stream));
+  if (count) *count = S->m;
+  return ESD_OK;
+  ESD_API_END
+}
+
+int esd_estimate_cond(esd_solver* S, double* lmin, double* lmax, double* kappa, double* ritz_min) {
+  ESD_API_BEGIN
+  ESD_CHECK(S, ESD_ERR_INVALID, "NULL solver");
+  ESD_CHECK(S->last_iters >= 1, ESD_ERR_STATE, "the last solve took no CG step");
+  k_lanczos_extremes<<<1, 256, 0, S->stream>>>(S->ahist.as<double>(), S->bhist.as<double>(), S->last_iters,
+                                               S->ext.as<double>());
+  ESD_CUDA(cudaGetLastError());
+  double h[2];
+  ESD_CUDA(cudaMemcpyAsync(h, S->ext.get(), sizeof(h), cudaMemcpyDeviceToHost, S->stream));
+  double r0 = std::numeric_limits<double>::quiet_NaN();
+  if (S->have_W) ESD_CUDA(cudaMemcpyAsync(&r0, S->ritz.get(), sizeof(double), cudaMemcpyDeviceToHost, S->stream));
+  ESD_CUDA(cudaStreamSynchronize(S->stream));
+  if (lmin) *lmin = h[0];
+  if (lmax) *lmax = h[1];
+  if (kappa) *kappa = h[1] / h[0];
+  if (ritz_min) *ritz_min = r0;
+  return ESD_OK;
+  ESD_API_END
+}
+
+int esd_get_history(esd_solver* S, double* alpha, double* beta, int32_t cap, int32_t* count) {
+  ESD_API_BEGIN
+  ESD_CHECK(S, ESD_ERR_INVALID, "NULL solver");
+  const int k = std::min<int>(cap, S->last_iters);
+  if (alpha && k > 0)
+    ESD_CUDA(cudaMemcpyAsync(alpha, S->ahist.get(), sizeof(double) * k, cudaMemcpyDeviceToHost, S->stream));
+  if (beta && k > 1)
+    ESD_CUDA(cudaMemcpyAsync(beta, S->bhist.get(), sizeof(double) * (k - 1), cudaMemcpyDeviceToHost, S->stream));
+  ESD_CUDA(cudaStreamSynchronize(S->stream));
+  if (count) *count = S->last_iters;
+  return ESD_OK;
+  ESD_API_END
+}
+
+int esd_get_samples(esd_solver* S, double* samples, int32_t* slot_iter, int32_t cap, int32_t* m) {
+  ESD_API_BEGIN
+  ESD_CHECK(S, ESD_ERR_INVALID, "NULL solver");
+  const int k = std::min<int>(cap, S->last_sample_m);
+  const int n = S->A->n;
+  for (int j = 0; j < k; ++j) {
+    if (slot_iter) slot_iter[j] = S->hst->slot_iter[j];
+    if (samples)
+      copy_out(S->samples.as<double>() + (size_t)j * S->ld, samples + (size_t)j * n, sizeof(double) * n, S->stream);
+  }
+  ESD_CUDA(cudaStreamSynchronize(S->stream));
+  if (m) *m = S->last_sample_m;
+  return ESD_OK;
+  ESD_API_END
+}
+
+int esd_backward_euler_rhs(esd_solver* S, const double* x_prev, const double* s, double inv_dt, double* b) {
+  ESD_API_BEGIN
+  ESD_CHECK(S && x_prev && s && b, ESD_ERR_INVALID, "NULL argument");
+  const int n = S->A->n;
+  cudaStream_t st = S->stream;
+  const bool dev = is_device_ptr(x_prev) && is_device_ptr(s) && is_device_ptr(b);
+  if (dev) {
+    launch_axpby(n, x_prev, inv_dt, s, b, st);
+  } else {
+    double* t0 = S->A->tmp.as<double>();
+    double* t1 = t0 + S->ld;
+    double* t2 = t1 + S->ld;
+    copy_in(x_prev, t0, sizeof(double) * n, st);
+    copy_in(s, t1, sizeof(double) * n, st);
+    launch_axpby(n, t0, inv_dt, t1, t2, st);
+    copy_out(t2, b, sizeof(double) * n, st);
+    ESD_CUDA(cudaStreamSynchronize(st));
+  }
+  return ESD_OK;
+  ESD_API_END
+}
+
+int esd_profile_iterations(esd_solver* S, const double* b, double* x, int32_t reps, double* ms, char* names,
+                           int32_t cap, int32_t* count) {
+  ESD_API_BEGIN
+  ESD_CHECK(S && b && x && ms && count, ESD_ERR_INVALID, "NULL argument");
+  ESD_CHECK(reps >= 1 && reps < S->prm.maxit_cap, ESD_ERR_INVALID, "reps must be 1..maxit_cap-1");
+  cudaStream_t s = S->stream;
+  const int n = S->A->n;
+  copy_in(b, S->vb.get(), sizeof(double) * n, s);
+  copy_in(x, S->vx.get(), sizeof(double) * n, s);
+  State* h = S->hst;
+  std::memset(h, 0, sizeof(State));
+  h->scal0 = 0.0;  // tolerance 0: the iterations run for reps steps
+  h->maxit = reps + 1;
+  h->h = 1;
+  h->pend_slot = -1;
+  ESD_CUDA(cudaMemcpyAsync(S->state.get(), h, sizeof(State), cudaMemcpyHostToDevice, s));
+  IterCtx<double> c = S->ctx(S->mode);
+  launch_init<double>(c, s);
+  std::vector<std::unique_ptr<KernelMarks>> marks;
+  for (int r = 0; r < reps; ++r) {
+    marks.emplace_back(new KernelMarks());
+    launch_iteration<double>(c, s, marks.back().get());
+  }
+  copy_out(S->vx.get(), x, sizeof(double) * n, s);
+  ESD_CUDA(cudaStreamSynchronize(s));
+  const int k = (int)marks[0]->ev.size() - 1;
+  *count = k;
+  for (int j = 0; j < std::min(k, (int)cap); ++j) {
+    double tot = 0.0;
+    for (auto& mk : marks) {
+      float t = 0.f;
+      ESD_CUDA(cudaEventElapsedTime(&t, mk->ev[j], mk->ev[j + 1]));
+      tot += t;
+    }
+    ms[j] = tot / reps;
+    if (names) {
+      std::strncpy(names + 32 * j, marks[0]->names[j + 1].c_str(), 31);
+      names[32 * j + 31] = 0;
+    }
+  }
+  return ESD_OK;
+  ESD_API_END
+}
+
+int esd_pattern_grad(esd_matrix* A, const double* lambda, const double* x, double* grad) {
+  ESD_API_BEGIN
+  ESD_CHECK(A && lambda && x && grad, ESD_ERR_INVALID, "NULL argument");
+  cudaStream_t s = A->stream;
+  double* t0 = A->tmp.as<double>();
+  double* t1 = t0 + A->vec_stride();
+  copy_in(lambda, t0, sizeof(double) * A->n, s);
+  copy_in(x, t1, sizeof(double) * A->n, s);
+  const bool dev = is_device_ptr(grad);
+  DevBuf tmp;
+  double* g = grad;
+  if (!dev) {
+    tmp.alloc(sizeof(double) * A->nnz);
+    g = tmp.as<double>();
+  }
+  k_pattern_grad<<<max_grid_blocks(), kBlock, 0, s>>>(A->n, A->csr_rowptr.as<int>(), A->csr_colind.as<int>(), t0,
+                                                      t1, g);
+  ESD_CUDA(cudaGetLastError());
+  if (!dev) copy_out(g, grad, sizeof(double) * A->nnz, s);
+  ESD_CUDA(cudaStreamSynchronize(s));
+  return ESD_OK;
+  ESD_API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,395 @@
+"""CUDA path against the CPU oracle, element by element, through the C ABI (GPU only).
+
+Layers, each compared on identical inputs:
+  kernels        SpMV and IC(0) application, 1e-13 / 1e-12 relative (summation order only);
+  iteration      alpha_j, beta_j of the first 10 iterations to 1e-11 (1e-9 without a
+                 preconditioner); iteration count +-1 and solution 1e-10 for the workloads'
+                 tolerance 1e-8, in plain, deflation and SC modes (the latter two with the
+                 oracle's own W);
+  sampling       the slot schedule bit-exact, the stored iterates 1e-10;
+  W              W, E and the Ritz values built from the same samples, 1e-10;
+  sequences      each side follows its own sequence: counts within max(1, 2%), true
+                 residuals below the tolerance, solutions within 1e-6.
+Why counts get an allowance once the trajectories are independent: after ~50 iterations
+two correct FP64 CG runs drift apart (the oracle itself moves by two iterations on a
+warm-started 64 x 64 system between an FMA and a non-FMA build), so a later count can
+differ by rounding alone when the residual plateaus near the tolerance.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2203_08498_gb300 as esd  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def close_slack(k_oracle):
+    """Allowed iteration difference once the two trajectories are independent."""
+    return max(1, int(math.ceil(0.02 * k_oracle)))
+
+
+def rel(a, b):
+    a = a.cpu().numpy() if hasattr(a, "cpu") else a
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+PROBLEMS = {
+    "c1_64x64_redblack": lambda: wl.config_c1(),
+    "fv7_9cube_ragged": lambda: wl.small_3d(9, seed=11),
+    "fv7_20cube": lambda: wl.small_3d(20, seed=12, count=3, rmin=2, rmax=3, value=1e4),
+    "lap1d_odd": lambda: wl.laplacian_1d(37),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(PROBLEMS))
+def problem(request):
+    return request.param, PROBLEMS[request.param]()
+
+
+def test_spmv_matches_oracle(problem):
+    name, p = problem
+    A = esd.Matrix.from_problem(p)
+    x = np.random.default_rng(1).standard_normal(p.n)
+    y = torch.empty(p.n, dtype=torch.float64, device=DEV)
+    A.spmv(dev(x), y)
+    ref = oracle.spmv(p, x)
+    assert rel(y, ref) <= 1e-13
+
+
+def test_spmv_host_pointers(problem):
+    name, p = problem
+    A = esd.Matrix.from_problem(p)
+    x = np.random.default_rng(2).standard_normal(p.n)
+    y = np.zeros(p.n)
+    A.spmv(x, y)
+    assert rel(y, oracle.spmv(p, x)) <= 1e-13
+
+
+def test_ic0_apply_matches_oracle(problem):
+    name, p = problem
+    A = esd.Matrix.from_problem(p)
+    shift = A.factor_ic0()
+    ic = oracle.IC0(p)
+    assert shift == ic.shift
+    r = np.random.default_rng(3).standard_normal(p.n)
+    z = torch.empty(p.n, dtype=torch.float64, device=DEV)
+    A.apply_ic(dev(r), z)
+    assert rel(z, ic.apply(r)) <= 1e-12
+
+
+def test_colour_levels_merge_independent_colours():
+    p = wl.small_3d(8, seed=1)
+    info = esd.Matrix.from_problem(p).info()
+    assert info["ncolours"] == 8 and info["fwd_levels"] == 4 and info["bwd_levels"] == 4
+    info = esd.Matrix.from_problem(wl.config_c1()).info()
+    assert info["fwd_levels"] == 2 and info["bwd_levels"] == 2
+
+
+@pytest.mark.parametrize("precond", [esd.PRECOND_IC0, esd.PRECOND_NONE])
+def test_single_solve_matches_oracle(problem, precond):
+    """Iterations +-1 and solution 1e-10 at the workloads' tolerance 1e-8, and the CG
+    coefficients alpha_j, beta_j equal to 1e-11 over the first 10 iterations. (Later
+    coefficients of two correct FP64 runs drift apart exponentially once the Lanczos
+    vectors lose orthogonality, whatever the summation order, so they are not compared.)"""
+    name, p = problem
+    A = esd.Matrix.from_problem(p)
+    if precond == esd.PRECOND_IC0:
+        A.factor_ic0()
+    S = esd.Solver(A, precond=precond, maxit_cap=5000, sample_cap=8)
+    b = p.source if p.source is not None else np.random.default_rng(4).uniform(size=p.n)
+    x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+    st, it, rr = S.solve(dev(b), x, tol=1e-8, maxit=5000)
+    ic = oracle.IC0(p) if precond == esd.PRECOND_IC0 else None
+    out = oracle.System(p, ic).solve(b, tol=1e-8, maxit=5000)
+    slack = 1 if precond == esd.PRECOND_IC0 else close_slack(out["iters"])
+    assert st == esd.OK and abs(it - out["iters"]) <= slack, (it, out["iters"])
+    assert rel(x, out["x"]) <= 1e-10
+    assert S.true_relres() <= 1.05e-8
+    a, bb = S.history()
+    assert len(a) == it and len(bb) == it - 1
+    k = min(it, out["iters"], 10)
+    rt = 1e-11 if precond == esd.PRECOND_IC0 else 1e-9
+    np.testing.assert_allclose(a[:k], out["alpha"][:k], rtol=rt)
+    np.testing.assert_allclose(bb[:k - 1], out["beta"][:k - 1], rtol=rt)
+
+
+def test_tight_tolerance_solution(problem):
+    """At tol 1e-12 both sides converge; the solutions agree within the conditioning."""
+    name, p = problem
+    A = esd.Matrix.from_problem(p)
+    A.factor_ic0()
+    S = esd.Solver(A, maxit_cap=5000)
+    b = p.source if p.source is not None else np.random.default_rng(4).uniform(size=p.n)
+    x = np.zeros(p.n)
+    st, it, rr = S.solve(b, x, tol=1e-12, maxit=5000)
+    out = oracle.System(p, oracle.IC0(p)).solve(b, tol=1e-12, maxit=5000)
+    assert st == esd.OK and S.true_relres() <= 5e-11
+    assert rel(x, out["x"]) <= 1e-10
+
+
+def test_sampling_slots_match_oracle():
+    p = wl.config_c1()
+    A = esd.Matrix.from_problem(p)
+    A.factor_ic0()
+    S = esd.Solver(A, sample_cap=8)
+    x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+    st, it, rr = S.solve(dev(p.source), x, tol=1e-8, sample_m=8)
+    samples, slot_iter = S.samples(8)
+    out = oracle.System(p, oracle.IC0(p)).solve(p.source, tol=1e-8, sample_m=8)
+    assert it == out["iters"]
+    assert slot_iter.tolist() == out["sample_iter"].tolist()
+    assert rel(samples, out["samples"]) <= 1e-10
+
+
+@pytest.fixture(scope="module")
+def c1_oracle_w():
+    """Oracle run of system 1 of the 64 x 64 sequence with m = 8 samples, its W, and the
+    right-hand side and warm start of system 2."""
+    p = wl.config_c1()
+    ic = oracle.IC0(p)
+    o1 = oracle.System(p, ic).solve(p.source, tol=1e-8, sample_m=8)
+    aux, info = oracle.build_w(p, o1["x"], o1["samples"], o1["sample_iter"])
+    b2 = o1["x"] / p.dt + p.source
+    return p, ic, aux, o1["x"], b2
+
+
+@pytest.mark.parametrize("mode", [esd.DEFLATION, esd.SUBSPACE_CORRECTION])
+def test_accelerated_solve_with_oracle_w(c1_oracle_w, mode):
+    """Deflated PCG (Algorithm DPCG) and SC-PCG (Eq. mc) with the oracle's W, on the
+    oracle's system 2 (same b, same warm start)."""
+    p, ic, aux, x1, b2 = c1_oracle_w
+    A = esd.Matrix.from_problem(p)
+    A.factor_ic0()
+    S = esd.Solver(A, sample_cap=0)
+    S.set_W(aux.W)
+    W, AW, E = S.get_W()
+    np.testing.assert_allclose(E, aux.E, rtol=1e-12, atol=1e-12 * np.abs(aux.E).max())
+    S.set_mode(mode)
+    x = dev(x1.copy())
+    st, it, rr = S.solve(dev(b2), x, tol=1e-8)
+    out = oracle.System(p, ic, mode, aux).solve(b2, x1, tol=1e-8)
+    assert st == esd.OK and abs(it - out["iters"]) <= 1, (it, out["iters"])
+    assert rel(x, out["x"]) <= 1e-10
+    assert S.true_relres() <= 1.05e-8
+    a, bb = S.history()
+    k = min(it, out["iters"], 10)
+    np.testing.assert_allclose(a[:k], out["alpha"][:k], rtol=1e-11)
+    np.testing.assert_allclose(bb[:k - 1], out["beta"][:k - 1], rtol=1e-11)
+
+
+def test_w_build_from_same_samples():
+    """Eq. ek / ekd / Rayleigh-Ritz on the GPU's own samples: W spans the oracle's W, E and
+    the Ritz values agree."""
+    p = wl.config_c1()
+    A = esd.Matrix.from_problem(p)
+    A.factor_ic0()
+    S = esd.Solver(A, sample_cap=8)
+    x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+    S.solve(dev(p.source), x, tol=1e-8, sample_m=8)
+    samples, slot_iter = S.samples(8)
+    m = S.sample_and_build_W()
+    W, AW, E = S.get_W()
+    aux, info = oracle.build_w(p, x.cpu().numpy(), samples, slot_iter)
+    assert m == aux.m == info["mbar"]
+    np.testing.assert_allclose(W.T @ W, np.eye(m), atol=1e-12)
+    assert np.linalg.norm(W @ (W.T @ aux.W) - aux.W) <= 1e-10 * np.linalg.norm(aux.W)
+    # CholeskyQR2 and Gram-Schmidt give the same Q (R with a positive diagonal)
+    assert rel(W, aux.W) <= 1e-10
+    np.testing.assert_allclose(AW, p.scipy() @ W, rtol=1e-12, atol=1e-12 * np.abs(AW).max())
+    np.testing.assert_allclose(E, aux.E, rtol=1e-10, atol=1e-10 * np.abs(aux.E).max())
+    np.testing.assert_allclose(np.sort(S.ritz_values()), np.sort(aux.ritz), rtol=1e-10)
+
+
+def test_theta_filter_keeps_small_ritz_vectors():
+    p = wl.config_c1()
+    A = esd.Matrix.from_problem(p)
+    A.factor_ic0()
+    S = esd.Solver(A, sample_cap=8)
+    x = np.zeros(p.n)
+    S.solve(p.source, x, tol=1e-8, sample_m=8)
+    samples, slot_iter = S.samples(8)
+    S.sample_and_build_W()
+    ritz = np.sort(S.ritz_values())
+    theta = 0.5 * (ritz[3] + ritz[4])
+    m = S.sample_and_build_W(theta)
+    assert m == 4
+    W, AW, E = S.get_W()
+    aux, info = oracle.build_w(p, x, samples, slot_iter, theta=theta)
+    np.testing.assert_allclose(np.diag(E), np.diag(aux.E), rtol=1e-10)
+    assert np.linalg.norm(W @ (W.T @ aux.W) - aux.W) <= 1e-8 * np.linalg.norm(aux.W)
+
+
+@pytest.mark.parametrize("mode", [esd.PLAIN, esd.DEFLATION, esd.SUBSPACE_CORRECTION])
+def test_c1_sequence_end_to_end(mode):
+    """The 64 x 64 sequence of 5 systems, W from m = 8 samples of system 1, each side on its
+    own trajectory."""
+    p = wl.config_c1()
+    A = esd.Matrix.from_problem(p)
+    A.factor_ic0()
+    S = esd.Solver(A, sample_cap=8)
+    src = dev(p.source)
+    x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+    b = torch.empty_like(x)
+    res_o, aux = oracle.run_sequence(p, 5, mode, 8)
+    plain_o, _ = oracle.run_sequence(p, 5, oracle.PLAIN, 8)
+    for t in range(5):
+        S.backward_euler_rhs(x, src, 1.0 / p.dt, b)
+        if t == 0:
+            S.set_mode(esd.PLAIN)
+            st, it, rr = S.solve(b, x, tol=1e-8, sample_m=8 if mode != esd.PLAIN else 0)
+            if mode != esd.PLAIN:
+                assert S.sample_and_build_W() == aux.m
+                np.testing.assert_allclose(np.sort(S.ritz_values()), np.sort(aux.ritz), rtol=1e-6)
+                S.set_mode(mode)
+        else:
+            st, it, rr = S.solve(b, x, tol=1e-8)
+            if mode != esd.PLAIN:
+                assert it < 0.7 * plain_o[t]["iters"]
+        k_o = res_o[t]["iters"]
+        assert st == esd.OK and abs(it - k_o) <= close_slack(k_o), (t, it, k_o)
+        assert S.true_relres() <= 1.05e-8
+        assert rel(x, res_o[t]["x"]) <= 1e-6, t
+
+
+def test_deflation_exact_eigenvectors_gpu():
+    """Section 4.1 on the GPU: deflating exact small eigenvectors (M = I) ends in <= k
+    iterations; the result solves A x = b."""
+    n, k = 64, 6
+    ev = np.concatenate([[1e-4, 3e-4, 7e-4, 1.5e-3], np.repeat(np.linspace(1, 50, k), (n - 4) // k)])
+    a = wl.random_spd_dense(ev, seed=7)
+    p = wl.csr_of_dense(a, ncolours=n)  # dense pattern: one row per colour
+    w, V = np.linalg.eigh(a)
+    A = esd.Matrix.from_problem(p)
+    S = esd.Solver(A, precond=esd.PRECOND_NONE, maxit_cap=500, sample_cap=0)
+    S.set_W(V[:, :4])
+    S.set_mode(esd.DEFLATION)
+    b = np.random.default_rng(1).standard_normal(n)
+    x = np.zeros(n)
+    st, it, rr = S.solve(b, x, tol=1e-10, maxit=500)
+    assert st == esd.OK and it <= k
+    assert np.linalg.norm(b - a @ x) <= 1.05e-10 * np.linalg.norm(b)
+    aux = oracle.Aux.from_basis(p, V[:, :4])
+    out = oracle.System(p, None, oracle.DEFLATION, aux).solve(b, tol=1e-10, maxit=500)
+    assert abs(out["iters"] - it) <= 1 and rel(x, out["x"]) <= 1e-10
+
+
+def test_lanczos_condition_estimate_closed_form():
+    n = 50
+    p = wl.laplacian_1d(n)
+    A = esd.Matrix.from_problem(p)
+    S = esd.Solver(A, precond=esd.PRECOND_NONE, maxit_cap=200, sample_cap=0)
+    b = np.random.default_rng(0).standard_normal(n)
+    x = np.zeros(n)
+    S.solve(b, x, tol=1e-14, maxit=200)
+    lmin, lmax, kappa, ritz = S.estimate_cond()
+    assert lmin == pytest.approx(2 - 2 * math.cos(math.pi / (n + 1)), rel=1e-8)
+    assert lmax == pytest.approx(2 - 2 * math.cos(n * math.pi / (n + 1)), rel=1e-8)
+    assert math.isnan(ritz)
+
+
+def test_condition_estimate_matches_oracle():
+    p = wl.config_c1()
+    A = esd.Matrix.from_problem(p)
+    A.factor_ic0()
+    S = esd.Solver(A)
+    x = np.zeros(p.n)
+    S.solve(p.source, x, tol=1e-8)
+    lmin, lmax, kappa, _ = S.estimate_cond()
+    out = oracle.System(p, oracle.IC0(p)).solve(p.source, tol=1e-8)
+    omin, omax, okappa = oracle.estimate_cond(out["alpha"], out["beta"])
+    assert lmin == pytest.approx(omin, rel=1e-6) and lmax == pytest.approx(omax, rel=1e-8)
+
+
+def test_zero_rhs_and_converged_start():
+    p = wl.small_3d(6, seed=0)
+    A = esd.Matrix.from_problem(p)
+    A.factor_ic0()
+    S = esd.Solver(A)
+    x = np.ones(p.n)
+    st, it, rr = S.solve(np.zeros(p.n), x, tol=1e-8)
+    assert st == esd.OK and it == 0 and np.all(x == 0)
+    x_ref = oracle.System(p, oracle.IC0(p)).solve(p.source, tol=1e-14)["x"]
+    x = x_ref.copy()
+    st, it, rr = S.solve(p.source, x, tol=1e-8)
+    assert it == 0 and np.array_equal(x, x_ref)
+
+
+def test_maxit_reports_status_and_last_iterate():
+    p = wl.config_c1()
+    A = esd.Matrix.from_problem(p)
+    A.factor_ic0()
+    S = esd.Solver(A, maxit_cap=100)
+    x = np.zeros(p.n)
+    st, it, rr = S.solve(p.source, x, tol=1e-12, maxit=7)
+    assert st == esd.ERR_MAXIT and it == 7
+    out = oracle.System(p, oracle.IC0(p)).solve(p.source, tol=1e-12, maxit=7)
+    assert rel(x, out["x"]) <= 1e-12
+
+
+def test_invalid_inputs_are_rejected():
+    p = wl.small_3d(5, seed=0)
+    # columns out of order
+    ci = p.colind.copy()
+    r0, r1 = p.rowptr[3], p.rowptr[4]
+    ci[r0:r1] = ci[r0:r1][::-1]
+    with pytest.raises(esd.EsdError) as e:
+        esd.Matrix(p.rowptr, ci, p.val, p.colour_ptr)
+    assert e.value.code == esd.ERR_INVALID
+    # two coupled rows in one colour
+    with pytest.raises(esd.EsdError):
+        esd.Matrix(p.rowptr, p.colind, p.val, np.array([0, p.n], np.int32))
+    # sampling in deflation mode
+    A = esd.Matrix.from_problem(p)
+    A.factor_ic0()
+    S = esd.Solver(A, sample_cap=4)
+    with pytest.raises(esd.EsdError):
+        S.set_mode(esd.DEFLATION)
+
+
+def test_not_spd_factor_reports_error():
+    a = np.array([[1.0, 2.0], [2.0, 1.0]])  # indefinite, IC(0) fails for every small shift
+    p = wl.csr_of_dense(a, ncolours=2)
+    A = esd.Matrix(p.rowptr, p.colind, p.val, p.colour_ptr)
+    with pytest.raises(esd.EsdError) as e:
+        A.factor_ic0(max_tries=3)
+    assert e.value.code == esd.ERR_NOT_SPD
+
+
+@pytest.mark.slow
+def test_full_size_128cube_kernels_and_first_solve():
+    """The 128^3 7-point workload (2.1M rows) in the launch configuration the benchmark
+    uses: SpMV and IC(0) application on every row, and the first ICCG solve of the
+    sequence against the oracle (iterations +-1, solution 1e-10)."""
+    p = wl.config_c2()
+    A = esd.Matrix.from_problem(p)
+    A.factor_ic0()
+    rng = np.random.default_rng(9)
+    v = rng.standard_normal(p.n)
+    y = torch.empty(p.n, dtype=torch.float64, device=DEV)
+    A.spmv(dev(v), y)
+    assert rel(y, oracle.spmv(p, v)) <= 1e-13
+    ic = oracle.IC0(p)
+    A.apply_ic(dev(v), y)
+    assert rel(y, ic.apply(v)) <= 1e-12
+    S = esd.Solver(A, sample_cap=16)
+    b = dev(p.source / 1.0)
+    x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+    st, it, rr = S.solve(b, x, tol=1e-8, sample_m=16)
+    out = oracle.System(p, ic).solve(p.source, tol=1e-8, sample_m=16)
+    assert st == esd.OK and abs(it - out["iters"]) <= 1
+    assert rel(x, out["x"]) <= 1e-10

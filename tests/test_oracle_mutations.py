@@ -60,7 +60,7 @@ def mutant(tmp_path, monkeypatch):
         src = tmp_path / f"{name}.c"
         src.write_text(SRC.replace(old, new))
         so = tmp_path / f"{name}.so"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", str(so), str(src), "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", str(so), str(src), "-lm"])
         monkeypatch.setattr(oracle, "_lib", oracle.load(str(so)))
     return make
 
