@@ -1,0 +1,58 @@
+"""Per-kernel timing of one PCG iteration, outside any CUDA graph (for ncu and for users).
+
+python -m paper_2203_08498_gb300.profile --grid 96 --mode deflation --m 16 --reps 5
+
+Builds the heterogeneous-diffusion matrix of the given grid, factors it, installs an
+orthonormal W of m columns (random, seeded: the per-iteration cost does not depend on W's
+values) and runs reps iterations with esd_profile_iterations, which launches each kernel of
+the iteration body directly on the stream with CUDA events between them. Prints one JSON
+line with the average milliseconds per kernel.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+import numpy as np
+
+
+def main(argv=None):
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import torch
+
+    import paper_2203_08498_gb300 as esd
+    import workloads as wl
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--grid", type=int, default=96)
+    ap.add_argument("--mode", default="deflation", choices=["plain", "deflation", "sc"])
+    ap.add_argument("--m", type=int, default=16)
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--precond", default="ic0", choices=["ic0", "none"])
+    a = ap.parse_args(argv)
+    r = a.grid / 128.0
+    p = wl.config_c2(N=a.grid, rmin=4 * r, rmax=8 * r)
+    dev = torch.device("cuda:0")
+    A = esd.Matrix.from_problem(p)
+    pre = esd.PRECOND_IC0 if a.precond == "ic0" else esd.PRECOND_NONE
+    if pre == esd.PRECOND_IC0:
+        A.factor_ic0()
+    S = esd.Solver(A, precond=pre, maxit_cap=a.reps + 10, sample_cap=0)
+    mode = {"plain": esd.PLAIN, "deflation": esd.DEFLATION, "sc": esd.SUBSPACE_CORRECTION}[a.mode]
+    if mode != esd.PLAIN:
+        W, _ = np.linalg.qr(np.random.default_rng(0).standard_normal((p.n, a.m)))
+        S.set_W(np.asfortranarray(W))
+    S.set_mode(mode)
+    b = torch.from_numpy(p.source).to(dev)
+    x = torch.zeros(p.n, dtype=torch.float64, device=dev)
+    prof = S.profile_iterations(b, x, reps=a.reps)
+    print(json.dumps({"grid": a.grid, "n": p.n, "nnz": p.nnz, "mode": a.mode, "m": a.m,
+                      "kernels_ms": prof}), flush=True)
+
+
+if __name__ == "__main__":
+    main()
