@@ -212,6 +212,28 @@ int esd_get_samples(esd_solver* S, double* samples, int32_t* slot_iter, int32_t 
 int esd_profile_iterations(esd_solver* S, const double* b, double* x, int32_t reps, double* ms,
                            char* names, int32_t cap, int32_t* count);
 
+/*
+ * Condition estimate that allocates no device memory. The paper has no counterpart: it exists
+ * for callers that cannot call cudaMalloc, for example code whose whole device memory has
+ * been handed to another allocator, or a time-stepping loop that must not block on the
+ * implicit device synchronisation an allocation can cause. It returns what esd_estimate_cond
+ * returns (without the Ritz value), from CG coefficients the caller supplies.
+ *   alpha  device array of k doubles, beta device array of k-1 doubles (as esd_get_history
+ *          returns them; beta may be NULL when k = 1)
+ *   k      1 .. ESD_NOALLOC_MAX_K; a larger k returns ESD_ERR_INVALID before any launch
+ *   out    device array of 3 doubles: lambda_min, lambda_max, kappa
+ *   stream cudaStream_t of the launch (0 = legacy default stream); the call does not wait
+ * Scratch: a file-scope device array of 2 * ESD_NOALLOC_MAX_K doubles (512 KB), which every
+ * GPU that loads the library holds until the process exits. The first call on a device, with
+ * that device current, looks up the array's device address; make that first call before any
+ * stream capture. All calls share the array, so calls that overlap on the GPU (unordered
+ * streams) race; order them on one stream. Nothing needs clearing: each call writes the k
+ * entries it reads.
+ */
+#define ESD_NOALLOC_MAX_K 32768
+int esd_lanczos_extremes_noalloc(const double* alpha, const double* beta, int32_t k, double* out,
+                                 void* stream);
+
 /* b = x_prev * inv_dt + s, the backward-Euler right-hand side of the next system. */
 int esd_backward_euler_rhs(esd_solver* S, const double* x_prev, const double* s, double inv_dt,
                            double* b);

@@ -27,7 +27,9 @@ __all__ = [
     "esd_solver_destroy", "esd_set_mode", "esd_solve", "esd_true_relres", "esd_sample_and_build_W",
     "esd_set_W", "esd_get_W", "esd_ritz_values", "esd_estimate_cond", "esd_get_history",
     "esd_get_samples", "esd_backward_euler_rhs", "esd_profile_iterations", "esd_last_error",
+    "esd_lanczos_extremes_noalloc", "NOALLOC_MAX_K",
 ]
+NOALLOC_MAX_K = 32768
 
 OK, ERR_INVALID, ERR_NOT_SPD, ERR_BREAKDOWN, ERR_MAXIT, ERR_STATE, ERR_RANK, ERR_CHOL_E, ERR_CUDA, ERR_NOMEM = (
     0, -1, -2, -3, -4, -5, -6, -7, -8, -9)
@@ -97,6 +99,7 @@ def lib(build_if_missing: bool = True):
             "esd_get_samples": (i32, [vp, vp, vp, i32, P(i32)]),
             "esd_backward_euler_rhs": (i32, [vp, vp, vp, f64, vp]),
             "esd_profile_iterations": (i32, [vp, vp, vp, i32, vp, vp, i32, P(i32)]),
+            "esd_lanczos_extremes_noalloc": (i32, [vp, vp, i32, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -296,6 +299,13 @@ def esd_profile_iterations(h, b, x, reps, cap=64):
     k = min(cnt.value, cap)
     raw = names.raw
     return [(raw[32 * j: 32 * j + 32].split(b"\0")[0].decode(), float(ms[j])) for j in range(k)]
+
+
+def esd_lanczos_extremes_noalloc(alpha, beta, k, out, stream=None):
+    """Condition estimate from caller-owned device arrays, allocating nothing (for callers
+    that cannot call cudaMalloc). out: device array of 3 doubles (lmin, lmax, kappa)."""
+    st = current_stream() if stream is None else stream
+    _check(lib().esd_lanczos_extremes_noalloc(_ptr(alpha), _ptr(beta), k, _ptr(out), C.c_void_p(st)))
 
 
 # ---------------------------------------------------------------- handle owners
