@@ -15,7 +15,7 @@
 #include <stdexcept>
 #include <string>
 
-#include "../../include/esdcg.h"
+#include "esdcg.h"
 
 namespace esd {
 
@@ -145,34 +145,49 @@ __device__ __forceinline__ int warp_sum_index(int lane) {
   return idx;
 }
 
-__host__ __device__ constexpr int pow2_ceil(int x) { return x <= 1 ? 1 : (x <= 2 ? 2 : (x <= 4 ? 4 : (x <= 8 ? 8 : (x <= 16 ? 16 : 32)))); }
+__host__ __device__ constexpr int pow2_floor(int x) {
+  return x >= 32 ? 32 : (x >= 16 ? 16 : (x >= 8 ? 8 : (x >= 4 ? 4 : (x >= 2 ? 2 : 1))));
+}
 
-// Block-wide sum of R values per thread (R <= 64). The block totals end up in red[0..R).
-// red must hold 32 * (blockDim/32) ... at least (blockDim/32) * R entries of shared memory.
+// Warp totals of in[C0 .. R) in exact power-of-two chunks (17 values = 16 + 1), written by
+// one lane per value into red[warp * R + j].
+template <int C0, int R, typename T>
+__device__ __forceinline__ void warp_sum_chunks(const T (&in)[R], T* red, int lane, int warp) {
+  if constexpr (C0 < R) {
+    constexpr int C = pow2_floor(R - C0);
+    T v[C];
+#pragma unroll
+    for (int k = 0; k < C; ++k) v[k] = in[C0 + k];
+    warp_sum_multi<C>(v);
+    const int idx = warp_sum_index<C>(lane);
+    if ((lane & ((32 / C) - 1)) == 0) red[warp * R + C0 + idx] = v[0];
+    warp_sum_chunks<C0 + C, R>(in, red, lane, warp);
+  }
+}
+
+// Block-wide sum of R values per thread (R <= 64) with one block barrier: a butterfly per
+// warp, then warp 0 adds the warp totals. On return red[0..R) holds the totals, visible to
+// warp 0 (and to every thread when R > 32). red needs (blockDim/32 + 1) * R entries.
 template <int R, typename T>
 __device__ __forceinline__ void block_sum_multi(const T (&in)[R], T* red) {
-  constexpr int C = R > 32 ? 32 : R;  // chunk size
-  constexpr int P = pow2_ceil(C);
   const int lane = lane_id(), warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-#pragma unroll
-  for (int c0 = 0; c0 < R; c0 += C) {
-    T v[P];
-#pragma unroll
-    for (int k = 0; k < P; ++k) v[k] = (k < C && c0 + k < R) ? in[c0 + k] : T(0);
-    warp_sum_multi<P>(v);
-    const int idx = warp_sum_index<P>(lane);
-    // lanes holding the same index carry the same total; the lowest such lane writes it
-    if (idx < C && c0 + idx < R && (lane & ((32 / P) - 1)) == 0) red[warp * R + c0 + idx] = v[0];
+  warp_sum_chunks<0, R>(in, red, lane, warp);
+  __syncthreads();
+  if (warp == 0) {
+    for (int j = lane; j < R; j += 32) {
+      T s = 0;
+      for (int w = 0; w < nwarp; ++w) s += red[w * R + j];
+      red[j] = s;
+    }
+    __syncwarp();
   }
-  __syncthreads();
-  if (threadIdx.x < R) {
-    T s = 0;
-    for (int w = 0; w < nwarp; ++w) s += red[w * R + threadIdx.x];
-    red[(nwarp)*R + threadIdx.x] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x < R) red[threadIdx.x] = red[nwarp * R + threadIdx.x];
-  __syncthreads();
+  if (R > 32) __syncthreads();
+}
+
+// Shared-memory entries block_sum_multi<R> needs for kBlock threads.
+template <int R>
+__host__ __device__ constexpr int red_size() {
+  return (kBlock / 32 + 1) * R;
 }
 
 // Grid-wide deterministic sum: every block stores its R block totals into
@@ -184,8 +199,10 @@ __device__ __forceinline__ bool grid_sum_multi(const T (&in)[R], T* red, T* part
   __shared__ bool s_last;
   block_sum_multi<R>(in, red);
   const int G = gridDim.x;
-  if (threadIdx.x < R) partials[threadIdx.x * G + blockIdx.x] = red[threadIdx.x];
-  __threadfence();
+  if (threadIdx.x < R) {
+    partials[threadIdx.x * G + blockIdx.x] = red[threadIdx.x];
+    __threadfence();
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned t = atomicAdd(ticket, 1u);
@@ -204,6 +221,13 @@ __device__ __forceinline__ bool grid_sum_multi(const T (&in)[R], T* red, T* part
   block_sum_multi<R>(acc, red);
   if (threadIdx.x == 0) *ticket = 0u;  // ready for the next launch
   return true;
+}
+
+// Programmatic dependent launch: wait for the grids this one depends on (their memory is
+// visible afterwards), then let the grids that depend on this one be scheduled.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // u = Einv f for the small dense (padded) M x M inverse stored row-major; one warp.

@@ -2,19 +2,27 @@
 // sequences that form a solve. Instantiated for double (esd_iter_f64.cu) and float
 // (esd_iter_f32.cu).
 //
-// Iteration i (plain IC(0) mode, 7-point stencil with 8 colours => 4 forward / 4 backward
-// colour levels), one launch per line:
+// Iteration i (IC(0), 7-point stencil with 8 colours => forward levels {0}{1,2,4}{3,5,6}{7},
+// backward levels {7}{3,5,6}{1,2,4}{0}), one launch per line:
 //   spmv_pq   q = A p, (p, q)                 [+ h = (AW)^T p, y = E^-1 h, deflation]
 //   update    x += a p, r -= a q, ||r||^2, y = r/l_ii on forward level 0
 //             [deflation: r -= a (q - AW y); SC: f = W^T r, u = E^-1 f]
 //   fwd l     y_i = (r_i - sum_k l_ik y_k)/l_ii for the rows of level l, sum y_i^2
 //             (rows without later neighbours store z_i = y_i/l_ii at once)
 //   bwd l     z_i = (y_i - sum_j l_ji z_j)/l_ii, p_i = z_i [+ (W u)_i] + beta p_i
-// rho = (r, M^-1 r) is accumulated as sum y_i^2 (= ||L^-1 r||^2) during the forward
-// sweep, so beta is known before the backward sweep and p is updated in place by it.
-// Scalars never leave the device: the last block of every reduction computes alpha, beta,
-// the convergence test and the sampling decision, and ends the graph's while loop.
+// rho = (r, M^-1 r) is accumulated as sum y_i^2 (= ||L^-1 r||^2) during the forward sweep,
+// so beta is known before the backward sweep and p is updated in place by it. The
+// strict factors are stored negated, so each substitution is one FMA chain started at r_i.
+// Scalars never leave the device: the last block of a reduction computes alpha, beta, the
+// convergence test and the sampling decision, and ends the graph's while loop. Every
+// kernel is launched with programmatic stream serialisation: it waits for its predecessor
+// at entry (griddepcontrol) and lets its successor be scheduled at once, which hides the
+// launch and the tail of each grid behind its neighbour.
 #pragma once
+
+#include <mutex>
+#include <unordered_map>
+#include <utility>
 
 #include "esd_iter.h"
 
@@ -22,15 +30,22 @@ namespace esd {
 
 enum { kModePlain = ESD_PLAIN, kModeDefl = ESD_DEFLATION, kModeSC = ESD_SUBSPACE_CORRECTION };
 
+// Resident blocks per SM requested from the compiler for the slice kernels without W terms
+// (4 caps them at 32 registers per thread).
+#ifndef ESD_SWEEP_MINB
+#define ESD_SWEEP_MINB 4
+#endif
+
 template <typename T>
 __device__ __forceinline__ T ld_stream(const T* p) { return __ldcs(p); }
 
-// sum_k val[s,k,lane] * v[col[s,k,lane]] for the row of this lane in slice md
+// init + sum_k val[s,k,lane] * v[col[s,k,lane]] for the row of this lane in slice md
 template <typename T>
-__device__ __forceinline__ T row_dot(const SellView<T>& M, const int4& md, int lane, const T* __restrict__ v) {
+__device__ __forceinline__ T row_fma(const SellView<T>& M, const int4& md, int lane, const T* __restrict__ v,
+                                     T init) {
   const int* cp = M.col + md.x + lane;
   const T* vp = M.val + md.x + lane;
-  T acc = T(0);
+  T acc = init;
 #pragma unroll 4
   for (int k = 0; k < md.y; ++k) acc = fma(ld_stream(vp + k * kSlice), v[ld_stream(cp + k * kSlice)], acc);
   return acc;
@@ -78,47 +93,93 @@ __device__ __forceinline__ void sampling_a(State* st) {
   const int nw = (gridDim.x * blockDim.x) >> 5;                          \
   for (int g = gw; g < (set).total(); g += nw)
 
+// ------------------------------------------------------------------ launch helpers
+
+// Blocks of this kernel that fit on the whole GPU at once (one wave), cached per kernel.
+inline int wave_blocks(const void* kernel) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(kernel);
+  if (it != cache.end()) return it->second;
+  int per_sm = 0;
+  ESD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0));
+  const int w = std::max(1, std::min(per_sm, 4)) * (max_grid_blocks() / 4);
+  cache[kernel] = w;
+  return w;
+}
+
+template <typename... KArgs>
+inline int grid_for(void (*kernel)(KArgs...), int slices) {
+  const int need = (slices * kSlice + kBlock - 1) / kBlock;
+  return std::max(1, std::min(need, wave_blocks((const void*)kernel)));
+}
+
+// Launch with programmatic stream serialisation on (see the file comment).
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), int blocks, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(kBlock);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  ESD_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+}
+
+// Forward launches whose y_i^2 block totals the last forward launch adds up.
+struct RhoSlots {
+  int n;
+  int G[kMaxRanges];
+};
+
 // ------------------------------------------------------------------ plain kernels
 
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_spmv(SellView<T> A, SliceSet set, const T* __restrict__ x,
+__global__ void __launch_bounds__(kBlock, 4) k_spmv(SellView<T> A, SliceSet set, const T* __restrict__ x,
                                                  T* __restrict__ y) {
+  pdl_enter();
   ESD_LOOP_SLICES(set) {
     int r;
     const int s = set.slice(g, &r);
     const int4 md = A.meta[s];
-    const T acc = row_dot(A, md, lane, x);
+    const T acc = row_fma(A, md, lane, x, T(0));
     if (lane < md.w) y[md.z + lane] = acc;
   }
 }
 
+// y_i = (r_i - sum_k l_ik y_k) / l_ii with the negated factor entries
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_fwd_plain(SellView<T> L, SliceSet set, const T* __restrict__ r,
+__global__ void __launch_bounds__(kBlock, 4) k_fwd_plain(SellView<T> L, SliceSet set, const T* __restrict__ r,
                                                       T* y, const T* __restrict__ inv_d) {
+  pdl_enter();
   ESD_LOOP_SLICES(set) {
     int rr;
     const int s = set.slice(g, &rr);
     const int4 md = L.meta[s];
-    const T sum = row_dot(L, md, lane, y);
-    if (lane < md.w) {
-      const int i = md.z + lane;
-      y[i] = (r[i] - sum) * inv_d[i];
-    }
+    const int i = md.z + lane;
+    const bool valid = lane < md.w;
+    const T acc = row_fma(L, md, lane, y, valid ? r[i] : T(0));
+    if (valid) y[i] = acc * inv_d[i];
   }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_bwd_plain(SellView<T> U, SliceSet set, const T* __restrict__ y,
+__global__ void __launch_bounds__(kBlock, 4) k_bwd_plain(SellView<T> U, SliceSet set, const T* __restrict__ y,
                                                       T* z, const T* __restrict__ inv_d) {
+  pdl_enter();
   ESD_LOOP_SLICES(set) {
     int rr;
     const int s = set.slice(g, &rr);
     const int4 md = U.meta[s];
-    const T sum = row_dot(U, md, lane, z);
-    if (lane < md.w) {
-      const int i = md.z + lane;
-      z[i] = (y[i] - sum) * inv_d[i];
-    }
+    const int i = md.z + lane;
+    const bool valid = lane < md.w;
+    const T acc = row_fma(U, md, lane, z, valid ? y[i] : T(0));
+    if (valid) z[i] = acc * inv_d[i];
   }
 }
 
@@ -127,10 +188,11 @@ __global__ void __launch_bounds__(kBlock) k_bwd_plain(SellView<T> U, SliceSet se
 // q = A p, pq = (p, q); deflation: h = (AW)^T p, y = E^-1 h, (p, P^T A p) = pq - h^T y.
 // Last block: alpha = rho / (p, P^T A p).
 template <typename T, int M>
-__global__ void __launch_bounds__(kBlock) k_spmv_pq(IterCtx<T> c, SliceSet set) {
+__global__ void __launch_bounds__(kBlock, M == 0 ? ESD_SWEEP_MINB : (M <= 16 ? 2 : 1)) k_spmv_pq(IterCtx<T> c, SliceSet set) {
   constexpr int R = 1 + M;
-  __shared__ T red[(kBlock / 32 + 1) * R];
+  __shared__ T red[red_size<R>()];
   __shared__ double hy_s;
+  pdl_enter();
   State* st = c.st;
   // Independent of every reduction: a loop body that starts more than maxit + 2 times ends
   // the loop, so no failure of the scalar bookkeeping can keep the while node running.
@@ -149,7 +211,7 @@ __global__ void __launch_bounds__(kBlock) k_spmv_pq(IterCtx<T> c, SliceSet set) 
     int r;
     const int s = set.slice(g, &r);
     const int4 md = c.Av.meta[s];
-    const T qi = row_dot(c.Av, md, lane, c.p);
+    const T qi = row_fma(c.Av, md, lane, c.p, T(0));
     if (lane < md.w) {
       const int i = md.z + lane;
       const T pi = c.p[i];
@@ -197,14 +259,15 @@ __global__ void __launch_bounds__(kBlock) k_spmv_pq(IterCtx<T> c, SliceSet set) 
 // sample of the previous iteration; SC: f = W^T r; forward level 0 (y = r / l_ii).
 // do_update = 0 runs the same epilogue on r0 (start of a solve).
 template <typename T, int M, int MODE, int PRE>
-__global__ void __launch_bounds__(kBlock) k_update(IterCtx<T> c, SliceSet set, int do_update,
-                                                   int finalize) {
+__global__ void __launch_bounds__(kBlock, M == 0 ? 4 : 1) k_update(IterCtx<T> c, SliceSet set, int do_update,
+                                                                  int finalize) {
   constexpr int SCM = (MODE == kModeSC) ? M : 0;
   constexpr int DM = (MODE == kModeDefl) ? M : 0;
   constexpr int R = 2 + SCM;
-  __shared__ T red[(kBlock / 32 + 1) * R];
+  __shared__ T red[red_size<R>()];
   __shared__ double ys[DM > 0 ? DM : 1];
   __shared__ double fu_s;
+  pdl_enter();
   State* st = c.st;
   if (st->conv) return;
   const T alpha = (T)st->alpha;
@@ -296,10 +359,14 @@ __global__ void __launch_bounds__(kBlock) k_update(IterCtx<T> c, SliceSet set, i
   }
 }
 
-// One forward colour level: y_i = (r_i - sum_k l_ik y_k) / l_ii; rho += y_i^2.
+// One forward colour level: y_i = (r_i - sum_k l_ik y_k) / l_ii and sum y_i^2. A launch that
+// is not the last stores its block totals in rho slot `slot`; the last launch adds its own
+// sum, the slots of the earlier launches and the level-0 part of the update, then sets beta.
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_fwd(IterCtx<T> c, SliceSet set, int last) {
-  __shared__ T red[(kBlock / 32 + 1)];
+__global__ void __launch_bounds__(kBlock, ESD_SWEEP_MINB) k_fwd(IterCtx<T> c, SliceSet set, int slot, RhoSlots prev) {
+  __shared__ T red[red_size<1>()];
+  __shared__ double own_s;
+  pdl_enter();
   State* st = c.st;
   if (st->conv) return;
   T acc[1] = {T(0)};
@@ -307,20 +374,34 @@ __global__ void __launch_bounds__(kBlock) k_fwd(IterCtx<T> c, SliceSet set, int 
     int r;
     const int s = set.slice(g, &r);
     const int4 md = c.Lv.meta[s];
-    const T sum = row_dot(c.Lv, md, lane, c.Y);
-    if (lane < md.w) {
-      const int i = md.z + lane;
-      const T d = c.inv_d[i];
-      const T yv = (c.r[i] - sum) * d;
+    const int i = md.z + lane;
+    const bool valid = lane < md.w;
+    const T d = valid ? c.inv_d[i] : T(0);
+    const T raw = row_fma(c.Lv, md, lane, c.Y, valid ? c.r[i] : T(0));
+    if (valid) {
+      const T yv = raw * d;
       acc[0] = fma(yv, yv, acc[0]);
       c.Y[i] = ((set.bwd0 >> r) & 1u) ? yv * d : yv;
     }
   }
+  T* slots = (T*)c.rho_part;
+  if (slot >= 0) {
+    block_sum_multi<1>(acc, red);
+    if (threadIdx.x == 0) slots[(size_t)slot * c.rho_stride + blockIdx.x] = red[0];
+    return;
+  }
   if (grid_sum_multi<1>(acc, red, (T*)c.partials, &st->ticket[kTkSweep])) {
-    if (threadIdx.x == 0) {
-      st->rho_acc += (double)red[0];
-      if (last) finalize_rho(st, st->rho_acc + st->fu, c.bhist, c.cond);
+    if (threadIdx.x == 0) own_s = (double)red[0];
+    T acc2[1] = {T(0)};
+#pragma unroll
+    for (int k = 0; k < kMaxRanges; ++k) {
+      if (k < prev.n) {
+        for (int b = threadIdx.x; b < prev.G[k]; b += blockDim.x)
+          acc2[0] += __ldcg(&slots[(size_t)k * c.rho_stride + b]);
+      }
     }
+    block_sum_multi<1>(acc2, red);
+    if (threadIdx.x == 0) finalize_rho(st, own_s + (double)red[0] + st->rho_acc + st->fu, c.bhist, c.cond);
   }
 }
 
@@ -328,8 +409,9 @@ __global__ void __launch_bounds__(kBlock) k_fwd(IterCtx<T> c, SliceSet set, int 
 // p_i = z_i [+ (W u)_i] + beta p_i. "elem" rows had z_i stored by the forward sweep and
 // only take the direction update.
 template <typename T, int SCM>
-__global__ void __launch_bounds__(kBlock) k_bwd(IterCtx<T> c, SliceSet set, SliceSet elem) {
+__global__ void __launch_bounds__(kBlock, SCM == 0 ? ESD_SWEEP_MINB : 1) k_bwd(IterCtx<T> c, SliceSet set, SliceSet elem) {
   __shared__ double us[SCM > 0 ? SCM : 1];
+  pdl_enter();
   State* st = c.st;
   if (st->conv) return;
   const T beta = (T)st->beta;
@@ -347,32 +429,29 @@ __global__ void __launch_bounds__(kBlock) k_bwd(IterCtx<T> c, SliceSet set, Slic
     int r;
     const bool sweep = g < nsweep;
     const int s = sweep ? set.slice(g, &r) : elem.slice(g - nsweep, &r);
-    const int4 md = sweep ? c.Uv.meta[s] : c.Av.meta[s];
-    T zic = T(0);
-    if (sweep) {
-      const T sum = row_dot(c.Uv, md, lane, c.Y);
-      if (lane < md.w) {
-        const int i = md.z + lane;
-        zic = (c.Y[i] - sum) * c.inv_d[i];
-        c.Y[i] = zic;
-      }
-    } else if (lane < md.w) {
-      zic = c.Y[md.z + lane];
-    }
-    if (lane < md.w) {
-      const int i = md.z + lane;
+    int4 md = c.Uv.meta[s];
+    if (!sweep) md.y = 0;  // rows whose z_i the forward sweep stored: no substitution
+    const int i = md.z + lane;
+    const bool valid = lane < md.w;
+    const T d = (valid && sweep) ? c.inv_d[i] : T(1);
+    const T pold = (valid && !first) ? c.p[i] : T(0);
+    const T raw = row_fma(c.Uv, md, lane, c.Y, valid ? c.Y[i] : T(0));
+    if (valid) {
+      const T zic = sweep ? raw * d : raw;
+      if (sweep) c.Y[i] = zic;
       T z = zic;
 #pragma unroll
       for (int k = 0; k < SCM; ++k) z = fma(c.W[k * c.ld + i], (T)us[k], z);
-      c.p[i] = first ? z : fma(beta, c.p[i], z);
+      c.p[i] = first ? z : fma(beta, pold, z);
     }
   }
 }
 
 // No preconditioner: p = r [+ W u] + beta p.
 template <typename T, int SCM>
-__global__ void __launch_bounds__(kBlock) k_dir(IterCtx<T> c, SliceSet set) {
+__global__ void __launch_bounds__(kBlock, SCM == 0 ? 4 : 1) k_dir(IterCtx<T> c, SliceSet set) {
   __shared__ double us[SCM > 0 ? SCM : 1];
+  pdl_enter();
   State* st = c.st;
   if (st->conv) return;
   const T beta = (T)st->beta;
@@ -397,15 +476,16 @@ __global__ void __launch_bounds__(kBlock) k_dir(IterCtx<T> c, SliceSet set) {
 
 // r = b - A x, ||b||^2, ||r||^2 (start of a solve).
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_residual0(IterCtx<T> c, SliceSet set) {
-  __shared__ T red[(kBlock / 32 + 1) * 2];
+__global__ void __launch_bounds__(kBlock, 4) k_residual0(IterCtx<T> c, SliceSet set) {
+  __shared__ T red[red_size<2>()];
+  pdl_enter();
   State* st = c.st;
   T acc[2] = {T(0), T(0)};
   ESD_LOOP_SLICES(set) {
     int r;
     const int s = set.slice(g, &r);
     const int4 md = c.Av.meta[s];
-    const T ax = row_dot(c.Av, md, lane, c.x);
+    const T ax = row_fma(c.Av, md, lane, c.x, T(0));
     if (lane < md.w) {
       const int i = md.z + lane;
       const T bi = c.b[i];
@@ -430,7 +510,8 @@ __global__ void __launch_bounds__(kBlock) k_residual0(IterCtx<T> c, SliceSet set
 template <typename T, int M>
 __global__ void __launch_bounds__(kBlock) k_tallT(IterCtx<T> c, SliceSet set, const T* X, const T* v,
                                                   const T* Y2, const T* w) {
-  __shared__ T red[(kBlock / 32 + 1) * M];
+  __shared__ T red[red_size<M>()];
+  pdl_enter();
   State* st = c.st;
   T acc[M];
 #pragma unroll
@@ -466,8 +547,9 @@ __global__ void __launch_bounds__(kBlock) k_tallT(IterCtx<T> c, SliceSet set, co
 template <typename T, int M>
 __global__ void __launch_bounds__(kBlock) k_tall_axpy(IterCtx<T> c, SliceSet set, const T* Z, T* v,
                                                       T sign, int norm) {
-  __shared__ T red[(kBlock / 32 + 1)];
+  __shared__ T red[red_size<1>()];
   __shared__ double us[M];
+  pdl_enter();
   State* st = c.st;
   for (int k = threadIdx.x; k < M; k += blockDim.x) us[k] = st->u[k];
   __syncthreads();
@@ -495,7 +577,8 @@ __global__ void __launch_bounds__(kBlock) k_tall_axpy(IterCtx<T> c, SliceSet set
 
 // The sample due at the last iteration (none is taken at the converging one), x = 0 for b = 0.
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_finish(IterCtx<T> c, SliceSet set) {
+__global__ void __launch_bounds__(kBlock, 4) k_finish(IterCtx<T> c, SliceSet set) {
+  pdl_enter();
   const State* st = c.st;
   const int pend = st->pend_slot;
   const bool zero = st->zero_rhs;
@@ -513,20 +596,19 @@ __global__ void __launch_bounds__(kBlock) k_finish(IterCtx<T> c, SliceSet set) {
 
 // ||b - A x||^2
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_true_res(IterCtx<T> c, SliceSet set) {
-  __shared__ T red[(kBlock / 32 + 1)];
+__global__ void __launch_bounds__(kBlock, 4) k_true_res(IterCtx<T> c, SliceSet set) {
+  __shared__ T red[red_size<1>()];
+  pdl_enter();
   State* st = c.st;
   T acc[1] = {T(0)};
   ESD_LOOP_SLICES(set) {
     int r;
     const int s = set.slice(g, &r);
     const int4 md = c.Av.meta[s];
-    const T ax = row_dot(c.Av, md, lane, c.x);
-    if (lane < md.w) {
-      const int i = md.z + lane;
-      const T t = c.b[i] - ax;
-      acc[0] = fma(t, t, acc[0]);
-    }
+    const int i = md.z + lane;
+    const bool valid = lane < md.w;
+    const T t = row_fma(c.Av, md, lane, c.x, valid ? -c.b[i] : T(0));  // A x - b
+    if (valid) acc[0] = fma(t, t, acc[0]);
   }
   if (grid_sum_multi<1>(acc, red, (T*)c.partials, &st->ticket[kTkAux])) {
     if (threadIdx.x == 0) st->true_rr = (double)red[0];
@@ -556,28 +638,36 @@ __global__ void __launch_bounds__(kBlock) k_true_res(IterCtx<T> c, SliceSet set)
     default: throw Error(ESD_ERR_INVALID, "unsupported padded column count");         \
   }
 
+// launch kernel K over `slices` slices with one wave at most
+#define ESD_LAUNCH(K, slices, s, ...) launch_pdl(K, grid_for(K, (slices)), (s), __VA_ARGS__)
+
+template <typename T, int M, int MODE, int PRE>
+static void launch_update_k(const IterCtx<T>& c, int do_update, int finalize, cudaStream_t s) {
+  auto k = k_update<T, M, MODE, PRE>;
+  ESD_LAUNCH(k, c.A->all.total(), s, c, c.A->all, do_update, finalize);
+}
+
 template <typename T>
 static void launch_update(const IterCtx<T>& c, int do_update, int finalize, cudaStream_t s,
                           KernelMarks* marks = nullptr) {
-  const SliceSet& all = c.A->all;
-  const int G = grid_blocks(all.total());
   const int Mm = (c.mode == ESD_PLAIN) ? 0 : c.M;
   if (c.pre == ESD_PRECOND_IC0) {
-    if (c.mode == ESD_PLAIN)
-      k_update<T, 0, kModePlain, ESD_PRECOND_IC0><<<G, kBlock, 0, s>>>(c, all, do_update, finalize);
-    else if (c.mode == ESD_DEFLATION)
-      ESD_DISPATCH_MPOS(Mm, k_update<T, MM, kModeDefl, ESD_PRECOND_IC0><<<G, kBlock, 0, s>>>(c, all, do_update, finalize))
-    else
-      ESD_DISPATCH_MPOS(Mm, k_update<T, MM, kModeSC, ESD_PRECOND_IC0><<<G, kBlock, 0, s>>>(c, all, do_update, finalize))
+    if (c.mode == ESD_PLAIN) {
+      launch_update_k<T, 0, kModePlain, ESD_PRECOND_IC0>(c, do_update, finalize, s);
+    } else if (c.mode == ESD_DEFLATION) {
+      ESD_DISPATCH_MPOS(Mm, (launch_update_k<T, MM, kModeDefl, ESD_PRECOND_IC0>(c, do_update, finalize, s)))
+    } else {
+      ESD_DISPATCH_MPOS(Mm, (launch_update_k<T, MM, kModeSC, ESD_PRECOND_IC0>(c, do_update, finalize, s)))
+    }
   } else {
-    if (c.mode == ESD_PLAIN)
-      k_update<T, 0, kModePlain, ESD_PRECOND_NONE><<<G, kBlock, 0, s>>>(c, all, do_update, finalize);
-    else if (c.mode == ESD_DEFLATION)
-      ESD_DISPATCH_MPOS(Mm, k_update<T, MM, kModeDefl, ESD_PRECOND_NONE><<<G, kBlock, 0, s>>>(c, all, do_update, finalize))
-    else
-      ESD_DISPATCH_MPOS(Mm, k_update<T, MM, kModeSC, ESD_PRECOND_NONE><<<G, kBlock, 0, s>>>(c, all, do_update, finalize))
+    if (c.mode == ESD_PLAIN) {
+      launch_update_k<T, 0, kModePlain, ESD_PRECOND_NONE>(c, do_update, finalize, s);
+    } else if (c.mode == ESD_DEFLATION) {
+      ESD_DISPATCH_MPOS(Mm, (launch_update_k<T, MM, kModeDefl, ESD_PRECOND_NONE>(c, do_update, finalize, s)))
+    } else {
+      ESD_DISPATCH_MPOS(Mm, (launch_update_k<T, MM, kModeSC, ESD_PRECOND_NONE>(c, do_update, finalize, s)))
+    }
   }
-  ESD_CUDA(cudaGetLastError());
   if (marks) marks->mark(s, "update");
 }
 
@@ -587,15 +677,20 @@ static void launch_precond(const IterCtx<T>& c, cudaStream_t s, KernelMarks* mar
   const esd_matrix* A = c.A;
   const int SCM = (c.mode == ESD_SUBSPACE_CORRECTION) ? c.M : 0;
   if (c.pre == ESD_PRECOND_NONE) {
-    ESD_DISPATCH_M(SCM, k_dir<T, MM><<<grid_blocks(A->all.total()), kBlock, 0, s>>>(c, A->all));
-    ESD_CUDA(cudaGetLastError());
+    ESD_DISPATCH_M(SCM, { auto k = k_dir<T, MM>; ESD_LAUNCH(k, A->all.total(), s, c, A->all); });
     if (marks) marks->mark(s, "dir");
     return;
   }
-  for (size_t l = 0; l < A->fwd_sets.size(); ++l) {
+  RhoSlots prev{};
+  const size_t nf = A->fwd_sets.size();
+  auto kf = k_fwd<T>;
+  for (size_t l = 0; l < nf; ++l) {
     const SliceSet& set = A->fwd_sets[l];
-    k_fwd<T><<<grid_blocks(set.total()), kBlock, 0, s>>>(c, set, l + 1 == A->fwd_sets.size() ? 1 : 0);
-    ESD_CUDA(cudaGetLastError());
+    const int G = grid_for(kf, set.total());
+    const bool last = l + 1 == nf;
+    if (!last && prev.n >= kMaxRanges) throw Error(ESD_ERR_INVALID, "too many forward launches");
+    launch_pdl(kf, G, s, c, set, last ? -1 : prev.n, prev);
+    if (!last) prev.G[prev.n++] = G;
     if (marks) marks->mark(s, ("fwd_" + std::to_string(l + 1)).c_str());
   }
   SliceSet none{};
@@ -603,8 +698,7 @@ static void launch_precond(const IterCtx<T>& c, cudaStream_t s, KernelMarks* mar
   for (size_t l = 0; l < nb; ++l) {
     const SliceSet& sw = l < A->bwd_sets.size() ? A->bwd_sets[l] : none;
     const SliceSet& el = l < A->bwd0_sets.size() ? A->bwd0_sets[l] : none;
-    ESD_DISPATCH_M(SCM, k_bwd<T, MM><<<grid_blocks(sw.total() + el.total()), kBlock, 0, s>>>(c, sw, el));
-    ESD_CUDA(cudaGetLastError());
+    ESD_DISPATCH_M(SCM, { auto k = k_bwd<T, MM>; ESD_LAUNCH(k, sw.total() + el.total(), s, c, sw, el); });
     if (marks) marks->mark(s, ("bwd_" + std::to_string(l + 1)).c_str());
   }
 }
@@ -612,15 +706,20 @@ static void launch_precond(const IterCtx<T>& c, cudaStream_t s, KernelMarks* mar
 template <typename T>
 void launch_init(const IterCtx<T>& c, cudaStream_t s) {
   const SliceSet& all = c.A->all;
-  const int G = grid_blocks(all.total());
-  k_residual0<T><<<G, kBlock, 0, s>>>(c, all);
-  ESD_CUDA(cudaGetLastError());
+  {
+    auto k = k_residual0<T>;
+    ESD_LAUNCH(k, all.total(), s, c, all);
+  }
   if (c.mode == ESD_DEFLATION) {
     // r0 = P^T (b - A x0) = r - AW E^-1 W^T r
-    ESD_DISPATCH_MPOS(c.M, k_tallT<T, MM><<<G, kBlock, 0, s>>>(c, all, c.W, c.r, (const T*)nullptr, (const T*)nullptr));
-    ESD_CUDA(cudaGetLastError());
-    ESD_DISPATCH_MPOS(c.M, k_tall_axpy<T, MM><<<G, kBlock, 0, s>>>(c, all, c.AW, c.r, T(-1), 1));
-    ESD_CUDA(cudaGetLastError());
+    ESD_DISPATCH_MPOS(c.M, {
+      auto k = k_tallT<T, MM>;
+      ESD_LAUNCH(k, all.total(), s, c, all, (const T*)c.W, (const T*)c.r, (const T*)nullptr, (const T*)nullptr);
+    });
+    ESD_DISPATCH_MPOS(c.M, {
+      auto k = k_tall_axpy<T, MM>;
+      ESD_LAUNCH(k, all.total(), s, c, all, (const T*)c.AW, c.r, T(-1), 1);
+    });
   }
   const bool fin = c.pre == ESD_PRECOND_NONE || c.A->fwd_sets.empty();
   launch_update<T>(c, 0, fin ? 1 : 0, s);
@@ -630,11 +729,9 @@ void launch_init(const IterCtx<T>& c, cudaStream_t s) {
 template <typename T>
 void launch_iteration(const IterCtx<T>& c, cudaStream_t s, KernelMarks* marks) {
   const SliceSet& all = c.A->all;
-  const int G = grid_blocks(all.total());
   const int Mm = (c.mode == ESD_DEFLATION) ? c.M : 0;
   if (marks) marks->mark(s, "start");
-  ESD_DISPATCH_M(Mm, k_spmv_pq<T, MM><<<G, kBlock, 0, s>>>(c, all));
-  ESD_CUDA(cudaGetLastError());
+  ESD_DISPATCH_M(Mm, { auto k = k_spmv_pq<T, MM>; ESD_LAUNCH(k, all.total(), s, c, all); });
   if (marks) marks->mark(s, "spmv_pq");
   const bool fin = c.pre == ESD_PRECOND_NONE || c.A->fwd_sets.empty();
   launch_update<T>(c, 1, fin ? 1 : 0, s, marks);
@@ -644,16 +741,21 @@ void launch_iteration(const IterCtx<T>& c, cudaStream_t s, KernelMarks* marks) {
 template <typename T>
 void launch_finish(const IterCtx<T>& c, cudaStream_t s) {
   const SliceSet& all = c.A->all;
-  const int G = grid_blocks(all.total());
   if (c.mode == ESD_DEFLATION) {
     // x = P x_i + W E^-1 W^T b = x_i + W E^-1 (W^T b - (AW)^T x_i)
-    ESD_DISPATCH_MPOS(c.M, k_tallT<T, MM><<<G, kBlock, 0, s>>>(c, all, c.W, c.b, c.AW, c.x));
-    ESD_CUDA(cudaGetLastError());
-    ESD_DISPATCH_MPOS(c.M, k_tall_axpy<T, MM><<<G, kBlock, 0, s>>>(c, all, c.W, c.x, T(1), 0));
-    ESD_CUDA(cudaGetLastError());
+    ESD_DISPATCH_MPOS(c.M, {
+      auto k = k_tallT<T, MM>;
+      ESD_LAUNCH(k, all.total(), s, c, all, (const T*)c.W, (const T*)c.b, (const T*)c.AW, (const T*)c.x);
+    });
+    ESD_DISPATCH_MPOS(c.M, {
+      auto k = k_tall_axpy<T, MM>;
+      ESD_LAUNCH(k, all.total(), s, c, all, (const T*)c.W, c.x, T(1), 0);
+    });
   }
-  k_finish<T><<<G, kBlock, 0, s>>>(c, all);
-  ESD_CUDA(cudaGetLastError());
+  {
+    auto k = k_finish<T>;
+    ESD_LAUNCH(k, all.total(), s, c, all);
+  }
 }
 
 #define ESD_INSTANTIATE_ITER(T)                                                        \

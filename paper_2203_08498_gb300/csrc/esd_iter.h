@@ -29,6 +29,8 @@ struct IterCtx {
   double* ahist = nullptr;
   double* bhist = nullptr;
   void* partials = nullptr;
+  void* rho_part = nullptr;     // block totals of the forward launches before the last one
+  size_t rho_stride = 0;        // entries per forward launch in rho_part
   State* st = nullptr;
   const unsigned char* sflags = nullptr;
   unsigned long long cond = 0;  // graph conditional handle (0 = none)

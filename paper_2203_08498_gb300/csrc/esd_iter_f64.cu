@@ -16,20 +16,16 @@ int pad_m(int m) {
 }
 
 void launch_spmv(const esd_matrix* A, const double* x, double* y, cudaStream_t s) {
-  k_spmv<double><<<grid_blocks(A->all.total()), kBlock, 0, s>>>(A->A.view<double>(), A->all, x, y);
-  ESD_CUDA(cudaGetLastError());
+  auto k = k_spmv<double>;
+  ESD_LAUNCH(k, A->all.total(), s, A->A.view<double>(), A->all, x, y);
 }
 
 void launch_apply_ic(const esd_matrix* A, const double* r, double* z, double* work, cudaStream_t s) {
   const double* inv_d = A->inv_d.as<double>();
-  for (const SliceSet& set : A->fwd_all_sets) {
-    k_fwd_plain<double><<<grid_blocks(set.total()), kBlock, 0, s>>>(A->L.view<double>(), set, r, work, inv_d);
-    ESD_CUDA(cudaGetLastError());
-  }
-  for (const SliceSet& set : A->bwd_all_sets) {
-    k_bwd_plain<double><<<grid_blocks(set.total()), kBlock, 0, s>>>(A->U.view<double>(), set, work, z, inv_d);
-    ESD_CUDA(cudaGetLastError());
-  }
+  auto kf = k_fwd_plain<double>;
+  auto kb = k_bwd_plain<double>;
+  for (const SliceSet& set : A->fwd_all_sets) ESD_LAUNCH(kf, set.total(), s, A->L.view<double>(), set, r, work, inv_d);
+  for (const SliceSet& set : A->bwd_all_sets) ESD_LAUNCH(kb, set.total(), s, A->U.view<double>(), set, (const double*)work, z, inv_d);
 }
 
 void launch_spmm(const esd_matrix* A, const double* X, double* Y, size_t ld, int m, cudaStream_t s) {
@@ -47,8 +43,8 @@ void launch_axpby(int n, const double* x, double a, const double* sv, double* b,
 }
 
 void launch_true_residual(const IterCtx<double>& c, cudaStream_t s) {
-  k_true_res<double><<<grid_blocks(c.A->all.total()), kBlock, 0, s>>>(c, c.A->all);
-  ESD_CUDA(cudaGetLastError());
+  auto k = k_true_res<double>;
+  ESD_LAUNCH(k, c.A->all.total(), s, c, c.A->all);
 }
 
 }  // namespace esd

@@ -236,16 +236,24 @@ __global__ void k_ic0_level(SliceSet set, int n, const int4* mL, const int* colL
   }
 }
 
-__global__ void k_ic0_finish(int n, const double* ldiag, double* inv_d, long long nU,
-                             const int* umap, const double* valL, double* valU) {
+// U = L^T as the negated strict factor: U[e] = -l_ji (read before L is negated).
+__global__ void k_ic0_upper(int n, const double* ldiag, double* inv_d, long long nU, const int* umap,
+                            const double* valL, double* valU) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = t; i < n; i += stride) inv_d[i] = 1.0 / ldiag[i];
   if (t == 0) inv_d[n] = 0.0;
   for (long long e = t; e < nU; e += stride) {
     int m = umap[e];
-    valU[e] = m >= 0 ? valL[m] : 0.0;
+    valU[e] = m >= 0 ? -valL[m] : 0.0;
   }
+}
+
+// L's strict entries are stored negated, so a substitution is one FMA chain from r_i.
+__global__ void k_negate(long long cnt, double* v) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = t; i < cnt; i += stride) v[i] = -v[i];
 }
 
 __global__ void k_to_float(long long cnt, const double* a, float* b) {
@@ -440,6 +448,7 @@ int esd_create_matrix(int32_t n, int64_t nnz, const int32_t* rowptr, const int32
     }
     M->colour_first_slice[ncolours] = (int)rows.size();
     M->nslices = (int)rows.size();
+    ESD_CHECK(M->nslices < (1 << 24), ESD_ERR_INVALID, "more than 2^24 slices (n too large)");
     const int NS = M->nslices;
     DevBuf drows(sizeof(int2) * NS), wA(sizeof(int) * NS), wL(sizeof(int) * NS), wU(sizeof(int) * NS),
         dfirst(sizeof(int) * (ncolours + 1));
@@ -550,9 +559,11 @@ int esd_factor_ic0(esd_matrix* A, int32_t max_tries, double* shift_used) {
       ESD_CUDA(cudaMemcpyAsync(herr, A->err.get(), sizeof(herr), cudaMemcpyDeviceToHost, s));
       ESD_CUDA(cudaStreamSynchronize(s));
       if (herr[2] == 0) {
-        k_ic0_finish<<<max_grid_blocks(), kBlock, 0, s>>>(A->n, A->ldiag.as<double>(), A->inv_d.as<double>(),
-                                                          A->U.entries, A->umap.as<int>(),
-                                                          A->L.val.as<double>(), A->U.val.as<double>());
+        k_ic0_upper<<<max_grid_blocks(), kBlock, 0, s>>>(A->n, A->ldiag.as<double>(), A->inv_d.as<double>(),
+                                                         A->U.entries, A->umap.as<int>(),
+                                                         A->L.val.as<double>(), A->U.val.as<double>());
+        ESD_CUDA(cudaGetLastError());
+        k_negate<<<max_grid_blocks(), kBlock, 0, s>>>(A->L.entries, A->L.val.as<double>());
         ESD_CUDA(cudaGetLastError());
         ESD_CUDA(cudaStreamSynchronize(s));
         A->factored = true;

@@ -108,7 +108,7 @@ struct esd_solver {
   int mode = ESD_PLAIN;
   size_t ld = 0;
   DevBuf vb, vx, vr, vp, vq, vY, samples;
-  DevBuf W, AW, E, Einv, ritz, ahist, bhist, state, partials, ext;
+  DevBuf W, AW, E, Einv, ritz, ahist, bhist, state, partials, rho_part, ext;
   State* hst = nullptr;  // pinned host copy
   int m = 0, M = 0;      // columns of W, padded count
   int mbar = 0;
@@ -154,6 +154,8 @@ struct esd_solver {
     c.ahist = ahist.as<double>();
     c.bhist = bhist.as<double>();
     c.partials = partials.get();
+    c.rho_part = rho_part.get();
+    c.rho_stride = (size_t)max_grid_blocks();
     c.st = state.as<State>();
     c.sflags = A->slice_flags.as<unsigned char>();
     return c;
@@ -281,6 +283,7 @@ int esd_solver_create(esd_matrix* A, const esd_params* params, esd_solver** out)
   S->state.alloc(sizeof(State));
   ESD_CUDA(cudaMemsetAsync(S->state.get(), 0, sizeof(State), S->stream));
   S->partials.alloc(sizeof(double) * (size_t)max_grid_blocks() * kMaxRed);
+  S->rho_part.alloc(sizeof(double) * (size_t)max_grid_blocks() * kMaxRanges);
   S->E.alloc(sizeof(double) * kMaxM * kMaxM);
   S->Einv.alloc(sizeof(double) * kMaxM * kMaxM);
   S->ritz.alloc(sizeof(double) * kMaxM);
