@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--systems", type=int, default=20)
     ap.add_argument("--m", type=int, default=16)
     ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
+                    help="fp32: FP32 inner PCG inside FP64 iterative refinement")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, comparison modes and CPU baseline")
     return ap.parse_args()
 
@@ -154,7 +156,8 @@ def gpu_arm(args):
     mode = {"plain": esd.PLAIN, "deflation": esd.DEFLATION, "sc": esd.SUBSPACE_CORRECTION}[args.mode]
     A = esd.Matrix.from_problem(p)
     A.factor_ic0()
-    S = esd.Solver(A, maxit_cap=20000, sample_cap=max(args.m, 2))
+    prec = {"fp64": esd.FP64, "fp32": esd.FP32_REFINE}[args.precision]
+    S = esd.Solver(A, maxit_cap=20000, sample_cap=max(args.m, 2), precision=prec)
     src = torch.from_numpy(p.source).to(dev)
     x = torch.zeros(n, dtype=torch.float64, device=dev)
     b = torch.empty_like(x)
@@ -181,9 +184,9 @@ def gpu_arm(args):
             its.append(it)
         return its, stats
 
-    def timed(md, steps, warm):
+    def timed(md, steps, warm, S=S):
         for _ in range(warm):
-            sequence(md)
+            sequence(md, S)
         torch.cuda.synchronize()
         if ws > 1:
             torch.distributed.barrier()
@@ -193,7 +196,7 @@ def gpu_arm(args):
         e0.record()
         out = []
         for _ in range(steps):
-            out.append(sequence(md))
+            out.append(sequence(md, S))
         e1.record()
         torch.cuda.synchronize()
         if ws > 1:
@@ -233,9 +236,11 @@ def gpu_arm(args):
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32 inner, f64 refinement", "data": "synthetic",
         "config": {"workload": workload_name(args, p), "grid": args.grid, "n": n, "nnz": nnz,
                    "systems": args.systems, "m": args.m, "mode": args.mode, "tol": args.tol,
+                   "precision": args.precision,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "inputs larger than L2 (matrix, factor and vectors ~1.3 GB > 129 MB)"},
         "gpu_launches": launches,
@@ -267,6 +272,18 @@ def gpu_arm(args):
         modes[name] = {"iterations": its_m, "ms_per_sequence": ms_m, "solves_per_s": args.systems / (ms_m / 1e3),
                        "mean_iters_2_to_T": float(np.mean(its_m[1:]))}
     result["modes"] = modes
+    # the precision form on the same sequence: FP32 inner PCG (resumed, inner_tol 0.3) inside
+    # FP64 refinement to the same tolerance, against plain FP64 PCG
+    if args.precision == "fp64":
+        S32 = esd.Solver(A, maxit_cap=20000, sample_cap=max(args.m, 2), precision=esd.FP32_REFINE)
+        fp64_plain_ms = modes["plain"]["ms_per_sequence"]
+        pf = {"fp64_plain_ms_per_system": fp64_plain_ms / args.systems}
+        for name, md in (("plain", esd.PLAIN), ("deflation", esd.DEFLATION), ("sc", esd.SUBSPACE_CORRECTION)):
+            ms_m, _, r = timed(md, 1, 1, S=S32)
+            its_m = r[-1][0]
+            pf[f"fp32_{name}"] = {"ms_per_system": ms_m / args.systems, "iterations": its_m,
+                                  "speedup_vs_fp64_plain": fp64_plain_ms / ms_m}
+        result["precision_form"] = pf
     # time per iteration and model bandwidth per mode (single solves of system 2)
     result["iteration"] = iteration_roofline(S, esd, p, args, x, b, src, peaks)
 

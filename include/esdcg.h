@@ -120,11 +120,14 @@ typedef struct {
   int32_t lmax;        /* sampling method A parameter l_max (m^l_max > N_max); 0 = smallest valid */
   double rank_tol;     /* rank rule for the sampled errors, e.g. 1e-12 */
   int32_t precision;   /* esd_precision */
-  double inner_tol;    /* relative tolerance of each FP32 inner solve (ESD_FP32_REFINE) */
-  int32_t max_outer;   /* refinement steps allowed (ESD_FP32_REFINE) */
+  double inner_tol;    /* ESD_FP32_REFINE: residual reduction of each FP32 inner solve */
+  int32_t max_outer;   /* ESD_FP32_REFINE: refinement steps allowed */
+  int32_t resume_direction; /* ESD_FP32_REFINE: 1 = every step resumes CG with the kept search
+                               direction (residual replacement), 0 = every step restarts CG */
 } esd_params;
 
-/* Default parameters: IC(0), maxit_cap 20000, sample_cap 32, lmax 0, rank_tol 1e-12, FP64. */
+/* Default parameters: IC(0), maxit_cap 20000, sample_cap 32, lmax 0, rank_tol 1e-12, FP64;
+ * for ESD_FP32_REFINE inner_tol 0.3, max_outer 60, resume_direction 1. */
 void esd_params_default(esd_params* p);
 
 int esd_solver_create(esd_matrix* A, const esd_params* params, esd_solver** out);
@@ -152,6 +155,17 @@ int esd_set_mode(esd_solver* S, int32_t mode);
  * final x = P x_i + W E^{-1} W^T b. b = 0 gives x = 0 and 0 iterations.
  * The whole solve is one CUDA graph launch (a device-side while loop); the call
  * synchronises once at the end to return iters and relres.
+ * Precision ESD_FP32_REFINE (not in the paper): x is refined in FP64. Each step forms
+ * r = b - A x in FP64; when ||r|| > tol ||b|| it solves A d = r with the selected mode in
+ * FP32 (FP32 matrix, factor, W and AW, FP32-accumulated dot products; E^{-1} stays FP64)
+ * to ||r_inner|| <= max(inner_tol ||r||, tol ||b|| / 2), then x += d in FP64; at most
+ * max_outer steps. With resume_direction the inner CG state carries over from step to step
+ * (only the residual is replaced by the FP64 one), so the steps form one CG run; otherwise
+ * each inner solve starts afresh. Both loops run on the device (nested while nodes). iters
+ * counts the inner iterations (and maxit bounds them: per inner solve when restarting, in
+ * total when resuming); relres is the FP64 true residual. Sampling (sample_m > 0) stores
+ * FP64 iterates (the FP64 x plus the inner iterate) of the first inner solve, or of the whole
+ * run when resuming.
  * Errors: ESD_ERR_MAXIT (x = last iterate), ESD_ERR_BREAKDOWN, ESD_ERR_STATE.
  */
 int esd_solve(esd_solver* S, const double* b, double* x, double tol, int32_t maxit,
@@ -159,6 +173,18 @@ int esd_solve(esd_solver* S, const double* b, double* x, double tol, int32_t max
 
 /* ||b - A x|| / ||b|| of the last solve, recomputed in FP64 from the returned x. */
 int esd_true_relres(esd_solver* S, double* relres);
+
+/*
+ * The last solve in numbers (host pointers, any may be NULL): iters = CG iterations (in the
+ * refinement form the inner FP32 iterations of all steps), outer_steps = refinement steps
+ * (0 in FP64 form), first_inner = iterations of the first inner solve, the one sampling
+ * reads (= iters in FP64 form), restarts = resumed steps that restarted the search
+ * direction because the inner residual had drifted from the true one by more than half of it,
+ * max_gap = the largest such relative drift seen, true_relres = ||b - A x||/||b|| in FP64,
+ * status = the solve's return code.
+ */
+int esd_last_solve_info(esd_solver* S, int32_t* iters, int32_t* outer_steps, int32_t* first_inner,
+                        int32_t* restarts, double* max_gap, double* true_relres, int32_t* status);
 
 /*
  * Build W from the iterates stored by the last sampling solve (Section 4.2):

@@ -24,7 +24,8 @@ __all__ = [
     "PRECOND_NONE", "PRECOND_IC0", "FP64", "FP32_REFINE", "EsdParams", "HEADER_SYMBOLS",
     "esd_create_matrix", "esd_matrix_destroy", "esd_matrix_info", "esd_factor_ic0", "esd_matrix_spmv",
     "esd_matrix_apply_ic", "esd_pattern_grad", "esd_params_default", "esd_solver_create",
-    "esd_solver_destroy", "esd_set_mode", "esd_solve", "esd_true_relres", "esd_sample_and_build_W",
+    "esd_solver_destroy", "esd_set_mode", "esd_solve", "esd_true_relres", "esd_last_solve_info",
+    "esd_sample_and_build_W",
     "esd_set_W", "esd_get_W", "esd_ritz_values", "esd_estimate_cond", "esd_get_history",
     "esd_get_samples", "esd_backward_euler_rhs", "esd_profile_iterations", "esd_last_error",
     "esd_lanczos_extremes_noalloc", "NOALLOC_MAX_K",
@@ -59,7 +60,7 @@ class EsdError(RuntimeError):
 class EsdParams(C.Structure):
     _fields_ = [("precond", C.c_int32), ("maxit_cap", C.c_int32), ("sample_cap", C.c_int32),
                 ("lmax", C.c_int32), ("rank_tol", C.c_double), ("precision", C.c_int32),
-                ("inner_tol", C.c_double), ("max_outer", C.c_int32)]
+                ("inner_tol", C.c_double), ("max_outer", C.c_int32), ("resume_direction", C.c_int32)]
 
 
 _lib = None
@@ -90,6 +91,7 @@ def lib(build_if_missing: bool = True):
             "esd_set_mode": (i32, [vp, i32]),
             "esd_solve": (i32, [vp, vp, vp, f64, i32, i32, P(i32), P(f64)]),
             "esd_true_relres": (i32, [vp, P(f64)]),
+            "esd_last_solve_info": (i32, [vp, P(i32), P(i32), P(i32), P(i32), P(f64), P(f64), P(i32)]),
             "esd_sample_and_build_W": (i32, [vp, f64, P(i32)]),
             "esd_set_W": (i32, [vp, vp, i32]),
             "esd_get_W": (i32, [vp, vp, vp, vp, P(i32)]),
@@ -235,6 +237,17 @@ def esd_true_relres(h):
     return v.value
 
 
+def esd_last_solve_info(h):
+    """dict(iters, outer_steps, first_inner, restarts, max_gap, true_relres, status) of the
+    last solve."""
+    it, outer, first, rs, st = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+    gap, rr = C.c_double(), C.c_double()
+    _check(lib().esd_last_solve_info(h, C.byref(it), C.byref(outer), C.byref(first), C.byref(rs),
+                                     C.byref(gap), C.byref(rr), C.byref(st)))
+    return {"iters": it.value, "outer_steps": outer.value, "first_inner": first.value,
+            "restarts": rs.value, "max_gap": gap.value, "true_relres": rr.value, "status": st.value}
+
+
 def esd_sample_and_build_W(h, theta=math.inf):
     m = C.c_int32()
     _check(lib().esd_sample_and_build_W(h, theta, C.byref(m)))
@@ -361,10 +374,11 @@ class Solver:
     """``esd_solver`` bound to a Matrix; keeps the matrix alive."""
 
     def __init__(self, matrix: Matrix, precond=PRECOND_IC0, maxit_cap=20000, sample_cap=32, lmax=0,
-                 rank_tol=1e-12, precision=FP64, inner_tol=1e-4, max_outer=30):
+                 rank_tol=1e-12, precision=FP64, inner_tol=0.3, max_outer=60, resume_direction=1):
         p = esd_params_default()
         p.precond, p.maxit_cap, p.sample_cap, p.lmax = precond, maxit_cap, sample_cap, lmax
         p.rank_tol, p.precision, p.inner_tol, p.max_outer = rank_tol, precision, inner_tol, max_outer
+        p.resume_direction = resume_direction
         self.matrix = matrix
         self.maxit_cap = maxit_cap
         self._h = esd_solver_create(matrix.handle, p)
@@ -377,6 +391,9 @@ class Solver:
 
     def true_relres(self):
         return esd_true_relres(self._h)
+
+    def last_solve_info(self):
+        return esd_last_solve_info(self._h)
 
     def sample_and_build_W(self, theta=math.inf):
         return esd_sample_and_build_W(self._h, theta)

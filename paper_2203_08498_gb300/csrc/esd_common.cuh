@@ -75,9 +75,10 @@ struct State {
   int lmax;
   int h;            // the interval h of sampling method A
   int pend_slot;    // slot to receive x at the next update (-1 = none)
-  int pend_iter;
+  int pend_prev;    // slot_iter[pend_slot] before it was claimed (a deferred sample's undo)
   int guard;        // loop bodies started; a second, reduction-free bound on the loop
-  int pad1;
+  int defer_sample; // resumed runs: a stopping run leaves its sample to the run that resumes
+  int fresh_dir;    // the next direction update starts afresh (p = z) without resetting iter
   int slot_iter[kMaxM];
   double y[kMaxM];  // deflation: E^{-1} (AW)^T p
   double u[kMaxM];  // subspace correction / projection: E^{-1} f
@@ -85,6 +86,29 @@ struct State {
 };
 
 enum Ticket { kTkSpmv = 0, kTkUpdate = 1, kTkSweep = 2, kTkAux = 3, kTkAux2 = 4 };
+
+// Device state of the FP64 iterative refinement around FP32 inner solves.
+struct RefineState {
+  double bb;          // ||b||^2
+  double rr;          // ||b - A x||^2 of the current FP64 iterate
+  double tol2bb;      // tol^2 ||b||^2
+  double inner_tol2;  // relative tolerance^2 of every inner solve
+  int outer;          // refinement steps done
+  int max_outer;
+  int inner_total;    // inner iterations over all steps
+  int inner_maxit;
+  int samp_m;         // sampling in the first inner solve (0 = off)
+  int lmax;
+  int status;
+  int conv;
+  unsigned int ticket;
+  int first_inner;    // iterations of the first inner solve (the sampled one)
+  int keep;           // 1: every step resumes CG with the previous step's direction
+  int fresh;          // the step about to start resumes with p = z (the gap was too large)
+  int restarts;       // resumed steps that restarted the direction
+  int pad;
+  double max_gap;     // largest ||r_true - r_inner|| / ||r_true|| at a resumed step
+};
 
 struct Error : std::runtime_error {
   int code;

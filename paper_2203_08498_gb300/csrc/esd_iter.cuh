@@ -51,6 +51,20 @@ __device__ __forceinline__ T row_fma(const SellView<T>& M, const int4& md, int l
   return acc;
 }
 
+// Difference form of the same row product: s_i v_i + sum_j a_ij (v_j - v_i), s = A 1. For
+// a smooth v the differences are exact (or nearly) and nothing cancels, so in FP32 the
+// result keeps its relative accuracy where the plain sum loses up to cond(A) of it.
+template <typename T>
+__device__ __forceinline__ T row_fma_diff(const SellView<T>& M, const int4& md, int lane, const T* __restrict__ v,
+                                          T vi, T si, T init) {
+  const int* cp = M.col + md.x + lane;
+  const T* vp = M.val + md.x + lane;
+  T acc = fma(si, vi, init);
+#pragma unroll 4
+  for (int k = 0; k < md.y; ++k) acc = fma(ld_stream(vp + k * kSlice), v[ld_stream(cp + k * kSlice)] - vi, acc);
+  return acc;
+}
+
 __device__ __forceinline__ void end_loop(unsigned long long cond) {
   if (cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, 0u);
 }
@@ -64,9 +78,9 @@ __device__ __forceinline__ bool finalize_rho(State* st, double rho_new, double* 
     end_loop(cond);
     return false;
   }
-  const bool first = st->iter == 0;
+  const bool first = st->iter == 0 || st->fresh_dir;
   const double beta = first ? 0.0 : rho_new / st->rho;
-  if (!first) bhist[st->iter - 1] = beta;
+  if (st->iter > 0) bhist[st->iter - 1] = beta;
   st->beta = beta;
   st->rho = rho_new;
   return true;
@@ -83,6 +97,7 @@ __device__ __forceinline__ void sampling_a(State* st) {
   }
   const int slot = (int)(it % m);
   st->pend_slot = slot;
+  st->pend_prev = st->slot_iter[slot];
   st->slot_iter[slot] = i;
   if (i == st->h * m) st->h *= 2;
 }
@@ -134,7 +149,7 @@ inline void launch_pdl(void (*kernel)(KArgs...), int blocks, cudaStream_t s, Arg
 // Forward launches whose y_i^2 block totals the last forward launch adds up.
 struct RhoSlots {
   int n;
-  int G[kMaxRanges];
+  int G[kMaxColours];
 };
 
 // ------------------------------------------------------------------ plain kernels
@@ -211,9 +226,16 @@ __global__ void __launch_bounds__(kBlock, M == 0 ? ESD_SWEEP_MINB : (M <= 16 ? 2
     int r;
     const int s = set.slice(g, &r);
     const int4 md = c.Av.meta[s];
-    const T qi = row_fma(c.Av, md, lane, c.p, T(0));
-    if (lane < md.w) {
-      const int i = md.z + lane;
+    const int i = md.z + lane;
+    const bool valid = lane < md.w;
+    T qi;
+    if (sizeof(T) == 4 && c.rowsum) {
+      const T pv = valid ? c.p[i] : T(0);
+      qi = row_fma_diff(c.Av, md, lane, c.p, pv, valid ? c.rowsum[i] : T(0), T(0));
+    } else {
+      qi = row_fma(c.Av, md, lane, c.p, T(0));
+    }
+    if (valid) {
       const T pi = c.p[i];
       c.q[i] = qi;
       acc[0] = fma(pi, qi, acc[0]);
@@ -288,7 +310,10 @@ __global__ void __launch_bounds__(kBlock, M == 0 ? 4 : 1) k_update(IterCtx<T> c,
       T ri;
       if (do_update) {
         const T xi = c.x[i];
-        if (pend >= 0) c.samples[(size_t)pend * c.ld + i] = xi;
+        if (pend >= 0) {
+          if (c.samples64) c.samples64[(size_t)pend * c.ld + i] = c.xbase[i] + (double)xi;
+          else c.samples[(size_t)pend * c.ld + i] = xi;
+        }
         c.x[i] = fma(alpha, c.p[i], xi);
         T t = c.q[i];
 #pragma unroll
@@ -332,6 +357,7 @@ __global__ void __launch_bounds__(kBlock, M == 0 ? 4 : 1) k_update(IterCtx<T> c,
         st->rr = (double)red[0];
         st->iter += 1;
         st->pend_slot = -1;
+        st->fresh_dir = 0;
       }
       const double rr = st->rr;
       bool stop = false;
@@ -344,7 +370,9 @@ __global__ void __launch_bounds__(kBlock, M == 0 ? 4 : 1) k_update(IterCtx<T> c,
         st->status = ESD_ERR_MAXIT;
         stop = true;
       }
-      if (!stop && do_update && st->samp_m > 0) sampling_a(st);
+      // a run that will be resumed goes on sampling at its stop: the iterate is written by
+      // the next run's first update, or the claim is undone if no run follows
+      if ((!stop || st->defer_sample) && do_update && st->samp_m > 0) sampling_a(st);
       st->fu = SCM > 0 ? fu_s : 0.0;
       if (PRE == ESD_PRECOND_IC0) st->rho_acc = (double)red[1];
       if (stop) {
@@ -393,13 +421,9 @@ __global__ void __launch_bounds__(kBlock, ESD_SWEEP_MINB) k_fwd(IterCtx<T> c, Sl
   if (grid_sum_multi<1>(acc, red, (T*)c.partials, &st->ticket[kTkSweep])) {
     if (threadIdx.x == 0) own_s = (double)red[0];
     T acc2[1] = {T(0)};
-#pragma unroll
-    for (int k = 0; k < kMaxRanges; ++k) {
-      if (k < prev.n) {
-        for (int b = threadIdx.x; b < prev.G[k]; b += blockDim.x)
-          acc2[0] += __ldcg(&slots[(size_t)k * c.rho_stride + b]);
-      }
-    }
+    for (int k = 0; k < prev.n; ++k)
+      for (int b = threadIdx.x; b < prev.G[k]; b += blockDim.x)
+        acc2[0] += __ldcg(&slots[(size_t)k * c.rho_stride + b]);
     block_sum_multi<1>(acc2, red);
     if (threadIdx.x == 0) finalize_rho(st, own_s + (double)red[0] + st->rho_acc + st->fu, c.bhist, c.cond);
   }
@@ -415,7 +439,7 @@ __global__ void __launch_bounds__(kBlock, SCM == 0 ? ESD_SWEEP_MINB : 1) k_bwd(I
   State* st = c.st;
   if (st->conv) return;
   const T beta = (T)st->beta;
-  const bool first = st->iter == 0;
+  const bool first = st->iter == 0 || st->fresh_dir;
   if (SCM > 0) {
     for (int k = threadIdx.x; k < SCM; k += blockDim.x) us[k] = st->u[k];
     __syncthreads();
@@ -455,7 +479,7 @@ __global__ void __launch_bounds__(kBlock, SCM == 0 ? 4 : 1) k_dir(IterCtx<T> c, 
   State* st = c.st;
   if (st->conv) return;
   const T beta = (T)st->beta;
-  const bool first = st->iter == 0;
+  const bool first = st->iter == 0 || st->fresh_dir;
   if (SCM > 0) {
     for (int k = threadIdx.x; k < SCM; k += blockDim.x) us[k] = st->u[k];
     __syncthreads();
@@ -485,7 +509,16 @@ __global__ void __launch_bounds__(kBlock, 4) k_residual0(IterCtx<T> c, SliceSet 
     int r;
     const int s = set.slice(g, &r);
     const int4 md = c.Av.meta[s];
-    const T ax = row_fma(c.Av, md, lane, c.x, T(0));
+    T ax = T(0);
+    if (!c.x_zero) {
+      if (sizeof(T) == 4 && c.rowsum) {
+        const bool valid = lane < md.w;
+        const int i = md.z + lane;
+        ax = row_fma_diff(c.Av, md, lane, c.x, valid ? c.x[i] : T(0), valid ? c.rowsum[i] : T(0), T(0));
+      } else {
+        ax = row_fma(c.Av, md, lane, c.x, T(0));
+      }
+    }
     if (lane < md.w) {
       const int i = md.z + lane;
       const T bi = c.b[i];
@@ -580,7 +613,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock, 4) k_finish(IterCtx<T> c, SliceSet set) {
   pdl_enter();
   const State* st = c.st;
-  const int pend = st->pend_slot;
+  const int pend = st->defer_sample ? -1 : st->pend_slot;
   const bool zero = st->zero_rhs;
   ESD_LOOP_SLICES(set) {
     int r;
@@ -588,7 +621,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_finish(IterCtx<T> c, SliceSet set
     const int4 md = c.Av.meta[s];
     if (lane < md.w) {
       const int i = md.z + lane;
-      if (pend >= 0 && c.samples) c.samples[(size_t)pend * c.ld + i] = c.x[i];
+      if (pend >= 0 && c.samples64) c.samples64[(size_t)pend * c.ld + i] = c.xbase[i] + (double)c.x[i];
+      else if (pend >= 0 && c.samples) c.samples[(size_t)pend * c.ld + i] = c.x[i];
       if (zero) c.x[i] = T(0);
     }
   }
@@ -688,7 +722,7 @@ static void launch_precond(const IterCtx<T>& c, cudaStream_t s, KernelMarks* mar
     const SliceSet& set = A->fwd_sets[l];
     const int G = grid_for(kf, set.total());
     const bool last = l + 1 == nf;
-    if (!last && prev.n >= kMaxRanges) throw Error(ESD_ERR_INVALID, "too many forward launches");
+    if (!last && prev.n >= kMaxColours) throw Error(ESD_ERR_INVALID, "too many forward launches");
     launch_pdl(kf, G, s, c, set, last ? -1 : prev.n, prev);
     if (!last) prev.G[prev.n++] = G;
     if (marks) marks->mark(s, ("fwd_" + std::to_string(l + 1)).c_str());

@@ -14,6 +14,7 @@ struct IterCtx {
   const esd_matrix* A = nullptr;
   SellView<T> Av{}, Lv{}, Uv{};
   const T* inv_d = nullptr;
+  const T* rowsum = nullptr;  // set: A v is formed as s_i v_i + sum_j a_ij (v_j - v_i)
   T* b = nullptr;   // right-hand side
   T* x = nullptr;   // iterate
   T* r = nullptr;   // residual (deflated residual in deflation mode)
@@ -26,6 +27,8 @@ struct IterCtx {
   const double* Einv = nullptr;  // M x M row-major (zero-padded)
   int M = 0;              // padded number of W columns (0, 8, 16, 24, 32, 64)
   T* samples = nullptr;   // sample slots, stride ld
+  double* samples64 = nullptr;   // refinement form: FP64 slots receive xbase + x instead
+  const double* xbase = nullptr;  // refinement form: the FP64 iterate the inner x corrects
   double* ahist = nullptr;
   double* bhist = nullptr;
   void* partials = nullptr;
@@ -36,6 +39,7 @@ struct IterCtx {
   unsigned long long cond = 0;  // graph conditional handle (0 = none)
   int mode = ESD_PLAIN;
   int pre = ESD_PRECOND_IC0;
+  int x_zero = 0;  // the start vector is known to be zero (r0 = b without a product)
 };
 
 // Optional event marks between the kernels of a launch sequence (profiling): mark() records

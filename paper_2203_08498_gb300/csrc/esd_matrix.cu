@@ -262,6 +262,20 @@ __global__ void k_to_float(long long cnt, const double* a, float* b) {
   for (long long i = t; i < cnt; i += stride) b[i] = (float)a[i];
 }
 
+// s_i = sum_j a_ij in FP64 (the row's own entries, padding adds zeros), stored as FP32
+__global__ void k_rowsum(SellView<double> A, int nslices, float* s) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int sl = gw; sl < nslices; sl += nw) {
+    const int4 md = A.meta[sl];
+    if (lane >= md.w) continue;
+    double acc = 0.0;
+    for (int k = 0; k < md.y; ++k) acc += A.val[md.x + lane + k * kSlice];
+    s[md.z + lane] = (float)acc;
+  }
+}
+
 static void to_float(const DevBuf& src, DevBuf& dst, long long cnt, cudaStream_t s) {
   if (dst.bytes() < (size_t)cnt * sizeof(float)) dst.alloc((size_t)cnt * sizeof(float));
   if (cnt == 0) return;
@@ -276,6 +290,12 @@ using namespace esd;
 void esd_matrix::ensure_fp32() {
   if (fp32_version == factor_version && A.val32.get()) return;
   to_float(A.val, A.val32, A.entries, stream);
+  if (!rowsum32.get()) {
+    rowsum32.alloc(sizeof(float) * vec_stride());
+    ESD_CUDA(cudaMemsetAsync(rowsum32.get(), 0, rowsum32.bytes(), stream));
+    k_rowsum<<<max_grid_blocks(), kBlock, 0, stream>>>(A.view<double>(), nslices, rowsum32.as<float>());
+    ESD_CUDA(cudaGetLastError());
+  }
   if (factored) {
     to_float(L.val, L.val32, L.entries, stream);
     to_float(U.val, U.val32, U.entries, stream);

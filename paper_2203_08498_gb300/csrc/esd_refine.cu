@@ -1,0 +1,179 @@
+// FP64 iterative refinement around FP32 inner PCG solves (the precision form): the FP64
+// residual, the conversion of a refinement step's right-hand side to FP32, and the FP64
+// correction x += d. The inner solve is the FP32 instantiation of the iteration kernels.
+//
+// Two forms of the step. Restart: every inner solve is a fresh PCG run on A d = r.
+// Resume (residual replacement, after van der Vorst & Ye, SIAM J. Sci. Comput. 22, 2000):
+// the inner CG state (p, rho, iteration count, sampling schedule) carries over and only the
+// residual is replaced by the FP64 one. An inner run stops right after its x, r update, so
+// the start pass of the next run is the rest of that iteration on the replaced residual:
+// z = M^-1 r, beta = (r, z) / rho, p = z + beta p. The steps together are one CG run whose
+// residual is refreshed in FP64 whenever it has dropped by inner_tol.
+#include "esd_iter.cuh"
+#include "esd_refine.h"
+
+namespace esd {
+
+// r = b - A x in FP64, ||b||^2, ||r||^2 and, after a step, ||r - r_inner||^2 (the drift of
+// the inner recursive residual r32 from the true one). The last block books the step that
+// has just been applied (st_in != NULL: its inner iterations), decides whether the next
+// resumed step must restart its direction (drift above half the residual, so the kept p no
+// longer belongs to this residual, or a step that cut the true residual by less than 10%)
+// and whether refinement goes on (stops when ||r|| <= tol ||b||, b = 0, or max_outer
+// steps are done).
+__global__ void __launch_bounds__(kBlock, 4) k_ref_residual(IterCtx<double> c, SliceSet set, double* r64,
+                                                             const float* r32, RefineState* rs, State* st_in,
+                                                             unsigned long long cond) {
+  __shared__ double red[red_size<3>()];
+  double acc[3] = {0.0, 0.0, 0.0};
+  const bool gap = st_in != nullptr;
+  ESD_LOOP_SLICES(set) {
+    int r;
+    const int s = set.slice(g, &r);
+    const int4 md = c.Av.meta[s];
+    const double ax = row_fma(c.Av, md, lane, c.x, 0.0);
+    if (lane < md.w) {
+      const int i = md.z + lane;
+      const double bi = c.b[i];
+      const double ri = bi - ax;
+      r64[i] = ri;
+      acc[0] = fma(bi, bi, acc[0]);
+      acc[1] = fma(ri, ri, acc[1]);
+      if (gap) {
+        const double di = ri - (double)r32[i];
+        acc[2] = fma(di, di, acc[2]);
+      }
+    }
+  }
+  if (grid_sum_multi<3>(acc, red, (double*)c.partials, &rs->ticket)) {
+    if (threadIdx.x == 0) {
+      if (st_in) {
+        if (rs->outer == 0) rs->first_inner = st_in->iter;
+        rs->inner_total = rs->keep ? st_in->iter : rs->inner_total + st_in->iter;
+        rs->outer += 1;
+        const double g2 = red[1] > 0.0 ? red[2] / red[1] : 0.0;
+        rs->max_gap = fmax(rs->max_gap, sqrt(g2));
+        rs->fresh = rs->keep && (g2 > 0.25 || red[1] > 0.81 * rs->rr);
+        rs->restarts += rs->fresh;
+      }
+      const double bb = red[0], rr = red[1];
+      rs->bb = bb;
+      rs->rr = rr;
+      rs->tol2bb = c.st->scal0 * bb;  // the outer tolerance^2 travels in the outer state's scal0
+      bool stop = false;
+      if (!(rr == rr)) {
+        rs->status = ESD_ERR_BREAKDOWN;
+        stop = true;
+      } else if (bb == 0.0 || rr <= rs->tol2bb) {
+        stop = true;
+      } else if (st_in && rs->keep && st_in->status != ESD_OK) {
+        // a resumed run cannot go on after its iteration limit or a breakdown
+        rs->status = st_in->status;
+        stop = true;
+      } else if (rs->outer >= rs->max_outer) {
+        rs->status = ESD_ERR_MAXIT;
+        stop = true;
+      }
+      if (stop) {
+        rs->conv = 1;
+        if (st_in && st_in->defer_sample && st_in->pend_slot >= 0) {
+          // no run follows: the last claimed slot keeps its earlier sample
+          st_in->slot_iter[st_in->pend_slot] = st_in->pend_prev;
+          st_in->pend_slot = -1;
+        }
+        if (cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, 0u);
+      }
+    }
+  }
+}
+
+// b32 = (float) r, x32 = 0; block 0 sets up the inner solve (fresh, or resumed) and opens
+// its loop. The inner tolerance is inner_tol relative to ||r||, but never tighter than half
+// of what the outer tolerance still asks for.
+__global__ void __launch_bounds__(kBlock, 4) k_ref_prep(int n, const double* r64, float* b32, float* x32,
+                                                         State* st_in, const RefineState* rs,
+                                                         unsigned long long cond_in) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    b32[i] = (float)r64[i];
+    x32[i] = 0.0f;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const bool first = rs->outer == 0;
+    const bool resume = rs->keep && !first;
+    if (!resume) {
+      st_in->iter = 0;
+      st_in->samp_m = first ? rs->samp_m : 0;
+      st_in->h = 1;
+      st_in->pend_slot = -1;
+      st_in->rho = st_in->rho_acc = st_in->fu = 0.0;
+      if (first)
+        for (int k = 0; k < kMaxM; ++k) st_in->slot_iter[k] = 0;
+    }
+    st_in->defer_sample = rs->keep;
+    st_in->fresh_dir = resume && rs->fresh;
+    st_in->conv = 0;
+    st_in->status = ESD_OK;
+    st_in->zero_rhs = 0;
+    st_in->guard = 0;
+    st_in->maxit = rs->inner_maxit;
+    st_in->lmax = rs->lmax;
+    st_in->scal0 = fmax(rs->inner_tol2, 0.25 * rs->tol2bb / rs->rr);
+    cudaGraphSetConditional((cudaGraphConditionalHandle)cond_in, 1u);
+  }
+}
+
+// x += (double) d
+__global__ void __launch_bounds__(kBlock, 4) k_ref_apply(int n, double* x64, const float* x32) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x64[i] += (double)x32[i];
+}
+
+void launch_ref_residual(const IterCtx<double>& c, double* r64, const float* r32, RefineState* rs, State* st_in,
+                         unsigned long long cond, cudaStream_t s) {
+  const SliceSet& all = c.A->all;
+  k_ref_residual<<<grid_for(k_ref_residual, all.total()), kBlock, 0, s>>>(c, all, r64, r32, rs, st_in, cond);
+  ESD_CUDA(cudaGetLastError());
+}
+
+void launch_ref_prep(int n, const double* r64, float* b32, float* x32, State* st_in, const RefineState* rs,
+                     unsigned long long cond_in, cudaStream_t s) {
+  k_ref_prep<<<max_grid_blocks(), kBlock, 0, s>>>(n, r64, b32, x32, st_in, rs, cond_in);
+  ESD_CUDA(cudaGetLastError());
+}
+
+void launch_ref_apply(int n, double* x64, const float* x32, cudaStream_t s) {
+  k_ref_apply<<<max_grid_blocks(), kBlock, 0, s>>>(n, x64, x32);
+  ESD_CUDA(cudaGetLastError());
+}
+
+__global__ void k_d2f(long long cnt, const double* a, float* b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cnt; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+__global__ void k_f2d(long long cnt, const float* a, double* b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cnt; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+
+__global__ void k_round_f32(long long cnt, const double* a, double* b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cnt; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (double)(float)a[i];
+}
+
+void round_to_f32(long long cnt, const double* a, double* b, cudaStream_t s) {
+  if (cnt <= 0) return;
+  k_round_f32<<<max_grid_blocks(), kBlock, 0, s>>>(cnt, a, b);
+  ESD_CUDA(cudaGetLastError());
+}
+
+void convert_d2f(long long cnt, const double* a, float* b, cudaStream_t s) {
+  if (cnt <= 0) return;
+  k_d2f<<<max_grid_blocks(), kBlock, 0, s>>>(cnt, a, b);
+  ESD_CUDA(cudaGetLastError());
+}
+void convert_f2d(long long cnt, const float* a, double* b, cudaStream_t s) {
+  if (cnt <= 0) return;
+  k_f2d<<<max_grid_blocks(), kBlock, 0, s>>>(cnt, a, b);
+  ESD_CUDA(cudaGetLastError());
+}
+
+}  // namespace esd

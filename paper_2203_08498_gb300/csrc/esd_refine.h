@@ -1,0 +1,16 @@
+// Launchers of the FP64 refinement kernels (esd_refine.cu).
+#pragma once
+
+#include "esd_iter.h"
+
+namespace esd {
+void launch_ref_residual(const IterCtx<double>& c, double* r64, const float* r32, RefineState* rs, State* st_in,
+                         unsigned long long cond, cudaStream_t s);
+void launch_ref_prep(int n, const double* r64, float* b32, float* x32, State* st_in, const RefineState* rs,
+                     unsigned long long cond_in, cudaStream_t s);
+void launch_ref_apply(int n, double* x64, const float* x32, cudaStream_t s);
+void convert_d2f(long long cnt, const double* a, float* b, cudaStream_t s);
+// b = a rounded to the nearest FP32 value (kept in FP64)
+void round_to_f32(long long cnt, const double* a, double* b, cudaStream_t s);
+void convert_f2d(long long cnt, const float* a, double* b, cudaStream_t s);
+}  // namespace esd

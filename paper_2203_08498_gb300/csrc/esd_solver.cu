@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "esd_dense.h"
+#include "esd_refine.h"
 
 namespace esd {
 
@@ -95,6 +96,30 @@ __global__ void k_pattern_grad(int n, const int* rp, const int* ci, const double
   }
 }
 
+// Add a conditional while node after the current dependencies of the capture on stream s
+// (whatever graph s captures into) and return its body graph.
+static cudaGraph_t add_while_node(cudaStream_t s, cudaGraphConditionalHandle h) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  ESD_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, nullptr, &nd));
+  cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  ESD_CUDA(cudaGraphAddNode(&wnode, cg, deps, nullptr, nd, &np));
+  ESD_CUDA(cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return np.conditional.phGraph_out[0];
+}
+
+// b = 0 gives x = 0 (refinement form)
+__global__ void k_ref_final(int n, double* x, const RefineState* rs) {
+  if (rs->bb != 0.0) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = 0.0;
+}
+
 }  // namespace esd
 
 using namespace esd;
@@ -105,11 +130,18 @@ struct esd_solver {
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;   // private capture streams
   cudaStream_t cap2 = nullptr;
+  cudaStream_t cap3 = nullptr;
   int mode = ESD_PLAIN;
   size_t ld = 0;
   DevBuf vb, vx, vr, vp, vq, vY, samples;
   DevBuf W, AW, E, Einv, ritz, ahist, bhist, state, partials, rho_part, ext;
   State* hst = nullptr;  // pinned host copy
+  // FP32-inner / FP64-refinement form
+  bool fp32 = false;
+  DevBuf b32, x32, r32, p32, q32, Y32, W32, AW32, r64, state_in, rstate;
+  State* hst_in = nullptr;      // pinned copy of the inner state
+  RefineState* hrs = nullptr;   // pinned copy of the refinement state
+  int last_outer = 0;
   int m = 0, M = 0;      // columns of W, padded count
   int mbar = 0;
   bool have_W = false;
@@ -125,7 +157,46 @@ struct esd_solver {
       if (e) cudaGraphExecDestroy(e);
     if (cap) cudaStreamDestroy(cap);
     if (cap2) cudaStreamDestroy(cap2);
+    if (cap3) cudaStreamDestroy(cap3);
     if (hst) cudaFreeHost(hst);
+    if (hst_in) cudaFreeHost(hst_in);
+    if (hrs) cudaFreeHost(hrs);
+  }
+
+  IterCtx<float> ctx32(int md) const {
+    IterCtx<float> c;
+    c.A = A;
+    c.Av = A->A.view<float>();
+    c.Lv = A->L.view<float>();
+    c.Uv = A->U.view<float>();
+    c.inv_d = A->inv_d32.as<float>();
+    c.rowsum = A->rowsum32.as<float>();
+    c.b = b32.as<float>();
+    c.x = x32.as<float>();
+    c.r = r32.as<float>();
+    c.p = p32.as<float>();
+    c.q = q32.as<float>();
+    c.Y = Y32.as<float>();
+    c.ld = ld;
+    c.mode = md;
+    c.pre = prm.precond;
+    if (md != ESD_PLAIN) {
+      c.W = W32.as<float>();
+      c.AW = AW32.as<float>();
+      c.Einv = Einv.as<double>();
+      c.M = M;
+    }
+    c.samples = nullptr;
+    c.samples64 = samples.get() ? samples.as<double>() : nullptr;  // FP64 full iterates
+    c.xbase = vx.as<double>();
+    c.ahist = ahist.as<double>();
+    c.bhist = bhist.as<double>();
+    c.partials = partials.get();
+    c.rho_part = rho_part.get();
+    c.rho_stride = (size_t)max_grid_blocks();
+    c.st = state_in.as<State>();
+    c.sflags = A->slice_flags.as<unsigned char>();
+    return c;
   }
 
   IterCtx<double> ctx(int md) const {
@@ -169,6 +240,22 @@ struct esd_solver {
     }
     cudaGraph_t g;
     ESD_CUDA(cudaGraphCreate(&g, 0));
+    try {
+      if (fp32) capture_refine(g, md); else capture_fp64(g, md);
+    } catch (...) {
+      cudaGraphDestroy(g);
+      throw;
+    }
+    cudaGraphExec_t e;
+    cudaError_t err = cudaGraphInstantiate(&e, g, 0);
+    cudaGraphDestroy(g);
+    ESD_CUDA(err);
+    exec[md] = e;
+    exec_version[md] = w_version;
+  }
+
+  // r0, z0, p0 -> while (not stopped) { PCG iteration } -> correction, true residual
+  void capture_fp64(cudaGraph_t g, int md) {
     cudaGraphConditionalHandle h;
     ESD_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
     IterCtx<double> c = ctx(md);
@@ -176,18 +263,7 @@ struct esd_solver {
     ESD_CUDA(cudaStreamBeginCaptureToGraph(cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     try {
       launch_init<double>(c, cap);
-      cudaStreamCaptureStatus cs;
-      const cudaGraphNode_t* deps = nullptr;
-      size_t nd = 0;
-      ESD_CUDA(cudaStreamGetCaptureInfo(cap, &cs, nullptr, nullptr, &deps, nullptr, &nd));
-      cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
-      np.conditional.handle = h;
-      np.conditional.type = cudaGraphCondTypeWhile;
-      np.conditional.size = 1;
-      cudaGraphNode_t wnode;
-      ESD_CUDA(cudaGraphAddNode(&wnode, g, deps, nullptr, nd, &np));
-      cudaGraph_t body = np.conditional.phGraph_out[0];
-      ESD_CUDA(cudaStreamUpdateCaptureDependencies(cap, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+      cudaGraph_t body = add_while_node(cap, h);
       ESD_CUDA(cudaStreamBeginCaptureToGraph(cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
       try {
         launch_iteration<double>(c, cap2);
@@ -202,16 +278,72 @@ struct esd_solver {
     } catch (...) {
       cudaGraph_t dummy;
       cudaStreamEndCapture(cap, &dummy);
-      cudaGraphDestroy(g);
       throw;
     }
     ESD_CUDA(cudaStreamEndCapture(cap, &g));
-    cudaGraphExec_t e;
-    cudaError_t err = cudaGraphInstantiate(&e, g, 0);
-    cudaGraphDestroy(g);
-    ESD_CUDA(err);
-    exec[md] = e;
-    exec_version[md] = w_version;
+  }
+
+  // FP64 residual -> while (not converged) { b32 = r; FP32 PCG (its own while loop);
+  // x += d; FP64 residual } -> x = 0 when b = 0
+  void capture_refine(cudaGraph_t g, int md) {
+    cudaGraphConditionalHandle h_out, h_in;
+    ESD_CUDA(cudaGraphConditionalHandleCreate(&h_out, g, 1, cudaGraphCondAssignDefault));
+    IterCtx<double> c64 = ctx(ESD_PLAIN);
+    IterCtx<float> c32 = ctx32(md);
+    c32.x_zero = 1;  // every inner solve starts from d = 0
+    RefineState* rs = rstate.as<RefineState>();
+    const int n = A->n;
+    ESD_CUDA(cudaStreamBeginCaptureToGraph(cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    try {
+      launch_ref_residual(c64, r64.as<double>(), r32.as<float>(), rs, nullptr, (unsigned long long)h_out, cap);
+      cudaGraph_t body = add_while_node(cap, h_out);
+      // the inner loop's handle belongs to the graph that holds the inner while node
+      ESD_CUDA(cudaGraphConditionalHandleCreate(&h_in, body, 0, 0));
+      c32.cond = (unsigned long long)h_in;
+      ESD_CUDA(cudaStreamBeginCaptureToGraph(cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+      try {
+        launch_ref_prep(n, r64.as<double>(), b32.as<float>(), x32.as<float>(), state_in.as<State>(), rs,
+                        (unsigned long long)h_in, cap2);
+        launch_init<float>(c32, cap2);
+        cudaGraph_t inner = add_while_node(cap2, h_in);
+        ESD_CUDA(cudaStreamBeginCaptureToGraph(cap3, inner, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        try {
+          launch_iteration<float>(c32, cap3);
+        } catch (...) {
+          cudaGraph_t dummy;
+          cudaStreamEndCapture(cap3, &dummy);
+          throw;
+        }
+        ESD_CUDA(cudaStreamEndCapture(cap3, &inner));
+        launch_finish<float>(c32, cap2);
+        launch_ref_apply(n, vx.as<double>(), x32.as<float>(), cap2);
+        launch_ref_residual(c64, r64.as<double>(), r32.as<float>(), rs, state_in.as<State>(),
+                            (unsigned long long)h_out, cap2);
+      } catch (...) {
+        cudaGraph_t dummy;
+        cudaStreamEndCapture(cap2, &dummy);
+        throw;
+      }
+      ESD_CUDA(cudaStreamEndCapture(cap2, &body));
+      k_ref_final<<<max_grid_blocks(), kBlock, 0, cap>>>(n, vx.as<double>(), rs);
+      ESD_CUDA(cudaGetLastError());
+    } catch (...) {
+      cudaGraph_t dummy;
+      cudaStreamEndCapture(cap, &dummy);
+      throw;
+    }
+    ESD_CUDA(cudaStreamEndCapture(cap, &g));
+  }
+
+  // FP32 copies of W and AW for the inner solves
+  void refresh_w32() {
+    if (!fp32 || !have_W) return;
+    if (!W32.get()) {
+      W32.alloc(sizeof(float) * ld * kMaxM);
+      AW32.alloc(sizeof(float) * ld * kMaxM);
+    }
+    convert_d2f((long long)ld * M, W.as<double>(), W32.as<float>(), stream);
+    convert_d2f((long long)ld * M, AW.as<double>(), AW32.as<float>(), stream);
   }
 };
 
@@ -238,6 +370,52 @@ static int smallest_lmax(int m, int maxit) {
     return ESD_ERR_INVALID;          \
   }
 
+// The refinement form of esd_solve (b and x already copied into vb / vx).
+static int solve_refine(esd_solver* S, double* x, double tol, int32_t maxit, int32_t sample_m, int32_t* iters,
+                        double* relres) {
+  cudaStream_t s = S->stream;
+  const int n = S->A->n;
+  State* h = S->hst;
+  std::memset(h, 0, sizeof(State));
+  h->scal0 = tol * tol;
+  ESD_CUDA(cudaMemcpyAsync(S->state.get(), h, sizeof(State), cudaMemcpyHostToDevice, s));
+  RefineState* hr = S->hrs;
+  std::memset(hr, 0, sizeof(RefineState));
+  hr->max_outer = S->prm.max_outer;
+  hr->inner_maxit = maxit;
+  hr->samp_m = sample_m;
+  hr->lmax = S->prm.lmax > 0 ? S->prm.lmax : smallest_lmax(sample_m, maxit);
+  hr->inner_tol2 = S->prm.inner_tol * S->prm.inner_tol;
+  hr->keep = S->prm.resume_direction ? 1 : 0;
+  ESD_CUDA(cudaMemcpyAsync(S->rstate.get(), hr, sizeof(RefineState), cudaMemcpyHostToDevice, s));
+  ESD_CUDA(cudaGraphLaunch(S->exec[S->mode], s));
+  copy_out(S->vx.get(), x, sizeof(double) * n, s);
+  ESD_CUDA(cudaMemcpyAsync(hr, S->rstate.get(), sizeof(RefineState), cudaMemcpyDeviceToHost, s));
+  ESD_CUDA(cudaMemcpyAsync(S->hst_in, S->state_in.get(), sizeof(State), cudaMemcpyDeviceToHost, s));
+  ESD_CUDA(cudaStreamSynchronize(s));
+  // coefficients of the whole resumed run, or of the last restarted inner solve
+  S->last_iters = hr->outer > 0 ? S->hst_in->iter : 0;
+  S->last_status = hr->status;
+  S->last_sample_m = sample_m;
+  S->last_maxit = maxit;
+  S->last_outer = hr->outer;
+  S->last_relres = hr->bb > 0.0 ? std::sqrt(hr->rr / hr->bb) : 0.0;
+  S->last_true = S->last_relres;
+  // slot_iter of the sampled (first) inner solve stays in the inner state
+  std::memcpy(S->hst->slot_iter, S->hst_in->slot_iter, sizeof(S->hst->slot_iter));
+  if (iters) *iters = hr->inner_total;
+  if (relres) *relres = S->last_relres;
+  if (hr->status == ESD_ERR_MAXIT) {
+    set_last_error("refinement did not reach the tolerance within max_outer steps");
+    return ESD_ERR_MAXIT;
+  }
+  if (hr->status == ESD_ERR_BREAKDOWN) {
+    set_last_error("non-finite residual in the refinement");
+    return ESD_ERR_BREAKDOWN;
+  }
+  return ESD_OK;
+}
+
 extern "C" {
 
 void esd_params_default(esd_params* p) {
@@ -249,8 +427,9 @@ void esd_params_default(esd_params* p) {
   p->lmax = 0;
   p->rank_tol = 1e-12;
   p->precision = ESD_FP64;
-  p->inner_tol = 1e-4;
-  p->max_outer = 30;
+  p->inner_tol = 0.3;
+  p->max_outer = 60;
+  p->resume_direction = 1;
 }
 
 int esd_solver_create(esd_matrix* A, const esd_params* params, esd_solver** out) {
@@ -262,7 +441,9 @@ int esd_solver_create(esd_matrix* A, const esd_params* params, esd_solver** out)
   ESD_CHECK(p.precond == ESD_PRECOND_NONE || p.precond == ESD_PRECOND_IC0, ESD_ERR_INVALID, "bad precond");
   ESD_CHECK(p.maxit_cap >= 1, ESD_ERR_INVALID, "maxit_cap must be >= 1");
   ESD_CHECK(p.sample_cap >= 0 && p.sample_cap <= kMaxM, ESD_ERR_INVALID, "sample_cap must be 0..64");
-  ESD_CHECK(p.precision == ESD_FP64, ESD_ERR_INVALID, "this build solves in FP64 only");
+  ESD_CHECK(p.precision == ESD_FP64 || p.precision == ESD_FP32_REFINE, ESD_ERR_INVALID, "unknown precision");
+  ESD_CHECK(p.precision == ESD_FP64 || (p.inner_tol > 0.0 && p.inner_tol < 1.0 && p.max_outer >= 1),
+            ESD_ERR_INVALID, "refinement needs 0 < inner_tol < 1 and max_outer >= 1");
   ESD_CHECK(p.precond == ESD_PRECOND_NONE || A->factored, ESD_ERR_STATE, "IC(0) preconditioner needs esd_factor_ic0");
   std::unique_ptr<esd_solver> S(new esd_solver());
   S->A = A;
@@ -283,7 +464,7 @@ int esd_solver_create(esd_matrix* A, const esd_params* params, esd_solver** out)
   S->state.alloc(sizeof(State));
   ESD_CUDA(cudaMemsetAsync(S->state.get(), 0, sizeof(State), S->stream));
   S->partials.alloc(sizeof(double) * (size_t)max_grid_blocks() * kMaxRed);
-  S->rho_part.alloc(sizeof(double) * (size_t)max_grid_blocks() * kMaxRanges);
+  S->rho_part.alloc(sizeof(double) * (size_t)max_grid_blocks() * kMaxColours);
   S->E.alloc(sizeof(double) * kMaxM * kMaxM);
   S->Einv.alloc(sizeof(double) * kMaxM * kMaxM);
   S->ritz.alloc(sizeof(double) * kMaxM);
@@ -292,6 +473,26 @@ int esd_solver_create(esd_matrix* A, const esd_params* params, esd_solver** out)
   std::memset(S->hst, 0, sizeof(State));
   ESD_CUDA(cudaStreamCreateWithFlags(&S->cap, cudaStreamNonBlocking));
   ESD_CUDA(cudaStreamCreateWithFlags(&S->cap2, cudaStreamNonBlocking));
+  ESD_CUDA(cudaStreamCreateWithFlags(&S->cap3, cudaStreamNonBlocking));
+  if (p.precision == ESD_FP32_REFINE) {
+    S->fp32 = true;
+    const size_t fbytes = sizeof(float) * S->ld;
+    for (DevBuf* b : {&S->b32, &S->x32, &S->r32, &S->p32, &S->q32, &S->Y32}) {
+      b->alloc(fbytes);
+      ESD_CUDA(cudaMemsetAsync(b->get(), 0, fbytes, S->stream));
+    }
+    S->r64.alloc(vbytes);
+    ESD_CUDA(cudaMemsetAsync(S->r64.get(), 0, vbytes, S->stream));
+    S->state_in.alloc(sizeof(State));
+    ESD_CUDA(cudaMemsetAsync(S->state_in.get(), 0, sizeof(State), S->stream));
+    S->rstate.alloc(sizeof(RefineState));
+    ESD_CUDA(cudaMemsetAsync(S->rstate.get(), 0, sizeof(RefineState), S->stream));
+    ESD_CUDA(cudaMallocHost(&S->hst_in, sizeof(State)));
+    ESD_CUDA(cudaMallocHost(&S->hrs, sizeof(RefineState)));
+    std::memset(S->hst_in, 0, sizeof(State));
+    std::memset(S->hrs, 0, sizeof(RefineState));
+    A->ensure_fp32();
+  }
   ESD_CUDA(cudaStreamSynchronize(S->stream));
   *out = S.release();
   return ESD_OK;
@@ -329,9 +530,11 @@ int esd_solve(esd_solver* S, const double* b, double* x, double tol, int32_t max
   ESD_CHECK(sample_m != 1, ESD_ERR_INVALID, "sampling method A needs m >= 2");
   cudaStream_t s = S->stream;
   const int n = S->A->n;
+  if (S->fp32) S->A->ensure_fp32();
   S->build_graph(S->mode);
   copy_in(b, S->vb.get(), sizeof(double) * n, s);
   copy_in(x, S->vx.get(), sizeof(double) * n, s);
+  if (S->fp32) return solve_refine(S, x, tol, maxit, sample_m, iters, relres);
   State* h = S->hst;
   std::memset(h, 0, sizeof(State));
   h->scal0 = tol * tol;
@@ -387,12 +590,24 @@ static void install_W(esd_solver* S, const double* X, int m, bool orth, double t
   const int mkeep = build_aux(S->A, S->aux, X, m, orth, S->prm.rank_tol, theta, S->W.as<double>(),
                               S->AW.as<double>(), S->E.as<double>(), S->Einv.as<double>(),
                               S->ritz.as<double>(), &mbar, S->stream);
+  if (S->fp32) {
+    // The inner solves see W rounded to FP32. AW, E and E^-1 are formed again (in FP64) for
+    // exactly that W, so that the FP64 coarse solve and the FP32 projection describe the
+    // same subspace; otherwise E^-1 is off by eps32 * cond(E) for the FP32 W.
+    round_to_f32((long long)ld * mkeep, S->W.as<double>(), S->aux.work1.as<double>(), S->stream);
+    int unused = 0;
+    build_aux(S->A, S->aux, S->aux.work1.as<double>(), mkeep, false, S->prm.rank_tol,
+              std::numeric_limits<double>::infinity(), S->W.as<double>(), S->AW.as<double>(),
+              S->E.as<double>(), S->Einv.as<double>(), S->ritz.as<double>(), &unused, S->stream);
+  }
   ESD_CUDA(cudaStreamSynchronize(S->stream));
   S->m = mkeep;
   S->M = pad_cols(mkeep);
   S->mbar = mbar;
   S->have_W = true;
   S->w_version++;
+  S->refresh_w32();
+  ESD_CUDA(cudaStreamSynchronize(S->stream));
 }
 
 int esd_sample_and_build_W(esd_solver* S, double theta, int32_t* m_kept) {
@@ -408,6 +623,7 @@ int esd_sample_and_build_W(esd_solver* S, double theta, int32_t* m_kept) {
   S->aux.ensure(S->A->n, S->ld);
   DevBuf dslots(sizeof(int) * m);
   ESD_CUDA(cudaMemcpyAsync(dslots.get(), slots.data(), sizeof(int) * m, cudaMemcpyHostToDevice, S->stream));
+  // (the refinement form stores FP64 iterates too: its FP64 base plus the inner iterate)
   k_errors<<<max_grid_blocks(), kBlock, 0, S->stream>>>(S->A->n, S->vx.as<double>(), S->samples.as<double>(),
                                                         S->ld, dslots.as<int>(), m, S->aux.work1.as<double>());
   ESD_CUDA(cudaGetLastError());
@@ -546,12 +762,27 @@ int esd_profile_iterations(esd_solver* S, const double* b, double* x, int32_t re
   h->h = 1;
   h->pend_slot = -1;
   ESD_CUDA(cudaMemcpyAsync(S->state.get(), h, sizeof(State), cudaMemcpyHostToDevice, s));
-  IterCtx<double> c = S->ctx(S->mode);
-  launch_init<double>(c, s);
   std::vector<std::unique_ptr<KernelMarks>> marks;
-  for (int r = 0; r < reps; ++r) {
-    marks.emplace_back(new KernelMarks());
-    launch_iteration<double>(c, s, marks.back().get());
+  if (S->fp32) {
+    // the FP32 inner iteration on the system A d = b
+    S->A->ensure_fp32();
+    ESD_CUDA(cudaMemcpyAsync(S->state_in.get(), h, sizeof(State), cudaMemcpyHostToDevice, s));
+    convert_d2f(n, S->vb.as<double>(), S->b32.as<float>(), s);
+    convert_d2f(n, S->vx.as<double>(), S->x32.as<float>(), s);
+    IterCtx<float> c = S->ctx32(S->mode);
+    launch_init<float>(c, s);
+    for (int r = 0; r < reps; ++r) {
+      marks.emplace_back(new KernelMarks());
+      launch_iteration<float>(c, s, marks.back().get());
+    }
+    convert_f2d(n, S->x32.as<float>(), S->vx.as<double>(), s);
+  } else {
+    IterCtx<double> c = S->ctx(S->mode);
+    launch_init<double>(c, s);
+    for (int r = 0; r < reps; ++r) {
+      marks.emplace_back(new KernelMarks());
+      launch_iteration<double>(c, s, marks.back().get());
+    }
   }
   copy_out(S->vx.get(), x, sizeof(double) * n, s);
   ESD_CUDA(cudaStreamSynchronize(s));
@@ -572,6 +803,19 @@ int esd_profile_iterations(esd_solver* S, const double* b, double* x, int32_t re
   }
   return ESD_OK;
   ESD_API_END
+}
+
+int esd_last_solve_info(esd_solver* S, int32_t* iters, int32_t* outer_steps, int32_t* first_inner,
+                        int32_t* restarts, double* max_gap, double* true_relres, int32_t* status) {
+  if (!S) { set_last_error("NULL solver"); return ESD_ERR_INVALID; }
+  if (iters) *iters = S->fp32 ? S->hrs->inner_total : S->last_iters;
+  if (outer_steps) *outer_steps = S->fp32 ? S->last_outer : 0;
+  if (first_inner) *first_inner = S->fp32 ? S->hrs->first_inner : S->last_iters;
+  if (restarts) *restarts = S->fp32 ? S->hrs->restarts : 0;
+  if (max_gap) *max_gap = S->fp32 ? S->hrs->max_gap : 0.0;
+  if (true_relres) *true_relres = S->last_true;
+  if (status) *status = S->last_status;
+  return ESD_OK;
 }
 
 int esd_pattern_grad(esd_matrix* A, const double* lambda, const double* x, double* grad) {
