@@ -100,6 +100,45 @@ int esd_factor_ic0(esd_matrix* A, int32_t max_tries, double* shift_used);
 /* y = A x (device or host arrays of n doubles). */
 int esd_matrix_spmv(esd_matrix* A, const double* x, double* y);
 
+/*
+ * New values for A on the pattern given at creation (nnz doubles in that CSR order, host or
+ * device). The IC(0) factor is dropped (call esd_factor_ic0 again) and a W built for the
+ * old values goes stale (esd_refresh_W); solves refuse to run on either until then.
+ */
+int esd_matrix_set_values(esd_matrix* A, const double* val);
+
+/*
+ * Cell-centred finite-volume diffusion on a structured grid with per-cell coefficient
+ * k_c = exp(theta_c): A = inv_dt I + K(theta). An interior face between cells a and b
+ * carries T = 2 k_a k_b / (k_a + k_b) / h^2 (harmonic mean) on both diagonals and -T off
+ * them; a face on the boundary (Dirichlet) adds 2 k_c / h^2 to the diagonal. Cells are in
+ * natural order c = ix + nx (iy + ny iz); cell_row[c] is the matrix row of cell c (the
+ * colour-major permutation of the pattern). dims = 2 ignores nz.
+ */
+typedef struct {
+  int32_t dims;
+  int32_t nx, ny, nz;
+  double h;       /* cell size */
+  double inv_dt;  /* 1/dt of backward Euler, 0 for the steady operator */
+} esd_fv_grid;
+
+/* Assemble A(theta) on the device into A's values (the pattern must hold the stencil);
+ * like esd_matrix_set_values it drops the factor. theta[n], cell_row[n]: host or device.
+ * Errors: ESD_ERR_INVALID for a grid that does not match A, a row index outside 0..n-1 or a
+ * missing stencil entry (A is then left unchanged). */
+int esd_fv_assemble(esd_matrix* A, const esd_fv_grid* g, const double* theta, const int32_t* cell_row);
+
+/*
+ * Adjoint gradient of L(x(theta)) for A(theta) x = b: given x and lambda, the solution of the
+ * adjoint system A lambda = dL/dx (A is symmetric, so it is one more solve with the same
+ * matrix, mode and W), grad_theta[c] = dL/dtheta_c = k_c sum over the faces of c of
+ * dL/dT dT/dk_c, with dL/dT = -(lambda_a - lambda_b)(x_a - x_b) on interior faces and
+ * -lambda_c x_c 2/h^2 per boundary face. lambda, x: matrix order; theta, grad_theta: natural
+ * cell order. dL/db = lambda needs no call. Host or device arrays.
+ */
+int esd_fv_grad_theta(esd_matrix* A, const esd_fv_grid* g, const double* theta, const int32_t* cell_row,
+                      const double* lambda, const double* x, double* grad_theta);
+
 /* z = (L L^T)^{-1} r by colour-ordered forward and backward substitution
  * (requires esd_factor_ic0). */
 int esd_matrix_apply_ic(esd_matrix* A, const double* r, double* z);
@@ -202,6 +241,10 @@ int esd_sample_and_build_W(esd_solver* S, double theta, int32_t* m_kept);
 /* Use a caller-supplied W (n x m column-major doubles, device or host, 1 <= m <= 64,
  * columns linearly independent); AW, E and E^{-1} are built as above. */
 int esd_set_W(esd_solver* S, const double* W, int32_t m);
+
+/* AW, E = W^T A W, E^-1 and the Ritz values formed again for the current W and the current
+ * values of A (after esd_matrix_set_values / esd_fv_assemble). ESD_ERR_STATE without W. */
+int esd_refresh_W(esd_solver* S);
 
 /* Copy W, AW (n x m column-major) and E (m x m row-major) out; any pointer may be NULL. */
 int esd_get_W(esd_solver* S, double* W, double* AW, double* E, int32_t* m);

@@ -353,3 +353,86 @@ def run_sequence(prob, T: int, mode: int, m: int, tol: float = 1e-8, maxit: int 
         res.append(dict(iters=out["iters"], relres=out["relres"], status=out["status"], x=x.copy(),
                         alpha=out["alpha"], beta=out["beta"]))
     return res, aux
+
+
+# ------------------------------------------------------------------ adjoint gradient
+#
+# Not part of the paper's method: the differentiation form built on it. For A(theta) x = b
+# and a loss L(x), the adjoint lambda solves A^T lambda = dL/dx (A is symmetric, so this is
+# one more system with the same matrix: it can reuse W and E); then dL/db = lambda and
+# dL/da_ij = -lambda_i x_j on the pattern. The functions below carry that through the
+# finite-volume assembly of the workloads (harmonic-mean faces, Dirichlet boundaries,
+# k = exp(theta)) by the chain rule, face by face.
+
+def _face_dT_dka(ka, kb, inv_h2):
+    """d/dk_a of T = 2 k_a k_b / (k_a + k_b) / h^2."""
+    return 2.0 * kb * kb / ((ka + kb) * (ka + kb)) * inv_h2
+
+
+def _face_dL_dT(lam_a, lam_b, x_a, x_b):
+    """dL/dT of one interior face: the sum of -lambda_i x_j over its four entries
+    (+T at (a,a) and (b,b), -T at (a,b) and (b,a))."""
+    return -(lam_a - lam_b) * (x_a - x_b)
+
+
+def _boundary_dL_dk(lam_c, x_c, inv_h2):
+    """A Dirichlet face adds 2 k_c / h^2 at (c, c): dL/dk_c = -lambda_c x_c 2 / h^2."""
+    return -lam_c * x_c * 2.0 * inv_h2
+
+
+def fv_theta_gradient(theta, h: float, lam, x):
+    """dL/dtheta for the cell-centred FV operator A = I/dt + K(exp(theta)).
+
+    ``theta``, ``lam`` and ``x`` are arrays of the grid's shape (axis 0 = x); the I/dt term
+    does not depend on theta. Returns an array of the same shape.
+    """
+    theta = np.asarray(theta, dtype=np.float64)
+    k = np.exp(theta)
+    inv_h2 = 1.0 / (h * h)
+    g = np.zeros_like(k)
+    for ax in range(k.ndim):
+        n_ax = k.shape[ax]
+        lo = [slice(None)] * k.ndim
+        hi = [slice(None)] * k.ndim
+        lo[ax] = slice(0, n_ax - 1)
+        hi[ax] = slice(1, n_ax)
+        lo, hi = tuple(lo), tuple(hi)
+        dLdT = _face_dL_dT(lam[lo], lam[hi], x[lo], x[hi])
+        g[lo] += dLdT * _face_dT_dka(k[lo], k[hi], inv_h2)
+        g[hi] += dLdT * _face_dT_dka(k[hi], k[lo], inv_h2)
+        first = [slice(None)] * k.ndim
+        last = [slice(None)] * k.ndim
+        first[ax] = slice(0, 1)
+        last[ax] = slice(n_ax - 1, n_ax)
+        first, last = tuple(first), tuple(last)
+        g[first] += _boundary_dL_dk(lam[first], x[first], inv_h2)
+        g[last] += _boundary_dL_dk(lam[last], x[last], inv_h2)
+    return k * g
+
+
+def to_grid(prob, v):
+    """Matrix-ordered vector -> array of the grid's shape (natural order, axis 0 = x)."""
+    nat = np.empty(prob.n)
+    nat[prob.perm] = v
+    return nat.reshape(prob.shape, order="F")
+
+
+def from_grid(prob, a):
+    """Array of the grid's shape -> matrix-ordered vector."""
+    return np.asarray(a).ravel(order="F")[prob.perm]
+
+
+def adjoint_gradient(prob, theta, b, x_target, tol: float = 1e-13, maxit: int = 20000, mode: int = PLAIN,
+                     aux: "Aux | None" = None):
+    """Loss L = ||x - x_target||^2 with A(theta) x = b: forward ICCG, adjoint ICCG on
+    A lambda = 2 (x - x_target) (same mode and auxiliary matrix), then dL/db = lambda and
+    dL/dtheta by ``fv_theta_gradient``. ``prob`` is A(theta) with its ordering; vectors
+    are in matrix order, theta and the returned grad_theta in grid shape."""
+    ic = IC0(prob)
+    sysm = System(prob, ic, mode, aux)
+    x = sysm.solve(b, tol=tol, maxit=maxit, history=False)["x"]
+    g = 2.0 * (x - x_target)
+    lam = sysm.solve(g, tol=tol, maxit=maxit, history=False)["x"]
+    grad_theta = fv_theta_gradient(theta, prob.h, to_grid(prob, lam), to_grid(prob, x))
+    return {"x": x, "lambda": lam, "grad_b": lam, "grad_theta": grad_theta,
+            "loss": float(np.dot(x - x_target, x - x_target))}

@@ -28,7 +28,8 @@ __all__ = [
     "esd_sample_and_build_W",
     "esd_set_W", "esd_get_W", "esd_ritz_values", "esd_estimate_cond", "esd_get_history",
     "esd_get_samples", "esd_backward_euler_rhs", "esd_profile_iterations", "esd_last_error",
-    "esd_lanczos_extremes_noalloc", "NOALLOC_MAX_K",
+    "esd_lanczos_extremes_noalloc", "NOALLOC_MAX_K", "esd_matrix_set_values", "esd_fv_assemble",
+    "esd_fv_grad_theta", "esd_refresh_W", "EsdFvGrid",
 ]
 NOALLOC_MAX_K = 32768
 
@@ -55,6 +56,11 @@ class EsdError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"[{code}] {msg}")
         self.code = code
+
+
+class EsdFvGrid(C.Structure):
+    _fields_ = [("dims", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("h", C.c_double), ("inv_dt", C.c_double)]
 
 
 class EsdParams(C.Structure):
@@ -102,6 +108,10 @@ def lib(build_if_missing: bool = True):
             "esd_backward_euler_rhs": (i32, [vp, vp, vp, f64, vp]),
             "esd_profile_iterations": (i32, [vp, vp, vp, i32, vp, vp, i32, P(i32)]),
             "esd_lanczos_extremes_noalloc": (i32, [vp, vp, i32, vp, vp]),
+            "esd_matrix_set_values": (i32, [vp, vp]),
+            "esd_fv_assemble": (i32, [vp, P(EsdFvGrid), vp, vp]),
+            "esd_fv_grad_theta": (i32, [vp, P(EsdFvGrid), vp, vp, vp, vp, vp]),
+            "esd_refresh_W": (i32, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -200,6 +210,28 @@ def esd_matrix_apply_ic(h, r, z):
 
 def esd_pattern_grad(h, lam, x, grad):
     _check(lib().esd_pattern_grad(h, _ptr(lam), _ptr(x), _ptr(grad)))
+
+
+def esd_matrix_set_values(h, val):
+    _dtype_ok(val, "f64")
+    _check(lib().esd_matrix_set_values(h, _ptr(val)))
+
+
+def esd_fv_assemble(h, grid: EsdFvGrid, theta, cell_row):
+    _dtype_ok(theta, "f64"), _dtype_ok(cell_row, "i32")
+    _check(lib().esd_fv_assemble(h, C.byref(grid), _ptr(theta), _ptr(cell_row)))
+
+
+def esd_fv_grad_theta(h, grid: EsdFvGrid, theta, cell_row, lam, x, grad_theta):
+    for a in (theta, lam, x, grad_theta):
+        _dtype_ok(a, "f64")
+    _dtype_ok(cell_row, "i32")
+    _check(lib().esd_fv_grad_theta(h, C.byref(grid), _ptr(theta), _ptr(cell_row), _ptr(lam), _ptr(x),
+                                   _ptr(grad_theta)))
+
+
+def esd_refresh_W(h):
+    _check(lib().esd_refresh_W(h))
 
 
 def esd_params_default():
@@ -358,6 +390,9 @@ class Matrix:
     def pattern_grad(self, lam, x, grad):
         esd_pattern_grad(self._h, lam, x, grad)
 
+    def set_values(self, val):
+        esd_matrix_set_values(self._h, val)
+
     def close(self):
         if getattr(self, "_h", None):
             esd_matrix_destroy(self._h)
@@ -404,6 +439,9 @@ class Solver:
 
     def get_W(self):
         return esd_get_W(self._h, self.matrix.n)
+
+    def refresh_W(self):
+        esd_refresh_W(self._h)
 
     def ritz_values(self):
         return esd_ritz_values(self._h)

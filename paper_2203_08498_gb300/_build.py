@@ -15,7 +15,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libesdcg.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["esd_matrix.cu", "esd_solver.cu", "esd_dense.cu", "esd_iter_f64.cu", "esd_iter_f32.cu",
-           "esd_noalloc.cu", "esd_refine.cu"]
+           "esd_noalloc.cu", "esd_refine.cu", "esd_fv.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", f"-I{INCLUDE}"]
 

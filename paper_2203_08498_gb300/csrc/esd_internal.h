@@ -98,6 +98,8 @@ struct esd_matrix {
   esd::Scratch scratch;
   bool factored = false;
   int factor_version = 0;
+  int values_version = 0;  // bumped whenever the values of A change (same pattern)
+  int a32_version = -1;    // values_version of val32 / rowsum32
   int fp32_version = -1;
   double shift = 0.0;
   size_t vec_stride() const { return ((size_t)n + 1 + 31) / 32 * 32; }  // doubles per vector
@@ -109,6 +111,8 @@ namespace esd {
 void copy_in(const void* src, void* dst_dev, size_t bytes, cudaStream_t s);   // device or host src
 void copy_out(const void* src_dev, void* dst, size_t bytes, cudaStream_t s);  // device or host dst
 bool is_device_ptr(const void* p);
+// After csr_val changed on the device: refill the sliced-ELL values of A, drop the factor.
+void matrix_values_changed(esd_matrix* A);
 void set_last_error(const std::string& msg);
 
 // Kernel launchers used across files (defined in esd_iter.cu).

@@ -262,6 +262,18 @@ __global__ void k_to_float(long long cnt, const double* a, float* b) {
   for (long long i = t; i < cnt; i += stride) b[i] = (float)a[i];
 }
 
+// values of A only (the pattern and the slice layout are those of creation)
+__global__ void k_fill_values(int nslices, const int4* mA, const int* rp, const double* va, double* valA) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  int s = g >> 5, lane = g & 31;
+  if (s >= nslices) return;
+  const int4 a = mA[s];
+  const bool valid = lane < a.w;
+  const int i = a.z + lane;
+  const int b = valid ? rp[i] : 0, e = valid ? rp[i + 1] : 0;
+  for (int k = 0; k < a.y; ++k) valA[a.x + k * kSlice + lane] = (valid && b + k < e) ? va[b + k] : 0.0;
+}
+
 // s_i = sum_j a_ij in FP64 (the row's own entries, padding adds zeros), stored as FP32
 __global__ void k_rowsum(SellView<double> A, int nslices, float* s) {
   const int lane = threadIdx.x & 31;
@@ -287,15 +299,28 @@ static void to_float(const DevBuf& src, DevBuf& dst, long long cnt, cudaStream_t
 
 using namespace esd;
 
+void esd::matrix_values_changed(esd_matrix* A) {
+  const int NS = A->nslices;
+  k_fill_values<<<(NS * 32 + 255) / 256, 256, 0, A->stream>>>(NS, A->A.meta.as<int4>(), A->csr_rowptr.as<int>(),
+                                                              A->csr_val.as<double>(), A->A.val.as<double>());
+  ESD_CUDA(cudaGetLastError());
+  A->values_version++;
+  A->factored = false;
+  A->factor_version++;
+}
+
 void esd_matrix::ensure_fp32() {
-  if (fp32_version == factor_version && A.val32.get()) return;
-  to_float(A.val, A.val32, A.entries, stream);
-  if (!rowsum32.get()) {
-    rowsum32.alloc(sizeof(float) * vec_stride());
-    ESD_CUDA(cudaMemsetAsync(rowsum32.get(), 0, rowsum32.bytes(), stream));
+  if (a32_version != values_version || !A.val32.get()) {
+    to_float(A.val, A.val32, A.entries, stream);
+    if (!rowsum32.get()) {
+      rowsum32.alloc(sizeof(float) * vec_stride());
+      ESD_CUDA(cudaMemsetAsync(rowsum32.get(), 0, rowsum32.bytes(), stream));
+    }
     k_rowsum<<<max_grid_blocks(), kBlock, 0, stream>>>(A.view<double>(), nslices, rowsum32.as<float>());
     ESD_CUDA(cudaGetLastError());
+    a32_version = values_version;
   }
+  if (fp32_version == factor_version) return;
   if (factored) {
     to_float(L.val, L.val32, L.entries, stream);
     to_float(U.val, U.val32, U.entries, stream);
@@ -556,6 +581,19 @@ int esd_matrix_info(const esd_matrix* A, int32_t* n, int64_t* nnz, int32_t* ncol
   if (fwd_levels) *fwd_levels = 1 + *std::max_element(A->fwd_level.begin(), A->fwd_level.end());
   if (bwd_levels) *bwd_levels = 1 + *std::max_element(A->bwd_level.begin(), A->bwd_level.end());
   return ESD_OK;
+}
+
+int esd_matrix_set_values(esd_matrix* A, const double* val) {
+  try {
+    ESD_CHECK(A && val, ESD_ERR_INVALID, "NULL argument");
+    copy_in(val, A->csr_val.get(), sizeof(double) * A->nnz, A->stream);
+    matrix_values_changed(A);
+    ESD_CUDA(cudaStreamSynchronize(A->stream));
+    return ESD_OK;
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.code;
+  }
 }
 
 int esd_factor_ic0(esd_matrix* A, int32_t max_tries, double* shift_used) {

@@ -146,6 +146,7 @@ struct esd_solver {
   int mbar = 0;
   bool have_W = false;
   int w_version = 0;
+  int w_values_version = -1;  // the matrix values W's AW and E were formed for
   cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
   int exec_version[3] = {-1, -1, -1};
   int last_iters = 0, last_status = 0, last_sample_m = 0, last_maxit = 0;
@@ -528,6 +529,10 @@ int esd_solve(esd_solver* S, const double* b, double* x, double tol, int32_t max
   ESD_CHECK(sample_m == 0 || S->mode != ESD_DEFLATION, ESD_ERR_STATE,
             "sampling is defined on plain / subspace-correction iterates, not in deflation mode");
   ESD_CHECK(sample_m != 1, ESD_ERR_INVALID, "sampling method A needs m >= 2");
+  ESD_CHECK(S->prm.precond == ESD_PRECOND_NONE || S->A->factored, ESD_ERR_STATE,
+            "the IC(0) factor is missing or stale (the matrix values changed): call esd_factor_ic0");
+  ESD_CHECK(S->mode == ESD_PLAIN || S->w_values_version == S->A->values_version, ESD_ERR_STATE,
+            "the matrix values changed after W was built: call esd_refresh_W");
   cudaStream_t s = S->stream;
   const int n = S->A->n;
   if (S->fp32) S->A->ensure_fp32();
@@ -606,6 +611,7 @@ static void install_W(esd_solver* S, const double* X, int m, bool orth, double t
   S->mbar = mbar;
   S->have_W = true;
   S->w_version++;
+  S->w_values_version = S->A->values_version;
   S->refresh_w32();
   ESD_CUDA(cudaStreamSynchronize(S->stream));
 }
@@ -642,6 +648,20 @@ int esd_set_W(esd_solver* S, const double* W, int32_t m) {
   for (int j = 0; j < m; ++j)
     copy_in(W + (size_t)j * n, S->aux.work1.as<double>() + (size_t)j * S->ld, sizeof(double) * n, S->stream);
   install_W(S, S->aux.work1.as<double>(), m, false, std::numeric_limits<double>::infinity());
+  return ESD_OK;
+  ESD_API_END
+}
+
+int esd_refresh_W(esd_solver* S) {
+  ESD_API_BEGIN
+  ESD_CHECK(S, ESD_ERR_INVALID, "NULL solver");
+  ESD_CHECK(S->have_W, ESD_ERR_STATE, "no W");
+  S->aux.ensure(S->A->n, S->ld);
+  ESD_CUDA(cudaMemcpyAsync(S->aux.work1.get(), S->W.get(), sizeof(double) * S->ld * S->m, cudaMemcpyDeviceToDevice,
+                           S->stream));
+  const int mbar = S->mbar;
+  install_W(S, S->aux.work1.as<double>(), S->m, false, std::numeric_limits<double>::infinity());
+  S->mbar = mbar;
   return ESD_OK;
   ESD_API_END
 }

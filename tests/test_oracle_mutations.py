@@ -81,3 +81,23 @@ def test_lanczos_dropped_term_is_caught(monkeypatch):
     monkeypatch.setattr(oracle, "lanczos_tridiagonal", wrong)
     with pytest.raises(AssertionError):
         pins.test_lanczos_1d_laplacian_closed_form()
+
+
+import test_oracle_grad as grad_pins  # noqa: E402
+
+GRAD_MUTANTS = {
+    # dT/dk_a with k_a where k_b belongs
+    "dT_dk_operand": ("_face_dT_dka", lambda ka, kb, inv_h2: 2.0 * ka * ka / ((ka + kb) * (ka + kb)) * inv_h2),
+    # the Dirichlet faces forgotten
+    "no_boundary_term": ("_boundary_dL_dk", lambda lam_c, x_c, inv_h2: 0.0 * lam_c),
+    # dL/dT with the wrong sign
+    "dL_dT_sign": ("_face_dL_dT", lambda la, lb, xa, xb: (la - lb) * (xa - xb)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(GRAD_MUTANTS))
+def test_planted_gradient_mistake_is_caught(name, monkeypatch):
+    attr, wrong = GRAD_MUTANTS[name]
+    monkeypatch.setattr(oracle, attr, wrong)
+    with pytest.raises(AssertionError):
+        grad_pins.test_theta_gradient_matches_finite_differences("3d_3x4x2_steady")
