@@ -1,21 +1,30 @@
 #!/usr/bin/env python3
-"""Benchmark of the hot path on the 128^3 heterogeneous-diffusion sequence.
+"""Benchmark of the hot path.
 
-Workload (the configuration the headline metric is quoted on): 3D 7-point finite-volume
-diffusion on a 128^3 grid (n = 2,097,152, nnz = 14,581,760), background coefficient 1 and 16
-seeded balls of radius 4-8 cells with coefficient 1e5, Dirichlet boundaries, 8-colour
-ordering, FP64 CSR; a backward-Euler sequence of 20 systems b_t = x_{t-1}/dt + Gaussian
-source (dt = 1e-3, x_0 = 0); IC(0)-PCG to relative residual 1e-8; W from m = 16 error
-vectors sampled (method A) during system 1; systems 2..20 deflated.
+Headline (default, --config c2): 3D 7-point finite-volume diffusion on a 128^3 grid
+(n = 2,097,152, nnz = 14,581,760), background coefficient 1 and 16 seeded balls of radius
+4-8 cells with coefficient 1e5, Dirichlet boundaries, 8-colour ordering, FP64 CSR; a
+backward-Euler sequence of 20 systems b_t = x_{t-1}/dt + Gaussian source (dt = 1e-3,
+x_0 = 0); IC(0)-PCG to relative residual 1e-8; W from m = 16 error vectors sampled
+(method A) during system 1; systems 2..20 deflated.
 
 One step = one whole sequence: IC(0) factorisation, system 1 with sampling, the W build
 (CholeskyQR2, AW, E, E^-1), the Lanczos condition estimate, systems 2..20 in the selected
 mode, with the backward-Euler right-hand sides formed on the device. value = systems solved
 per second (all ranks). Inputs are resident in HBM when the timed region starts; the
-working set (~1.3 GB) is larger than L2, so no flush is needed between steps.
+working set is larger than L2, so no flush is needed between steps.
 
---impl reference times the CPU oracle (the FP64 C restatement of the method) on the same
-workload, a bounded number of iterations per step, extrapolated to solves per second.
+Other workloads (--config): c3 = 192^3 27-point anisotropic log-normal Q1 FE, 10 systems
+to 1e-10 in the precision form (FP32 inner PCG in FP64 refinement), deflation m = 24;
+c4 = 128^3 log-normal exp(theta) diffusion, one optimisation step (theta update, device
+assembly, IC(0), forward and adjoint solve through the autograd API), deflation m = 16;
+c5 = 256^3 7-point with 64 balls of 1e6, 50 systems in the precision form, deflation
+m = 32, each forward solve followed by its adjoint. Each reports plain FP64 PCG on the
+same work beside it.
+
+--impl reference times the CPU oracle (the FP64 C restatement of the method) on the
+headline workload, a bounded number of iterations per step, extrapolated to solves per
+second.
 """
 from __future__ import annotations
 
@@ -40,21 +49,40 @@ UNIT = "solves/s"
 L2_BYTES = 129e6
 
 
+# Per workload: grid, systems per step, sampled columns m, tolerance, mode, precision and
+# whether every forward solve is followed by its adjoint solve.
+CONFIGS = {
+    # 128^3 7-point, 16 balls of 1e5: the headline sequence
+    "c2": dict(grid=128, systems=20, m=16, tol=1e-8, mode="deflation", precision="fp64", adjoint=False),
+    # 192^3 27-point anisotropic log-normal FE: the precision form to 1e-10
+    "c3": dict(grid=192, systems=10, m=24, tol=1e-10, mode="deflation", precision="fp32", adjoint=False),
+    # 128^3 log-normal exp(theta): one optimisation step = theta update + forward + adjoint
+    "c4": dict(grid=128, systems=1, m=16, tol=1e-8, mode="deflation", precision="fp64", adjoint=True),
+    # 256^3 7-point, 64 balls of 1e6: precision form, each forward solve with its adjoint
+    "c5": dict(grid=256, systems=50, m=32, tol=1e-8, mode="deflation", precision="fp32", adjoint=True),
+}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="esdcg", choices=["esdcg", "reference"])
-    ap.add_argument("--mode", default="deflation", choices=["plain", "deflation", "sc"])
-    ap.add_argument("--grid", type=int, default=128)
-    ap.add_argument("--systems", type=int, default=20)
-    ap.add_argument("--m", type=int, default=16)
-    ap.add_argument("--tol", type=float, default=1e-8)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
+    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
+    ap.add_argument("--mode", default=None, choices=["plain", "deflation", "sc"])
+    ap.add_argument("--grid", type=int, default=None)
+    ap.add_argument("--systems", type=int, default=None)
+    ap.add_argument("--m", type=int, default=None)
+    ap.add_argument("--tol", type=float, default=None)
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32"],
                     help="fp32: FP32 inner PCG inside FP64 iterative refinement")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, comparison modes and CPU baseline")
-    return ap.parse_args()
+    a = ap.parse_args()
+    for k, v in CONFIGS[a.config].items():
+        if getattr(a, k, None) is None:
+            setattr(a, k, v)
+    return a
 
 
 def dist_env():
@@ -64,19 +92,43 @@ def dist_env():
     return ws, rank, local
 
 
+_WORKLOADS = {}
+
+
 def workload(args):
+    """The config's problem (C4 also returns theta and x_target); built once per process."""
+    key = (args.config, args.grid)
+    if key not in _WORKLOADS:
+        _WORKLOADS[key] = _make_workload(args)
+    return _WORKLOADS[key]
+
+
+def _make_workload(args):
     import workloads as wl
-    if args.grid == 128:
-        p = wl.config_c2()
-    else:
-        r = args.grid / 128.0
-        p = wl.config_c2(N=args.grid, rmin=4 * r, rmax=8 * r)
-    return p
+    r = args.grid / {"c2": 128.0, "c3": 192.0, "c4": 128.0, "c5": 256.0}[args.config]
+    if args.config == "c2":
+        return wl.config_c2() if args.grid == 128 else wl.config_c2(N=args.grid, rmin=4 * r, rmax=8 * r)
+    if args.config == "c3":
+        return wl.config_c3(N=args.grid)
+    if args.config == "c5":
+        return wl.config_c5(N=args.grid, rmin=8 * r, rmax=16 * r)
+    return wl.config_c4(N=args.grid)
 
 
 def workload_name(args, p):
-    return (f"fv7_{args.grid}cube_16balls_1e5_dt1e-3: {args.systems}-system backward-Euler sequence, "
-            f"IC(0)-PCG to {args.tol:g}, W from m={args.m} sampled error vectors, {args.mode}")
+    base = {
+        "c2": f"fv7_{args.grid}cube_16balls_1e5_dt1e-3",
+        "c3": f"fe27_{args.grid}cube_aniso1e-3_lognormal_s2_dt1e-3",
+        "c4": f"fv7_{args.grid}cube_exp_theta_smooth4_steady",
+        "c5": f"fv7_{args.grid}cube_64balls_1e6_dt1e-3",
+    }[args.config]
+    what = ("one optimisation step: theta update (device assembly, IC(0), AW/E refresh), forward solve "
+            "and adjoint solve through the autograd API" if args.config == "c4" else
+            f"{args.systems}-system backward-Euler sequence" + (", each solve followed by its adjoint"
+                                                                 if args.adjoint else ""))
+    prec = "FP64" if args.precision == "fp64" else "FP32 inner PCG in FP64 refinement"
+    return (f"{base}: {what}, IC(0)-PCG to {args.tol:g} ({prec}), W from m={args.m} sampled error "
+            f"vectors, {args.mode}")
 
 
 def level_stats(p):
@@ -141,6 +193,25 @@ class Clocks:
 
 # ---------------------------------------------------------------- GPU arm
 
+def launch_count(info, mode_is, m, fp32, its, outer):
+    """Kernels of this library launched by solves with these inner iteration counts and
+    refinement steps (from the launch sequences of the iteration and refinement graphs)."""
+    nf = info["fwd_levels"] - 1
+    nb = max(info["bwd_levels"] - 1, 1)
+    body = 2 + nf + nb
+    defl = 1 if mode_is == "deflation" else 0
+    start = 1 + 2 * defl + 1 + nf + nb  # residual0, projection, update, sweeps
+    end = 2 * defl + 1                   # correction, finish
+    total = 0
+    for k, o in zip(its, outer):
+        if fp32:
+            total += 1 + o * (1 + start + end + 2)  # residual; per step prep, start, end, apply, residual
+        else:
+            total += start + end + 1               # + true residual
+        total += body * k
+    return total
+
+
 def gpu_arm(args):
     import torch
     import paper_2203_08498_gb300 as esd
@@ -151,23 +222,34 @@ def gpu_arm(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
+    if args.config == "c4":
+        return c4_arm(args, esd, torch, dev, ws, rank)
     p = workload(args)
     n, nnz = p.n, p.nnz
-    mode = {"plain": esd.PLAIN, "deflation": esd.DEFLATION, "sc": esd.SUBSPACE_CORRECTION}[args.mode]
+    modes_map = {"plain": esd.PLAIN, "deflation": esd.DEFLATION, "sc": esd.SUBSPACE_CORRECTION}
+    mode = modes_map[args.mode]
+    fp32 = args.precision == "fp32"
     A = esd.Matrix.from_problem(p)
     A.factor_ic0()
-    prec = {"fp64": esd.FP64, "fp32": esd.FP32_REFINE}[args.precision]
-    S = esd.Solver(A, maxit_cap=20000, sample_cap=max(args.m, 2), precision=prec)
+    S = esd.Solver(A, maxit_cap=20000, sample_cap=max(args.m, 2),
+                   precision=esd.FP32_REFINE if fp32 else esd.FP64)
     src = torch.from_numpy(p.source).to(dev)
     x = torch.zeros(n, dtype=torch.float64, device=dev)
     b = torch.empty_like(x)
     inv_dt = 1.0 / p.dt
     info = A.info()
+    if args.adjoint:
+        # loss ||x - x_t||^2 per system: the adjoint right-hand side 2 x - 2 x_t is formed by
+        # the library's rhs kernel (inv_dt = 2, s = -2 x_t)
+        xt = np.random.default_rng(20220316 + 7).standard_normal(n) * float(np.abs(p.source).max()) * 1e-3
+        neg2xt = torch.from_numpy(-2.0 * xt).to(dev)
+        lam = torch.zeros_like(x)
+        g = torch.empty_like(x)
 
-    def sequence(md, S=S, A=A, x=x, b=b, src=src):
+    def sequence(md, S=S):
         A.factor_ic0()
         x.zero_()
-        its, stats = [], {}
+        its, outer, adj, stats = [], [], [], {}
         for t in range(args.systems):
             S.backward_euler_rhs(x, src, inv_dt, b)
             if t == 0:
@@ -182,7 +264,16 @@ def gpu_arm(args):
             if st != esd.OK:
                 raise RuntimeError(f"solve {t} returned {st}")
             its.append(it)
-        return its, stats
+            outer.append(S.last_solve_info()["outer_steps"])
+            if args.adjoint:
+                S.backward_euler_rhs(x, neg2xt, 2.0, g)
+                lam.zero_()
+                st, ita, rr = S.solve(g, lam, args.tol, 20000, 0)
+                if st != esd.OK:
+                    raise RuntimeError(f"adjoint solve {t} returned {st}")
+                adj.append(ita)
+                outer.append(S.last_solve_info()["outer_steps"])
+        return its, stats, adj, outer
 
     def timed(md, steps, warm, S=S):
         for _ in range(warm):
@@ -213,43 +304,46 @@ def gpu_arm(args):
     clocks = Clocks(local)
     ms, wall, runs = timed(mode, args.steps, args.warmup)
     clk = clocks.stop()
-    its, stats = runs[-1]
-    systems_total = args.systems * args.steps * ws
-    value = systems_total / (ms / 1e3)
+    its, stats, adj, outer = runs[-1]
+    solves_per_step = args.systems * (2 if args.adjoint else 1)
+    value = solves_per_step * args.steps * ws / (ms / 1e3)
     ms_step = ms / args.steps
 
-    # kernel launches inside the timed region (counted from the launch sequences)
-    nf = info["fwd_levels"] - 1
-    nb = max(info["bwd_levels"] - 1, 1)
-    body = 2 + nf + nb
-    defl = 1 if mode == esd.DEFLATION else 0
-    per_solve_fixed = (1 + 2 * defl + 1 + nf + nb) + (1 + 2 * defl + 1)
     launches = 0
-    for it_list, st_ in runs:
-        launches += info["fwd_levels"] + 1  # factorisation
-        launches += args.systems  # right-hand sides
-        launches += sum(per_solve_fixed + body * k for k in it_list)
+    for it_list, st_, adj_list, outer_list in runs:
+        all_its = []
+        for t in range(len(it_list)):
+            all_its.append(it_list[t])
+            if args.adjoint:
+                all_its.append(adj_list[t])
+        launches += info["fwd_levels"] + 1 + (2 if fp32 else 0)  # factorisation (+ FP32 copies)
+        launches += len(all_its) + (len(adj_list) if args.adjoint else 0)  # right-hand sides
+        launches += launch_count(info, args.mode, args.m, fp32, all_its, outer_list)
         launches += 1  # condition estimate
         if mode != esd.PLAIN:
-            launches += 1 + 8 + args.m  # errors, Gram/small/tall kernels, A W columns
+            launches += (1 + 8 + args.m) * (2 if fp32 else 1) + (3 if fp32 else 0)  # W build (+ FP32 pass)
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f32 inner, f64 refinement", "data": "synthetic",
-        "config": {"workload": workload_name(args, p), "grid": args.grid, "n": n, "nnz": nnz,
-                   "systems": args.systems, "m": args.m, "mode": args.mode, "tol": args.tol,
-                   "precision": args.precision,
+        "dtype": "f64" if not fp32 else "f32 inner, f64 refinement", "data": "synthetic",
+        "config": {"workload": workload_name(args, p), "config": args.config, "grid": args.grid, "n": n,
+                   "nnz": nnz, "systems": args.systems, "m": args.m, "mode": args.mode, "tol": args.tol,
+                   "precision": args.precision, "adjoint": args.adjoint,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                   "l2": "inputs larger than L2 (matrix, factor and vectors ~1.3 GB > 129 MB)"},
+                   "l2": "inputs larger than L2 (matrix, factor and vectors > 129 MB)"},
         "gpu_launches": launches,
         "clocks": clk,
         "iterations": its,
-        "time_to_tol_ms_per_system": ms_step / args.systems,
+        "time_to_tol_ms_per_system": ms_step / solves_per_step,
         "cond_estimate_system1": {"lmin": stats["cond"][0], "lmax": stats["cond"][1],
                                   "kappa": stats["cond"][2]},
     }
+    if args.adjoint:
+        result["adjoint_iterations"] = adj
+    if fp32:
+        result["refinement_steps"] = outer
     if rank != 0 or args.no_extras:
         return result, None
 
@@ -260,36 +354,106 @@ def gpu_arm(args):
     peaks = read_peaks()
     result["roofline"], result["kernel_times_ms"] = roofline(prof, p, args, mode, esd, peaks)
 
-    # per-iteration time in each mode through the graphs (from the timed sequences)
-    modes = {}
-    iter_time = {}
-    for name, md in (("plain", esd.PLAIN), ("deflation", esd.DEFLATION), ("sc", esd.SUBSPACE_CORRECTION)):
-        if md == mode:
-            its_m, ms_m = its, ms_step
-        else:
-            ms_m, _, r = timed(md, 1, 1)
-            its_m = r[-1][0]
-        modes[name] = {"iterations": its_m, "ms_per_sequence": ms_m, "solves_per_s": args.systems / (ms_m / 1e3),
-                       "mean_iters_2_to_T": float(np.mean(its_m[1:]))}
-    result["modes"] = modes
-    # the precision form on the same sequence: FP32 inner PCG (resumed, inner_tol 0.3) inside
-    # FP64 refinement to the same tolerance, against plain FP64 PCG
-    if args.precision == "fp64":
+    modes = None
+    if args.config == "c2" and not fp32:
+        # per-iteration time in each mode through the graphs (from the timed sequences)
+        modes = {}
+        for name, md in modes_map.items():
+            if md == mode:
+                its_m, ms_m = its, ms_step
+            else:
+                ms_m, _, r = timed(md, 1, 1)
+                its_m = r[-1][0]
+            modes[name] = {"iterations": its_m, "ms_per_sequence": ms_m,
+                           "solves_per_s": args.systems / (ms_m / 1e3),
+                           "mean_iters_2_to_T": float(np.mean(its_m[1:]))}
+        result["modes"] = modes
+        # the precision form on the same sequence: FP32 inner PCG (resumed, inner_tol 0.1) inside
+        # FP64 refinement to the same tolerance, against plain FP64 PCG
         S32 = esd.Solver(A, maxit_cap=20000, sample_cap=max(args.m, 2), precision=esd.FP32_REFINE)
         fp64_plain_ms = modes["plain"]["ms_per_sequence"]
         pf = {"fp64_plain_ms_per_system": fp64_plain_ms / args.systems}
-        for name, md in (("plain", esd.PLAIN), ("deflation", esd.DEFLATION), ("sc", esd.SUBSPACE_CORRECTION)):
+        for name, md in modes_map.items():
             ms_m, _, r = timed(md, 1, 1, S=S32)
             its_m = r[-1][0]
             pf[f"fp32_{name}"] = {"ms_per_system": ms_m / args.systems, "iterations": its_m,
                                   "speedup_vs_fp64_plain": fp64_plain_ms / ms_m}
         result["precision_form"] = pf
-    # time per iteration and model bandwidth per mode (single solves of system 2)
-    result["iteration"] = iteration_roofline(S, esd, p, args, x, b, src, peaks)
-
-    # end to end through the C ABI with host buffers
-    result["e2e"] = e2e(esd, p, args, torch)
+        # time per iteration and model bandwidth per mode (single solves of system 2)
+        result["iteration"] = iteration_roofline(S, esd, p, args, x, b, src, peaks)
+        # end to end through the C ABI with host buffers
+        result["e2e"] = e2e(esd, p, args, torch)
+    else:
+        # comparator: plain FP64 PCG on the same sequence (one timed pass)
+        S64 = S if not fp32 else esd.Solver(A, maxit_cap=20000, sample_cap=max(args.m, 2))
+        ms64, _, r64 = timed(esd.PLAIN, 1, 0, S=S64)
+        result["fp64_plain"] = {"ms_per_step": ms64, "iterations": r64[-1][0],
+                                "ms_per_solve": ms64 / solves_per_step,
+                                "speedup_of_this_run": ms64 / ms_step}
+        result["e2e"] = {"value": None, "unit": UNIT, "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                         "note": "end-to-end host-buffer timing is taken on the headline 128^3 sequence only"}
     return result, modes
+
+
+def c4_arm(args, esd, torch, dev, ws, rank):
+    """One optimisation step of the differentiation form: theta moves, A(theta) is assembled
+    on the device, refactored, AW/E refreshed for the kept W, then x = A^-1 b and the
+    adjoint solve with the gradients through the autograd API."""
+    from paper_2203_08498_gb300.adjoint import FVDiffusion, fv_solve
+    p, theta, xt = workload(args)
+    mode = {"plain": esd.PLAIN, "deflation": esd.DEFLATION, "sc": esd.SUBSPACE_CORRECTION}[args.mode]
+    fp32 = args.precision == "fp32"
+    model = FVDiffusion(p, mode=mode, precision=esd.FP32_REFINE if fp32 else esd.FP64, sample_cap=max(args.m, 2))
+    th0 = torch.from_numpy(np.ascontiguousarray(theta.ravel(order="F"))).to(dev)
+    b = torch.from_numpy(p.source).to(dev)
+    xt_d = torch.from_numpy(xt).to(dev)
+    kept = model.build_W(th0, b, m=args.m, tol=args.tol) if mode != esd.PLAIN else 0
+    delta = torch.from_numpy(np.random.default_rng(20220316 + 8).standard_normal(p.n)).to(dev)
+    counter = {"k": 0, "its": []}
+
+    def step():
+        counter["k"] += 1
+        th = (th0 + 1e-4 * counter["k"] * delta).requires_grad_(True)
+        x = fv_solve(th, b, model, tol=args.tol)
+        fwd = model.solver.last_solve_info()["iters"]
+        ((x - xt_d) ** 2).sum().backward()
+        adj = model.solver.last_solve_info()["iters"]
+        counter["its"].append((fwd, adj))
+        return th.grad
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(torch.cuda.current_device())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    info = model.matrix.info()
+    its = counter["its"][-args.steps:]
+    flat = [k for pair in its for k in pair]
+    launches = args.steps * (1 + info["fwd_levels"] + 1 + (9 + args.m if mode != esd.PLAIN else 0) + 1)
+    launches += launch_count(info, args.mode, args.m, fp32, flat, [1] * len(flat))
+    result = {
+        "metric": METRIC, "value": 2 * args.steps * ws / (ms / 1e3), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if not fp32 else "f32 inner, f64 refinement",
+        "data": "synthetic",
+        "config": {"workload": workload_name(args, p), "config": "c4", "grid": args.grid, "n": p.n,
+                   "nnz": p.nnz, "m": args.m, "m_kept": kept, "mode": args.mode, "tol": args.tol,
+                   "precision": args.precision, "parallelism": "single GPU",
+                   "l2": "inputs larger than L2"},
+        "gpu_launches": launches, "clocks": clk,
+        "iterations_forward_adjoint": its,
+        "time_to_tol_ms_per_system": ms / args.steps / 2,
+        "e2e": {"value": None, "unit": UNIT, "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                "note": "end-to-end host-buffer timing is taken on the headline 128^3 sequence only"},
+    }
+    return result, None
 
 
 def read_peaks():
@@ -304,19 +468,28 @@ def read_peaks():
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (CUDA cores and tensor), nominal
 
 
+FP32_NOMINAL_TFLOPS = 80.5  # 152 SMs x 128 FP32 FMA/clk x 2 x 2.07 GHz
+
+
 def kernel_model(name, p, args, mode, esd, lv):
-    """Algorithmic bytes and FP64 FMAs of one launch (per-kernel model)."""
+    """Algorithmic bytes and FMAs of one launch (per-kernel model); value
+    size s = 8 (FP64) or 4 (FP32 inner kernels, whose SpMV also reads s = A 1)."""
     n, nnz = p.n, p.nnz
+    s = 4 if args.precision == "fp32" else 8
     m = args.m if mode != esd.PLAIN else 0
     rows, low, up = lv
     if name == "spmv_pq":
         mb = m if mode == esd.DEFLATION else 0
-        return 12 * nnz + 20 * n + 8 * mb * n, nnz + n + mb * n
+        extra = 4 * n if s == 4 else 0
+        return (s + 4) * nnz + (2 * s + 4) * n + extra + s * mb * n, nnz + n + mb * n
     if name == "update":
         dm = m if mode == esd.DEFLATION else 0
         sm = m if mode == esd.SUBSPACE_CORRECTION else 0
         n0 = int(rows[0])  # forward level 0 (colour 0): y = r / l_ii
-        return 48 * n + 8 * (dm + sm) * n + 16 * n0, 3 * n + (dm + sm) * n + 2 * n0
+        # x read and written (FP64 in both forms: the refinement form keeps the iterate in
+        # FP64), p and q read, r read and written
+        base = 16 * n + 4 * s * n
+        return base + s * (dm + sm) * n + 2 * s * n0, 3 * n + (dm + sm) * n + 2 * n0
     return None, None
 
 
@@ -330,17 +503,18 @@ def roofline(prof, p, args, mode, esd, peaks):
     gbs = by / sec / 1e9
     tflops = 2 * fmas / sec / 1e12
     f_hbm = gbs / peaks["hbm_gbs"]
-    f_alu = tflops / FP64_NOMINAL_TFLOPS
-    traffic = read_traffic(name)
+    alu_peak = FP32_NOMINAL_TFLOPS if args.precision == "fp32" else FP64_NOMINAL_TFLOPS
+    f_alu = tflops / alu_peak
+    traffic = read_traffic(name) if args.config == "c2" and args.precision == "fp64" else None
     if f_alu > f_hbm:
-        roof = {"bound": "alu", "achieved": tflops, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+        roof = {"bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": f_alu, "traffic": traffic, "kernel": name,
                 "peak_src": "nominal FP64 (152 SMs x 2 FP64 FMA/clk x 2.07 GHz)",
                 "hbm": {"achieved": gbs, "peak": peaks["hbm_gbs"], "frac": f_hbm, "peak_src": peaks["src"]}}
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": f_hbm,
                 "traffic": traffic, "kernel": name, "peak_src": peaks["src"],
-                "alu": {"achieved": tflops, "peak": FP64_NOMINAL_TFLOPS, "frac": f_alu}}
+                "alu": {"achieved": tflops, "peak": alu_peak, "frac": f_alu}}
     roof["bytes_per_launch"] = by
     roof["ms_per_launch"] = t_ms
     return roof, times
@@ -452,11 +626,12 @@ def extrapolate(rates, its):
 
 
 def cpu_baseline(p, args, its):
-    r = oracle_rates(p, args)
+    k = 20 if p.nnz < 50_000_000 else 3  # keep the CPU sample to tens of seconds
+    r = oracle_rates(p, args, iters_plain=k, iters_acc=k)
     return {"value": extrapolate(r, its), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"20 plain and 20 {args.mode} ICCG iterations of the {args.grid}^3 system (m={args.m}, "
-                       f"orthonormal W) on one host core, extrapolated with this run's iteration counts "
-                       f"per system"), "s_per_iter": r}
+            "sample": (f"{k} plain and {k} {args.mode} FP64 ICCG iterations of the {args.config} system "
+                       f"(n={p.n}, m={args.m}, orthonormal W) on one host core, extrapolated with this "
+                       f"run's iteration counts per solve"), "s_per_iter": r}
 
 
 def oracle_counts(args):
@@ -472,6 +647,10 @@ def oracle_counts(args):
 def reference_arm(args):
     ws, rank, local = dist_env()
     if rank != 0:
+        return
+    if args.config != "c2":
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm is timed on the headline 128^3 "
+                          "sequence (config c2) only"}), flush=True)
         return
     p = workload(args)
     its = oracle_counts(args)
@@ -502,7 +681,15 @@ def main():
     result, modes = gpu_arm(args)
     if rank == 0:
         if not args.no_extras and ws == 1:
-            result["cpu_baseline"] = cpu_baseline(workload(args), args, result["iterations"])
+            if args.config == "c4":
+                p = workload(args)[0]
+                its = [k for pair in result["iterations_forward_adjoint"] for k in pair]
+            else:
+                p = workload(args)
+                its = list(result["iterations"])
+                if args.adjoint:
+                    its += list(result["adjoint_iterations"])
+            result["cpu_baseline"] = cpu_baseline(p, args, its)
         print(json.dumps(result), flush=True)
     if ws > 1:
         import torch.distributed as dist

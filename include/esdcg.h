@@ -166,7 +166,7 @@ typedef struct {
 } esd_params;
 
 /* Default parameters: IC(0), maxit_cap 20000, sample_cap 32, lmax 0, rank_tol 1e-12, FP64;
- * for ESD_FP32_REFINE inner_tol 0.3, max_outer 60, resume_direction 1. */
+ * for ESD_FP32_REFINE inner_tol 0.1, max_outer 60, resume_direction 1. */
 void esd_params_default(esd_params* p);
 
 int esd_solver_create(esd_matrix* A, const esd_params* params, esd_solver** out);

@@ -409,7 +409,7 @@ class Solver:
     """``esd_solver`` bound to a Matrix; keeps the matrix alive."""
 
     def __init__(self, matrix: Matrix, precond=PRECOND_IC0, maxit_cap=20000, sample_cap=32, lmax=0,
-                 rank_tol=1e-12, precision=FP64, inner_tol=0.3, max_outer=60, resume_direction=1):
+                 rank_tol=1e-12, precision=FP64, inner_tol=0.1, max_outer=60, resume_direction=1):
         p = esd_params_default()
         p.precond, p.maxit_cap, p.sample_cap, p.lmax = precond, maxit_cap, sample_cap, lmax
         p.rank_tol, p.precision, p.inner_tol, p.max_outer = rank_tol, precision, inner_tol, max_outer

@@ -82,6 +82,7 @@ struct State {
   int slot_iter[kMaxM];
   double y[kMaxM];  // deflation: E^{-1} (AW)^T p
   double u[kMaxM];  // subspace correction / projection: E^{-1} f
+  double gacc[kMaxM];  // FP64-iterate deflation: (AW)^T x_i accumulated as sum alpha_k h_k
   unsigned int ticket[8];
 };
 
@@ -106,7 +107,10 @@ struct RefineState {
   int keep;           // 1: every step resumes CG with the previous step's direction
   int fresh;          // the step about to start resumes with p = z (the gap was too large)
   int restarts;       // resumed steps that restarted the direction
-  int pad;
+  int breakdowns;     // inner runs that ended in a breakdown
+  int nonfinite;      // the FP64 residual was not finite
+  int stalled;        // consecutive steps that did not lower the best residual by 10%
+  double rr_best;     // the lowest ||b - A x||^2 so far
   double max_gap;     // largest ||r_true - r_inner|| / ||r_true|| at a resumed step
 };
 

@@ -92,7 +92,8 @@ struct esd_matrix {
   esd::DevBuf ldiag;         // double: l_ii
   esd::DevBuf inv_d;         // double: 1/l_ii (n+1, sentinel 0)
   esd::DevBuf inv_d32;       // float copy
-  esd::DevBuf rowsum32;      // s = A 1 summed in FP64, stored in FP32 (difference-form SpMV)
+  esd::DevBuf rowsum32;      // s = A 1 (compensated FP64 sum), stored in FP32 (difference-form SpMV)
+  esd::DevBuf rowsum64;      // the same row sums in FP64 (difference-form refinement residual)
   esd::DevBuf err;           // int[4] validation / factor error words
   esd::DevBuf tmp;           // 3 x (n+1) doubles for host-pointer staging
   esd::Scratch scratch;

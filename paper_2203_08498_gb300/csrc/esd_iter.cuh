@@ -202,8 +202,15 @@ __global__ void __launch_bounds__(kBlock, 4) k_bwd_plain(SellView<T> U, SliceSet
 
 // q = A p, pq = (p, q); deflation: h = (AW)^T p, y = E^-1 h, (p, P^T A p) = pq - h^T y.
 // Last block: alpha = rho / (p, P^T A p).
+// blocks per SM the deflated kernels must fit: their M accumulators per thread; FP32 needs
+// half the registers of FP64
 template <typename T, int M>
-__global__ void __launch_bounds__(kBlock, M == 0 ? ESD_SWEEP_MINB : (M <= 16 ? 2 : 1)) k_spmv_pq(IterCtx<T> c, SliceSet set) {
+constexpr int defl_minb() {
+  return M == 0 ? ESD_SWEEP_MINB : ((sizeof(T) == 4 ? M <= 32 : M <= 16) ? 2 : 1);
+}
+
+template <typename T, int M>
+__global__ void __launch_bounds__(kBlock, defl_minb<T, M>()) k_spmv_pq(IterCtx<T> c, SliceSet set) {
   constexpr int R = 1 + M;
   __shared__ T red[red_size<R>()];
   __shared__ double hy_s;
@@ -272,6 +279,8 @@ __global__ void __launch_bounds__(kBlock, M == 0 ? ESD_SWEEP_MINB : (M <= 16 ? 2
         const double a = st->rho / pap;
         st->alpha = a;
         c.ahist[st->iter] = a;
+        if (M > 0 && c.x64)  // (AW)^T x_i of the FP64 iterate, for the final correction
+          for (int k = 0; k < M; ++k) st->gacc[k] += a * (double)red[1 + k];
       }
     }
   }
@@ -281,7 +290,7 @@ __global__ void __launch_bounds__(kBlock, M == 0 ? ESD_SWEEP_MINB : (M <= 16 ? 2
 // sample of the previous iteration; SC: f = W^T r; forward level 0 (y = r / l_ii).
 // do_update = 0 runs the same epilogue on r0 (start of a solve).
 template <typename T, int M, int MODE, int PRE>
-__global__ void __launch_bounds__(kBlock, M == 0 ? 4 : 1) k_update(IterCtx<T> c, SliceSet set, int do_update,
+__global__ void __launch_bounds__(kBlock, M == 0 ? 4 : defl_minb<T, M>()) k_update(IterCtx<T> c, SliceSet set, int do_update,
                                                                   int finalize) {
   constexpr int SCM = (MODE == kModeSC) ? M : 0;
   constexpr int DM = (MODE == kModeDefl) ? M : 0;
@@ -293,6 +302,7 @@ __global__ void __launch_bounds__(kBlock, M == 0 ? 4 : 1) k_update(IterCtx<T> c,
   State* st = c.st;
   if (st->conv) return;
   const T alpha = (T)st->alpha;
+  const double alpha_d = st->alpha;
   const int pend = do_update ? st->pend_slot : -1;
   if (DM > 0) {
     for (int k = threadIdx.x; k < DM; k += blockDim.x) ys[k] = st->y[k];
@@ -309,12 +319,20 @@ __global__ void __launch_bounds__(kBlock, M == 0 ? 4 : 1) k_update(IterCtx<T> c,
       const int i = md.z + lane;
       T ri;
       if (do_update) {
-        const T xi = c.x[i];
-        if (pend >= 0) {
-          if (c.samples64) c.samples64[(size_t)pend * c.ld + i] = c.xbase[i] + (double)xi;
-          else c.samples[(size_t)pend * c.ld + i] = xi;
+        if (c.x64) {
+          // refinement form: the iterate is kept in FP64, so its rounding does not drift
+          // from the recursive residual
+          const double xi = c.x64[i];
+          if (pend >= 0) c.samples64[(size_t)pend * c.ld + i] = xi;
+          c.x64[i] = fma(alpha_d, (double)c.p[i], xi);
+        } else {
+          const T xi = c.x[i];
+          if (pend >= 0) {
+            if (c.samples64) c.samples64[(size_t)pend * c.ld + i] = c.xbase[i] + (double)xi;
+            else c.samples[(size_t)pend * c.ld + i] = xi;
+          }
+          c.x[i] = fma(alpha, c.p[i], xi);
         }
-        c.x[i] = fma(alpha, c.p[i], xi);
         T t = c.q[i];
 #pragma unroll
         for (int k = 0; k < DM; ++k) t = fma(-c.AW[k * c.ld + i], (T)ys[k], t);
@@ -535,6 +553,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_residual0(IterCtx<T> c, SliceSet 
       st->rr = (double)red[1];
       st->tol2bb = st->scal0 * bb;  // scal0 holds tol^2
       st->zero_rhs = (bb == 0.0);
+      for (int k = 0; k < kMaxM; ++k) st->gacc[k] = 0.0;
     }
   }
 }
@@ -542,7 +561,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_residual0(IterCtx<T> c, SliceSet 
 // f = X^T v - Y^T w (Y optional), u = E^-1 f (stored in st->u).
 template <typename T, int M>
 __global__ void __launch_bounds__(kBlock) k_tallT(IterCtx<T> c, SliceSet set, const T* X, const T* v,
-                                                  const T* Y2, const T* w) {
+                                                  const T* Y2, const T* w, int sub_gacc) {
   __shared__ T red[red_size<M>()];
   pdl_enter();
   State* st = c.st;
@@ -569,7 +588,7 @@ __global__ void __launch_bounds__(kBlock) k_tallT(IterCtx<T> c, SliceSet set, co
     if (threadIdx.x < 32) {
       for (int i = threadIdx.x; i < M; i += 32) {
         double u = 0.0;
-        for (int k = 0; k < M; ++k) u += c.Einv[i * M + k] * (double)red[k];
+        for (int k = 0; k < M; ++k) u += c.Einv[i * M + k] * ((double)red[k] - (sub_gacc ? st->gacc[k] : 0.0));
         st->u[i] = u;
       }
     }
@@ -604,6 +623,28 @@ __global__ void __launch_bounds__(kBlock) k_tall_axpy(IterCtx<T> c, SliceSet set
   if (norm) {
     if (grid_sum_multi<1>(acc, red, (T*)c.partials, &st->ticket[kTkAux2])) {
       if (threadIdx.x == 0) st->rr = (double)red[0];
+    }
+  }
+}
+
+// x64 += Z u (u = st->u): the correction summed in T, added to the FP64 iterate.
+template <typename T, int M>
+__global__ void __launch_bounds__(kBlock) k_tall_axpy64(IterCtx<T> c, SliceSet set, const T* Z) {
+  __shared__ double us[M];
+  pdl_enter();
+  State* st = c.st;
+  for (int k = threadIdx.x; k < M; k += blockDim.x) us[k] = st->u[k];
+  __syncthreads();
+  ESD_LOOP_SLICES(set) {
+    int r;
+    const int s = set.slice(g, &r);
+    const int4 md = c.Av.meta[s];
+    if (lane < md.w) {
+      const int i = md.z + lane;
+      T t = T(0);
+#pragma unroll
+      for (int k = 0; k < M; ++k) t = fma(Z[k * c.ld + i], (T)us[k], t);
+      c.x64[i] += (double)t;
     }
   }
 }
@@ -748,7 +789,7 @@ void launch_init(const IterCtx<T>& c, cudaStream_t s) {
     // r0 = P^T (b - A x0) = r - AW E^-1 W^T r
     ESD_DISPATCH_MPOS(c.M, {
       auto k = k_tallT<T, MM>;
-      ESD_LAUNCH(k, all.total(), s, c, all, (const T*)c.W, (const T*)c.r, (const T*)nullptr, (const T*)nullptr);
+      ESD_LAUNCH(k, all.total(), s, c, all, (const T*)c.W, (const T*)c.r, (const T*)nullptr, (const T*)nullptr, 0);
     });
     ESD_DISPATCH_MPOS(c.M, {
       auto k = k_tall_axpy<T, MM>;
@@ -776,15 +817,27 @@ template <typename T>
 void launch_finish(const IterCtx<T>& c, cudaStream_t s) {
   const SliceSet& all = c.A->all;
   if (c.mode == ESD_DEFLATION) {
-    // x = P x_i + W E^-1 W^T b = x_i + W E^-1 (W^T b - (AW)^T x_i)
-    ESD_DISPATCH_MPOS(c.M, {
-      auto k = k_tallT<T, MM>;
-      ESD_LAUNCH(k, all.total(), s, c, all, (const T*)c.W, (const T*)c.b, (const T*)c.AW, (const T*)c.x);
-    });
-    ESD_DISPATCH_MPOS(c.M, {
-      auto k = k_tall_axpy<T, MM>;
-      ESD_LAUNCH(k, all.total(), s, c, all, (const T*)c.W, c.x, T(1), 0);
-    });
+    // x = P x_i + W E^-1 W^T b = x_i + W E^-1 (W^T b - (AW)^T x_i); with the FP64 iterate
+    // (AW)^T x_i was accumulated along the iteration
+    if (c.x64) {
+      ESD_DISPATCH_MPOS(c.M, {
+        auto k = k_tallT<T, MM>;
+        ESD_LAUNCH(k, all.total(), s, c, all, (const T*)c.W, (const T*)c.b, (const T*)nullptr, (const T*)nullptr, 1);
+      });
+      ESD_DISPATCH_MPOS(c.M, {
+        auto k = k_tall_axpy64<T, MM>;
+        ESD_LAUNCH(k, all.total(), s, c, all, (const T*)c.W);
+      });
+    } else {
+      ESD_DISPATCH_MPOS(c.M, {
+        auto k = k_tallT<T, MM>;
+        ESD_LAUNCH(k, all.total(), s, c, all, (const T*)c.W, (const T*)c.b, (const T*)c.AW, (const T*)c.x, 0);
+      });
+      ESD_DISPATCH_MPOS(c.M, {
+        auto k = k_tall_axpy<T, MM>;
+        ESD_LAUNCH(k, all.total(), s, c, all, (const T*)c.W, c.x, T(1), 0);
+      });
+    }
   }
   {
     auto k = k_finish<T>;

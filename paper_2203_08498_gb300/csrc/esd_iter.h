@@ -28,6 +28,7 @@ struct IterCtx {
   int M = 0;              // padded number of W columns (0, 8, 16, 24, 32, 64)
   T* samples = nullptr;   // sample slots, stride ld
   double* samples64 = nullptr;   // refinement form: FP64 slots receive xbase + x instead
+  double* x64 = nullptr;  // refinement form: the iterate is updated here in FP64 (x stays 0)
   const double* xbase = nullptr;  // refinement form: the FP64 iterate the inner x corrects
   double* ahist = nullptr;
   double* bhist = nullptr;

@@ -274,17 +274,25 @@ __global__ void k_fill_values(int nslices, const int4* mA, const int* rp, const 
   for (int k = 0; k < a.y; ++k) valA[a.x + k * kSlice + lane] = (valid && b + k < e) ? va[b + k] : 0.0;
 }
 
-// s_i = sum_j a_ij in FP64 (the row's own entries, padding adds zeros), stored as FP32
-__global__ void k_rowsum(SellView<double> A, int nslices, float* s) {
+// s_i = sum_j a_ij of the stored entries (padding adds zeros), by compensated (Kahan)
+// summation: the row sum of a diffusion matrix is a small difference of large entries, and
+// its own rounding error must stay far below it. Stored in FP64 and FP32.
+__global__ void k_rowsum(SellView<double> A, int nslices, double* s64, float* s32) {
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int sl = gw; sl < nslices; sl += nw) {
     const int4 md = A.meta[sl];
     if (lane >= md.w) continue;
-    double acc = 0.0;
-    for (int k = 0; k < md.y; ++k) acc += A.val[md.x + lane + k * kSlice];
-    s[md.z + lane] = (float)acc;
+    double sum = 0.0, comp = 0.0;
+    for (int k = 0; k < md.y; ++k) {
+      const double y = A.val[md.x + lane + k * kSlice] - comp;
+      const double t = sum + y;
+      comp = (t - sum) - y;
+      sum = t;
+    }
+    s64[md.z + lane] = sum;
+    s32[md.z + lane] = (float)sum;
   }
 }
 
@@ -314,9 +322,12 @@ void esd_matrix::ensure_fp32() {
     to_float(A.val, A.val32, A.entries, stream);
     if (!rowsum32.get()) {
       rowsum32.alloc(sizeof(float) * vec_stride());
+      rowsum64.alloc(sizeof(double) * vec_stride());
       ESD_CUDA(cudaMemsetAsync(rowsum32.get(), 0, rowsum32.bytes(), stream));
+      ESD_CUDA(cudaMemsetAsync(rowsum64.get(), 0, rowsum64.bytes(), stream));
     }
-    k_rowsum<<<max_grid_blocks(), kBlock, 0, stream>>>(A.view<double>(), nslices, rowsum32.as<float>());
+    k_rowsum<<<max_grid_blocks(), kBlock, 0, stream>>>(A.view<double>(), nslices, rowsum64.as<double>(),
+                                                       rowsum32.as<float>());
     ESD_CUDA(cudaGetLastError());
     a32_version = values_version;
   }

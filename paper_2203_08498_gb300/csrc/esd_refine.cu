@@ -1,6 +1,8 @@
 // FP64 iterative refinement around FP32 inner PCG solves (the precision form): the FP64
-// residual, the conversion of a refinement step's right-hand side to FP32, and the FP64
-// correction x += d. The inner solve is the FP32 instantiation of the iteration kernels.
+// residual and the conversion of a refinement step's right-hand side to FP32. The inner
+// solve is the FP32 instantiation of the iteration kernels; it adds its steps alpha p to
+// the FP64 iterate directly (x += d in FP64 as it goes), so no rounding of an FP32 iterate
+// separates x from the recursive residual.
 //
 // Two forms of the step. Restart: every inner solve is a fresh PCG run on A d = r.
 // Resume (residual replacement, after van der Vorst & Ye, SIAM J. Sci. Comput. 22, 2000):
@@ -31,9 +33,14 @@ __global__ void __launch_bounds__(kBlock, 4) k_ref_residual(IterCtx<double> c, S
     int r;
     const int s = set.slice(g, &r);
     const int4 md = c.Av.meta[s];
-    const double ax = row_fma(c.Av, md, lane, c.x, 0.0);
-    if (lane < md.w) {
-      const int i = md.z + lane;
+    const bool valid = lane < md.w;
+    const int iv = md.z + lane;
+    // A x in the difference form: its rounding error scales with |A x|, not |A| |x|, which
+    // lowers the floor the refinement can reach on stiff problems
+    const double ax = c.rowsum ? row_fma_diff(c.Av, md, lane, c.x, valid ? c.x[iv] : 0.0, valid ? c.rowsum[iv] : 0.0, 0.0)
+                               : row_fma(c.Av, md, lane, c.x, 0.0);
+    if (valid) {
+      const int i = iv;
       const double bi = c.b[i];
       const double ri = bi - ax;
       r64[i] = ri;
@@ -53,22 +60,42 @@ __global__ void __launch_bounds__(kBlock, 4) k_ref_residual(IterCtx<double> c, S
         rs->outer += 1;
         const double g2 = red[1] > 0.0 ? red[2] / red[1] : 0.0;
         rs->max_gap = fmax(rs->max_gap, sqrt(g2));
-        rs->fresh = rs->keep && (g2 > 0.25 || red[1] > 0.81 * rs->rr);
+        // an inner breakdown ((p, P^T A p) or rho not positive in FP32) also restarts: the
+        // step's x is the last good iterate, and p = z gives a clean direction again
+        const bool broke = st_in->status == ESD_ERR_BREAKDOWN || st_in->status == ESD_ERR_INTERNAL;
+        rs->fresh = rs->keep && (broke || g2 > 0.25 || red[1] > 0.81 * rs->rr);
+        if (red[1] < 0.81 * rs->rr_best) {
+          rs->rr_best = red[1];
+          rs->stalled = 0;
+        } else {
+          rs->stalled += 1;
+        }
         rs->restarts += rs->fresh;
+        rs->breakdowns += broke;
       }
       const double bb = red[0], rr = red[1];
+      if (!st_in) {
+        rs->rr_best = rr;
+        rs->stalled = 0;
+      }
       rs->bb = bb;
       rs->rr = rr;
       rs->tol2bb = c.st->scal0 * bb;  // the outer tolerance^2 travels in the outer state's scal0
       bool stop = false;
-      if (!(rr == rr)) {
+      if (!(rr == rr) || !(bb == bb)) {
         rs->status = ESD_ERR_BREAKDOWN;
+        rs->nonfinite = 1;
         stop = true;
       } else if (bb == 0.0 || rr <= rs->tol2bb) {
         stop = true;
-      } else if (st_in && rs->keep && st_in->status != ESD_OK) {
-        // a resumed run cannot go on after its iteration limit or a breakdown
-        rs->status = st_in->status;
+      } else if (st_in && rs->keep && st_in->status == ESD_ERR_MAXIT) {
+        // the iteration limit of a resumed run counts all its steps
+        rs->status = ESD_ERR_MAXIT;
+        stop = true;
+      } else if (st_in && rs->stalled >= 4) {
+        // four steps in a row without a 10% gain: the residual has reached the floor that
+        // its own FP64 rounding allows
+        rs->status = ESD_ERR_MAXIT;
         stop = true;
       } else if (rs->outer >= rs->max_outer) {
         rs->status = ESD_ERR_MAXIT;
@@ -122,11 +149,6 @@ __global__ void __launch_bounds__(kBlock, 4) k_ref_prep(int n, const double* r64
   }
 }
 
-// x += (double) d
-__global__ void __launch_bounds__(kBlock, 4) k_ref_apply(int n, double* x64, const float* x32) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x64[i] += (double)x32[i];
-}
-
 void launch_ref_residual(const IterCtx<double>& c, double* r64, const float* r32, RefineState* rs, State* st_in,
                          unsigned long long cond, cudaStream_t s) {
   const SliceSet& all = c.A->all;
@@ -137,11 +159,6 @@ void launch_ref_residual(const IterCtx<double>& c, double* r64, const float* r32
 void launch_ref_prep(int n, const double* r64, float* b32, float* x32, State* st_in, const RefineState* rs,
                      unsigned long long cond_in, cudaStream_t s) {
   k_ref_prep<<<max_grid_blocks(), kBlock, 0, s>>>(n, r64, b32, x32, st_in, rs, cond_in);
-  ESD_CUDA(cudaGetLastError());
-}
-
-void launch_ref_apply(int n, double* x64, const float* x32, cudaStream_t s) {
-  k_ref_apply<<<max_grid_blocks(), kBlock, 0, s>>>(n, x64, x32);
   ESD_CUDA(cudaGetLastError());
 }
 

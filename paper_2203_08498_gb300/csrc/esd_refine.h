@@ -8,7 +8,6 @@ void launch_ref_residual(const IterCtx<double>& c, double* r64, const float* r32
                          unsigned long long cond, cudaStream_t s);
 void launch_ref_prep(int n, const double* r64, float* b32, float* x32, State* st_in, const RefineState* rs,
                      unsigned long long cond_in, cudaStream_t s);
-void launch_ref_apply(int n, double* x64, const float* x32, cudaStream_t s);
 void convert_d2f(long long cnt, const double* a, float* b, cudaStream_t s);
 // b = a rounded to the nearest FP32 value (kept in FP64)
 void round_to_f32(long long cnt, const double* a, double* b, cudaStream_t s);

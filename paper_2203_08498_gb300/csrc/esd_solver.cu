@@ -190,6 +190,7 @@ struct esd_solver {
     c.samples = nullptr;
     c.samples64 = samples.get() ? samples.as<double>() : nullptr;  // FP64 full iterates
     c.xbase = vx.as<double>();
+    c.x64 = vx.as<double>();  // the inner iteration updates the FP64 iterate directly
     c.ahist = ahist.as<double>();
     c.bhist = bhist.as<double>();
     c.partials = partials.get();
@@ -290,6 +291,7 @@ struct esd_solver {
     cudaGraphConditionalHandle h_out, h_in;
     ESD_CUDA(cudaGraphConditionalHandleCreate(&h_out, g, 1, cudaGraphCondAssignDefault));
     IterCtx<double> c64 = ctx(ESD_PLAIN);
+    c64.rowsum = A->rowsum64.as<double>();  // difference-form FP64 residual
     IterCtx<float> c32 = ctx32(md);
     c32.x_zero = 1;  // every inner solve starts from d = 0
     RefineState* rs = rstate.as<RefineState>();
@@ -317,7 +319,6 @@ struct esd_solver {
         }
         ESD_CUDA(cudaStreamEndCapture(cap3, &inner));
         launch_finish<float>(c32, cap2);
-        launch_ref_apply(n, vx.as<double>(), x32.as<float>(), cap2);
         launch_ref_residual(c64, r64.as<double>(), r32.as<float>(), rs, state_in.as<State>(),
                             (unsigned long long)h_out, cap2);
       } catch (...) {
@@ -407,11 +408,13 @@ static int solve_refine(esd_solver* S, double* x, double tol, int32_t maxit, int
   if (iters) *iters = hr->inner_total;
   if (relres) *relres = S->last_relres;
   if (hr->status == ESD_ERR_MAXIT) {
-    set_last_error("refinement did not reach the tolerance within max_outer steps");
+    set_last_error(hr->stalled >= 4 ? "refinement stalled: the FP64 residual stopped decreasing above the tolerance"
+                                    : "refinement did not reach the tolerance within max_outer steps or maxit");
     return ESD_ERR_MAXIT;
   }
   if (hr->status == ESD_ERR_BREAKDOWN) {
-    set_last_error("non-finite residual in the refinement");
+    set_last_error(hr->nonfinite ? "non-finite residual in the refinement"
+                                 : "inner CG breakdown in the refinement");
     return ESD_ERR_BREAKDOWN;
   }
   return ESD_OK;
@@ -428,7 +431,7 @@ void esd_params_default(esd_params* p) {
   p->lmax = 0;
   p->rank_tol = 1e-12;
   p->precision = ESD_FP64;
-  p->inner_tol = 0.3;
+  p->inner_tol = 0.1;
   p->max_outer = 60;
   p->resume_direction = 1;
 }
@@ -787,6 +790,7 @@ int esd_profile_iterations(esd_solver* S, const double* b, double* x, int32_t re
     // the FP32 inner iteration on the system A d = b
     S->A->ensure_fp32();
     ESD_CUDA(cudaMemcpyAsync(S->state_in.get(), h, sizeof(State), cudaMemcpyHostToDevice, s));
+    // r0 = b - A x0 from an FP32 copy of x0; the iterations then update the FP64 x
     convert_d2f(n, S->vb.as<double>(), S->b32.as<float>(), s);
     convert_d2f(n, S->vx.as<double>(), S->x32.as<float>(), s);
     IterCtx<float> c = S->ctx32(S->mode);
@@ -795,7 +799,6 @@ int esd_profile_iterations(esd_solver* S, const double* b, double* x, int32_t re
       marks.emplace_back(new KernelMarks());
       launch_iteration<float>(c, s, marks.back().get());
     }
-    convert_f2d(n, S->x32.as<float>(), S->vx.as<double>(), s);
   } else {
     IterCtx<double> c = S->ctx(S->mode);
     launch_init<double>(c, s);

@@ -237,6 +237,108 @@ def config_c4(N: int = 128, seed: int = SEED_BASE + 3, corr: float = 4.0):
     return p, theta, x_target
 
 
+def _colour_major_csr(cols_nat: np.ndarray, vals: np.ndarray, shape, dt: float, h: float, name: str,
+                      coef=None) -> Problem:
+    """CSR in the 8-colour (2-colour in 2D) order from a dense per-node stencil table:
+    ``cols_nat[c, s]`` is the natural index of the s-th neighbour of natural node c (-1 when
+    absent) and ``vals[c, s]`` its value. Columns are sorted inside each row."""
+    n = int(np.prod(shape))
+    colour = _colour_of(shape).ravel(order="F")  # natural order, x fastest
+    perm = np.argsort(colour, kind="stable").astype(np.int64)  # perm[row] = natural node
+    inv = np.empty(n, dtype=np.int64)
+    inv[perm] = np.arange(n)
+    counts = np.bincount(colour, minlength=int(colour.max()) + 1)
+    colour_ptr = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    big = np.iinfo(np.int32).max
+    cr = cols_nat[perm]
+    vr = vals[perm]
+    valid = cr >= 0
+    cols = np.where(valid, inv[np.where(valid, cr, 0)], big).astype(np.int32)
+    order = np.argsort(cols, axis=1, kind="stable")
+    cols = np.take_along_axis(cols, order, axis=1)
+    vr = np.take_along_axis(vr, order, axis=1)
+    keep = cols != big
+    rowptr = np.concatenate([[0], np.cumsum(keep.sum(axis=1))]).astype(np.int32)
+    return Problem(n=n, rowptr=rowptr, colind=np.ascontiguousarray(cols[keep]),
+                   val=np.ascontiguousarray(vr[keep]), colour_ptr=colour_ptr, perm=perm, dt=dt,
+                   shape=tuple(shape), h=h, coef=coef, name=name)
+
+
+def fe27_diffusion(kelem: np.ndarray, aniso=(1.0, 1.0, 1e-3), dt: float = 1e-3, name: str = "") -> Problem:
+    """Q1 (trilinear) finite elements on the unit cube, homogeneous Dirichlet boundary.
+
+    ``kelem`` holds one coefficient per element, shape (E, E, E) with axis 0 = x; the
+    unknowns are the N = E - 1 interior nodes per axis, h = 1/E. The element tensor is
+    ``k_e diag(aniso)``; on a cube of side h the stiffness of axis d is
+    ``k_e aniso_d (h/36) (K1 (x) M1 (x) M1)`` with K1 = [[1,-1],[-1,1]] along d and
+    M1 = [[2,1],[1,2]] along the other two axes. A = I/dt + K / h^3 (27-point stencil).
+    """
+    E = kelem.shape[0]
+    N = E - 1
+    h = 1.0 / E
+    shape = (N, N, N)
+    n = N ** 3
+    k1 = np.array([[1.0, -1.0], [-1.0, 1.0]])
+    m1 = np.array([[2.0, 1.0], [1.0, 2.0]])
+    idx = np.indices(shape)  # node (i, j, k) -> interior node index 0..N-1 along each axis
+    nat = (idx[0] + N * (idx[1] + N * idx[2]))
+    offsets = [(a, b, c) for c in (-1, 0, 1) for b in (-1, 0, 1) for a in (-1, 0, 1)]
+    cols = np.full((n, 27), -1, dtype=np.int64)
+    vals = np.zeros((n, 27))
+    inv_dt = 0.0 if not np.isfinite(dt) else 1.0 / dt
+    scale = (h / 36.0) / h ** 3
+    for s, o in enumerate(offsets):
+        v = np.zeros(shape)
+        # elements holding both the node p and its neighbour p + o: along an axis with o_d = 0
+        # the two elements left and right of p, otherwise the one between them; element e
+        # spans the nodes e, e + 1 of the full grid (interior node i is full-grid node i + 1)
+        choices = [(-1, 0) if od == 0 else ((0,) if od == 1 else (-1,)) for od in o]
+        for e0 in choices[0]:
+            for e1 in choices[1]:
+                for e2 in choices[2]:
+                    e_off = (e0, e1, e2)
+                    a = [-eo for eo in e_off]          # local index of p in the element
+                    b = [a[d] + o[d] for d in range(3)]  # local index of p + o
+                    cf = (aniso[0] * k1[a[0], b[0]] * m1[a[1], b[1]] * m1[a[2], b[2]]
+                          + aniso[1] * m1[a[0], b[0]] * k1[a[1], b[1]] * m1[a[2], b[2]]
+                          + aniso[2] * m1[a[0], b[0]] * m1[a[1], b[1]] * k1[a[2], b[2]])
+                    # element index of interior node i (full-grid node i + 1) is i + 1 + e_off
+                    sl = tuple(slice(1 + e_off[d], 1 + e_off[d] + N) for d in range(3))
+                    v += cf * kelem[sl]
+        v *= scale
+        if o == (0, 0, 0):
+            v += inv_dt
+        ok = np.ones(shape, dtype=bool)
+        for d in range(3):
+            q = idx[d] + o[d]
+            ok &= (q >= 0) & (q < N)
+        qn = nat + o[0] + N * (o[1] + N * o[2])
+        cols[:, s] = np.where(ok, qn, -1).ravel(order="F")
+        vals[:, s] = np.where(ok, v, 0.0).ravel(order="F")
+    return _colour_major_csr(cols, vals, shape, dt, h, name or f"fe27_{N}cube")
+
+
+def config_c3(N: int = 192, seed: int = SEED_BASE + 2, sigma: float = 2.0, corr: float = 8.0,
+              dt: float = 1e-3) -> Problem:
+    """3D 27-point Q1 FE on N^3 interior nodes, tensor diag(1, 1, 1e-3) times a log-normal
+    per-element coefficient (sigma 2, correlation length 8 elements), dt = 1e-3 (backward
+    Euler, as C2), Gaussian source (centre 0.5, sigma 0.1) at the nodes."""
+    rng = np.random.default_rng(seed)
+    E = N + 1
+    kelem = np.exp(sigma * smooth_gaussian_field((E, E, E), corr, rng))
+    p = fe27_diffusion(kelem, dt=dt, name=f"fe27_{N}cube_aniso_lognormal")
+    x = (np.indices((N, N, N)) + 1.0) / E
+    src = np.exp(-sum((x[a] - 0.5) ** 2 for a in range(3)) / (2.0 * 0.1 * 0.1))
+    return _finish(p, src)
+
+
+def config_c5(N: int = 256, seed: int = SEED_BASE + 4, count: int = 64, rmin: float = 8.0,
+              rmax: float = 16.0, value: float = 1e6, dt: float = 1e-3) -> Problem:
+    """C2's recipe at 256^3 with 64 balls of coefficient 1e6 (radius 8-16 cells: C2's 4-8
+    at twice the resolution)."""
+    return config_c2(N=N, seed=seed, count=count, rmin=rmin, rmax=rmax, value=value, dt=dt)
+
+
 def small_3d(N: int, seed: int, count: int = 2, rmin: float = 1.5, rmax: float = 2.5,
              value: float = 1e3, dt: float = 1e-3) -> Problem:
     """A reduced C2-like problem for parity tests (odd N gives ragged colour sizes)."""
