@@ -35,6 +35,23 @@ enum { kModePlain = ESD_PLAIN, kModeDefl = ESD_DEFLATION, kModeSC = ESD_SUBSPACE
 #ifndef ESD_SWEEP_MINB
 #define ESD_SWEEP_MINB 4
 #endif
+// FP32 kernels move half the bytes per load, so they need more loads in flight per thread
+#ifndef ESD_SWEEP_MINB_F32
+#define ESD_SWEEP_MINB_F32 4
+#endif
+#ifndef ESD_ROW_UNROLL
+#define ESD_ROW_UNROLL 4
+#endif
+#ifndef ESD_ROW_UNROLL_F32
+#define ESD_ROW_UNROLL_F32 4
+#endif
+#define ESD_PRAGMA(x) _Pragma(#x)
+#define ESD_UNROLL(n) ESD_PRAGMA(unroll n)
+
+template <typename T>
+constexpr int sweep_minb() {
+  return sizeof(T) == 4 ? ESD_SWEEP_MINB_F32 : ESD_SWEEP_MINB;
+}
 
 template <typename T>
 __device__ __forceinline__ T ld_stream(const T* p) { return __ldcs(p); }
@@ -46,8 +63,13 @@ __device__ __forceinline__ T row_fma(const SellView<T>& M, const int4& md, int l
   const int* cp = M.col + md.x + lane;
   const T* vp = M.val + md.x + lane;
   T acc = init;
-#pragma unroll 4
-  for (int k = 0; k < md.y; ++k) acc = fma(ld_stream(vp + k * kSlice), v[ld_stream(cp + k * kSlice)], acc);
+  if (sizeof(T) == 4) {
+    ESD_UNROLL(ESD_ROW_UNROLL_F32)
+    for (int k = 0; k < md.y; ++k) acc = fma(ld_stream(vp + k * kSlice), v[ld_stream(cp + k * kSlice)], acc);
+  } else {
+    ESD_UNROLL(ESD_ROW_UNROLL)
+    for (int k = 0; k < md.y; ++k) acc = fma(ld_stream(vp + k * kSlice), v[ld_stream(cp + k * kSlice)], acc);
+  }
   return acc;
 }
 
@@ -60,9 +82,17 @@ __device__ __forceinline__ T row_fma_diff(const SellView<T>& M, const int4& md, 
   const int* cp = M.col + md.x + lane;
   const T* vp = M.val + md.x + lane;
   T acc = fma(si, vi, init);
-#pragma unroll 4
+  ESD_UNROLL(ESD_ROW_UNROLL_F32)
   for (int k = 0; k < md.y; ++k) acc = fma(ld_stream(vp + k * kSlice), v[ld_stream(cp + k * kSlice)] - vi, acc);
   return acc;
+}
+
+// Index of W / AW entry (row i = lane l of slice s, column k) in the layout of this context:
+// column-major with stride ld, or slice-major (the M columns of a 32-row slice contiguous,
+// so a warp streams one block instead of M columns far apart).
+template <int M, typename T>
+__device__ __forceinline__ size_t wix(const IterCtx<T>& c, int k, int i, int s, int lane) {
+  return c.wsm ? ((size_t)s * M + k) * kSlice + lane : (size_t)k * c.ld + i;
 }
 
 __device__ __forceinline__ void end_loop(unsigned long long cond) {
@@ -206,7 +236,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_bwd_plain(SellView<T> U, SliceSet
 // half the registers of FP64
 template <typename T, int M>
 constexpr int defl_minb() {
-  return M == 0 ? ESD_SWEEP_MINB : ((sizeof(T) == 4 ? M <= 32 : M <= 16) ? 2 : 1);
+  return M == 0 ? sweep_minb<T>() : ((sizeof(T) == 4 ? M <= 32 : M <= 16) ? 2 : 1);
 }
 
 template <typename T, int M>
@@ -247,7 +277,7 @@ __global__ void __launch_bounds__(kBlock, defl_minb<T, M>()) k_spmv_pq(IterCtx<T
       c.q[i] = qi;
       acc[0] = fma(pi, qi, acc[0]);
 #pragma unroll
-      for (int k = 0; k < M; ++k) acc[1 + k] = fma(c.AW[k * c.ld + i], pi, acc[1 + k]);
+      for (int k = 0; k < M; ++k) acc[1 + k] = fma(c.AW[wix<M>(c, k, i, s, lane)], pi, acc[1 + k]);
     }
   }
   if (grid_sum_multi<R>(acc, red, (T*)c.partials, &st->ticket[kTkSpmv])) {
@@ -335,7 +365,7 @@ __global__ void __launch_bounds__(kBlock, M == 0 ? 4 : defl_minb<T, M>()) k_upda
         }
         T t = c.q[i];
 #pragma unroll
-        for (int k = 0; k < DM; ++k) t = fma(-c.AW[k * c.ld + i], (T)ys[k], t);
+        for (int k = 0; k < DM; ++k) t = fma(-c.AW[wix<DM>(c, k, i, s, lane)], (T)ys[k], t);
         ri = fma(-alpha, t, c.r[i]);
         c.r[i] = ri;
         acc[0] = fma(ri, ri, acc[0]);
@@ -343,7 +373,7 @@ __global__ void __launch_bounds__(kBlock, M == 0 ? 4 : defl_minb<T, M>()) k_upda
         ri = c.r[i];
       }
 #pragma unroll
-      for (int k = 0; k < SCM; ++k) acc[2 + k] = fma(c.W[k * c.ld + i], ri, acc[2 + k]);
+      for (int k = 0; k < SCM; ++k) acc[2 + k] = fma(c.W[wix<SCM>(c, k, i, s, lane)], ri, acc[2 + k]);
       if (PRE == ESD_PRECOND_IC0) {
         const unsigned char f = c.sflags[s];
         if (f & 1) {
@@ -409,7 +439,7 @@ __global__ void __launch_bounds__(kBlock, M == 0 ? 4 : defl_minb<T, M>()) k_upda
 // is not the last stores its block totals in rho slot `slot`; the last launch adds its own
 // sum, the slots of the earlier launches and the level-0 part of the update, then sets beta.
 template <typename T>
-__global__ void __launch_bounds__(kBlock, ESD_SWEEP_MINB) k_fwd(IterCtx<T> c, SliceSet set, int slot, RhoSlots prev) {
+__global__ void __launch_bounds__(kBlock, sweep_minb<T>()) k_fwd(IterCtx<T> c, SliceSet set, int slot, RhoSlots prev) {
   __shared__ T red[red_size<1>()];
   __shared__ double own_s;
   pdl_enter();
@@ -451,7 +481,7 @@ __global__ void __launch_bounds__(kBlock, ESD_SWEEP_MINB) k_fwd(IterCtx<T> c, Sl
 // p_i = z_i [+ (W u)_i] + beta p_i. "elem" rows had z_i stored by the forward sweep and
 // only take the direction update.
 template <typename T, int SCM>
-__global__ void __launch_bounds__(kBlock, SCM == 0 ? ESD_SWEEP_MINB : 1) k_bwd(IterCtx<T> c, SliceSet set, SliceSet elem) {
+__global__ void __launch_bounds__(kBlock, SCM == 0 ? sweep_minb<T>() : 1) k_bwd(IterCtx<T> c, SliceSet set, SliceSet elem) {
   __shared__ double us[SCM > 0 ? SCM : 1];
   pdl_enter();
   State* st = c.st;
@@ -483,7 +513,7 @@ __global__ void __launch_bounds__(kBlock, SCM == 0 ? ESD_SWEEP_MINB : 1) k_bwd(I
       if (sweep) c.Y[i] = zic;
       T z = zic;
 #pragma unroll
-      for (int k = 0; k < SCM; ++k) z = fma(c.W[k * c.ld + i], (T)us[k], z);
+      for (int k = 0; k < SCM; ++k) z = fma(c.W[wix<SCM>(c, k, i, s, lane)], (T)us[k], z);
       c.p[i] = first ? z : fma(beta, pold, z);
     }
   }
@@ -510,7 +540,7 @@ __global__ void __launch_bounds__(kBlock, SCM == 0 ? 4 : 1) k_dir(IterCtx<T> c, 
       const int i = md.z + lane;
       T z = c.r[i];
 #pragma unroll
-      for (int k = 0; k < SCM; ++k) z = fma(c.W[k * c.ld + i], (T)us[k], z);
+      for (int k = 0; k < SCM; ++k) z = fma(c.W[wix<SCM>(c, k, i, s, lane)], (T)us[k], z);
       c.p[i] = first ? z : fma(beta, c.p[i], z);
     }
   }
@@ -576,11 +606,11 @@ __global__ void __launch_bounds__(kBlock) k_tallT(IterCtx<T> c, SliceSet set, co
       const int i = md.z + lane;
       const T vi = v[i];
 #pragma unroll
-      for (int k = 0; k < M; ++k) acc[k] = fma(X[k * c.ld + i], vi, acc[k]);
+      for (int k = 0; k < M; ++k) acc[k] = fma(X[wix<M>(c, k, i, s, lane)], vi, acc[k]);
       if (Y2) {
         const T wi = w[i];
 #pragma unroll
-        for (int k = 0; k < M; ++k) acc[k] = fma(-Y2[k * c.ld + i], wi, acc[k]);
+        for (int k = 0; k < M; ++k) acc[k] = fma(-Y2[wix<M>(c, k, i, s, lane)], wi, acc[k]);
       }
     }
   }
@@ -614,7 +644,7 @@ __global__ void __launch_bounds__(kBlock) k_tall_axpy(IterCtx<T> c, SliceSet set
       const int i = md.z + lane;
       T t = T(0);
 #pragma unroll
-      for (int k = 0; k < M; ++k) t = fma(Z[k * c.ld + i], (T)us[k], t);
+      for (int k = 0; k < M; ++k) t = fma(Z[wix<M>(c, k, i, s, lane)], (T)us[k], t);
       const T vi = fma(sign, t, v[i]);
       v[i] = vi;
       acc[0] = fma(vi, vi, acc[0]);
@@ -643,7 +673,7 @@ __global__ void __launch_bounds__(kBlock) k_tall_axpy64(IterCtx<T> c, SliceSet s
       const int i = md.z + lane;
       T t = T(0);
 #pragma unroll
-      for (int k = 0; k < M; ++k) t = fma(Z[k * c.ld + i], (T)us[k], t);
+      for (int k = 0; k < M; ++k) t = fma(Z[wix<M>(c, k, i, s, lane)], (T)us[k], t);
       c.x64[i] += (double)t;
     }
   }

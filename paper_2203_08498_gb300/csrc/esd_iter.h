@@ -41,6 +41,7 @@ struct IterCtx {
   int mode = ESD_PLAIN;
   int pre = ESD_PRECOND_IC0;
   int x_zero = 0;  // the start vector is known to be zero (r0 = b without a product)
+  int wsm = 0;     // W and AW slice-major: entry (row of slice s, lane l; column k) at (s M + k) 32 + l
 };
 
 // Optional event marks between the kernels of a launch sequence (profiling): mark() records

@@ -171,6 +171,22 @@ __global__ void k_f2d(long long cnt, const float* a, double* b) {
     b[i] = (double)a[i];
 }
 
+// FP32 slice-major copy of a column-major n x M block: row i sits at lane (rowpos & 31) of
+// slice (rowpos >> 5); the M columns of one slice are stored one after another.
+__global__ void k_to_slice_major(int n, const int* rowpos, const double* X, size_t ld, int M, float* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int pos = rowpos[i];
+    const size_t base = (size_t)(pos >> 5) * M * kSlice + (pos & 31);
+    for (int k = 0; k < M; ++k) out[base + (size_t)k * kSlice] = (float)X[(size_t)k * ld + i];
+  }
+}
+
+void to_slice_major(int n, const int* rowpos, const double* X, size_t ld, int M, float* out, cudaStream_t s) {
+  if (n <= 0 || M <= 0) return;
+  k_to_slice_major<<<max_grid_blocks(), kBlock, 0, s>>>(n, rowpos, X, ld, M, out);
+  ESD_CUDA(cudaGetLastError());
+}
+
 __global__ void k_round_f32(long long cnt, const double* a, double* b) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cnt; i += (long long)gridDim.x * blockDim.x)
     b[i] = (double)(float)a[i];

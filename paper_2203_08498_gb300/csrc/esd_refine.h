@@ -9,6 +9,8 @@ void launch_ref_residual(const IterCtx<double>& c, double* r64, const float* r32
 void launch_ref_prep(int n, const double* r64, float* b32, float* x32, State* st_in, const RefineState* rs,
                      unsigned long long cond_in, cudaStream_t s);
 void convert_d2f(long long cnt, const double* a, float* b, cudaStream_t s);
+// FP32 slice-major copy (the layout IterCtx::wsm selects) of a column-major n x M block
+void to_slice_major(int n, const int* rowpos, const double* X, size_t ld, int M, float* out, cudaStream_t s);
 // b = a rounded to the nearest FP32 value (kept in FP64)
 void round_to_f32(long long cnt, const double* a, double* b, cudaStream_t s);
 void convert_f2d(long long cnt, const float* a, double* b, cudaStream_t s);

@@ -186,6 +186,7 @@ struct esd_solver {
       c.AW = AW32.as<float>();
       c.Einv = Einv.as<double>();
       c.M = M;
+      c.wsm = 1;  // W32 / AW32 are slice-major
     }
     c.samples = nullptr;
     c.samples64 = samples.get() ? samples.as<double>() : nullptr;  // FP64 full iterates
@@ -337,15 +338,18 @@ struct esd_solver {
     ESD_CUDA(cudaStreamEndCapture(cap, &g));
   }
 
-  // FP32 copies of W and AW for the inner solves
+  // FP32 slice-major copies of W and AW for the inner solves (padding lanes and columns 0)
   void refresh_w32() {
     if (!fp32 || !have_W) return;
+    const size_t entries = (size_t)A->nslices * kSlice * kMaxM;
     if (!W32.get()) {
-      W32.alloc(sizeof(float) * ld * kMaxM);
-      AW32.alloc(sizeof(float) * ld * kMaxM);
+      W32.alloc(sizeof(float) * entries);
+      AW32.alloc(sizeof(float) * entries);
     }
-    convert_d2f((long long)ld * M, W.as<double>(), W32.as<float>(), stream);
-    convert_d2f((long long)ld * M, AW.as<double>(), AW32.as<float>(), stream);
+    ESD_CUDA(cudaMemsetAsync(W32.get(), 0, W32.bytes(), stream));
+    ESD_CUDA(cudaMemsetAsync(AW32.get(), 0, AW32.bytes(), stream));
+    to_slice_major(A->n, A->rowpos.as<int>(), W.as<double>(), ld, M, W32.as<float>(), stream);
+    to_slice_major(A->n, A->rowpos.as<int>(), AW.as<double>(), ld, M, AW32.as<float>(), stream);
   }
 };
 

@@ -1,12 +1,13 @@
 """Per-kernel timing of one PCG iteration, outside any CUDA graph (for ncu and for users).
 
-python -m paper_2203_08498_gb300.profile --grid 96 --mode deflation --m 16 --reps 5
+python -m paper_2203_08498_gb300.profile --grid 96 --mode deflation --m 16 --reps 5 [--precision fp32]
 
 Builds the heterogeneous-diffusion matrix of the given grid, factors it, installs an
 orthonormal W of m columns (random, seeded: the per-iteration cost does not depend on W's
 values) and runs reps iterations with esd_profile_iterations, which launches each kernel of
-the iteration body directly on the stream with CUDA events between them. Prints one JSON
-line with the average milliseconds per kernel.
+the iteration body directly on the stream with CUDA events between them (FP64 kernels, or
+with --precision fp32 the FP32 inner kernels of the refinement form). Prints one JSON line
+with the average milliseconds per kernel.
 """
 from __future__ import annotations
 
@@ -33,6 +34,7 @@ def main(argv=None):
     ap.add_argument("--m", type=int, default=16)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--precond", default="ic0", choices=["ic0", "none"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     a = ap.parse_args(argv)
     r = a.grid / 128.0
     p = wl.config_c2(N=a.grid, rmin=4 * r, rmax=8 * r)
@@ -41,7 +43,8 @@ def main(argv=None):
     pre = esd.PRECOND_IC0 if a.precond == "ic0" else esd.PRECOND_NONE
     if pre == esd.PRECOND_IC0:
         A.factor_ic0()
-    S = esd.Solver(A, precond=pre, maxit_cap=a.reps + 10, sample_cap=0)
+    prec = esd.FP64 if a.precision == "fp64" else esd.FP32_REFINE
+    S = esd.Solver(A, precond=pre, maxit_cap=a.reps + 10, sample_cap=0, precision=prec)
     mode = {"plain": esd.PLAIN, "deflation": esd.DEFLATION, "sc": esd.SUBSPACE_CORRECTION}[a.mode]
     if mode != esd.PLAIN:
         W, _ = np.linalg.qr(np.random.default_rng(0).standard_normal((p.n, a.m)))
@@ -51,7 +54,7 @@ def main(argv=None):
     x = torch.zeros(p.n, dtype=torch.float64, device=dev)
     prof = S.profile_iterations(b, x, reps=a.reps)
     print(json.dumps({"grid": a.grid, "n": p.n, "nnz": p.nnz, "mode": a.mode, "m": a.m,
-                      "kernels_ms": prof}), flush=True)
+                      "precision": a.precision, "kernels_ms": prof}), flush=True)
 
 
 if __name__ == "__main__":

@@ -395,3 +395,37 @@ def test_full_size_128cube_kernels_and_first_solve():
     out = oracle.System(p, ic).solve(p.source, tol=1e-8, sample_m=16)
     assert st == esd.OK and abs(it - out["iters"]) <= 1
     assert rel(x, out["x"]) <= 1e-10
+
+
+@pytest.mark.parametrize("mode_name", ["plain", "deflation"])
+def test_full_128cube_sequence_counts_match_oracle(mode_name):
+    """The whole 20-system 128^3 sequence (W from m = 16 samples of system 1) against the
+    oracle's own run of it (oracle/data, written by oracle/sequence_counts.py from the oracle
+    alone): every system's iteration count within +-1, every true residual below 1e-8."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(oracle.__file__), "data", f"fv7_128cube_{mode_name}_counts.json")
+    ref = json.load(open(path))
+    p = wl.config_c2()
+    A = esd.Matrix.from_problem(p)
+    A.factor_ic0()
+    S = esd.Solver(A, sample_cap=16)
+    src = dev(p.source)
+    x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+    b = torch.empty_like(x)
+    mode = {"plain": esd.PLAIN, "deflation": esd.DEFLATION}[mode_name]
+    its = []
+    for t in range(len(ref["iterations"])):
+        S.backward_euler_rhs(x, src, 1.0 / p.dt, b)
+        if t == 0:
+            S.set_mode(esd.PLAIN)
+            st, it, rr = S.solve(b, x, tol=ref["tol"], sample_m=ref["m"] if mode != esd.PLAIN else 0)
+            if mode != esd.PLAIN:
+                S.sample_and_build_W()
+                S.set_mode(mode)
+        else:
+            st, it, rr = S.solve(b, x, tol=ref["tol"])
+        assert st == esd.OK and S.true_relres() <= 1.05 * ref["tol"]
+        its.append(it)
+    diff = np.abs(np.array(its) - np.array(ref["iterations"]))
+    assert diff.max() <= 1, (its, ref["iterations"])
