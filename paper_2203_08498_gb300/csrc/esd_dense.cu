@@ -192,12 +192,15 @@ __device__ void warp_jacobi(double* A, double* V, int m) {
     }
     off = warp_sum(off);
     dia = warp_sum(dia);
-    if (off <= 1e-32 * dia || off == 0.0) break;
+    // off-diagonal mass 1e-28 of the diagonal: far below what any use of the eigenvalues
+    // needs, and reachable (1e-32 sat at the rounding floor and ran every sweep)
+    if (off <= 1e-28 * dia || off == 0.0) break;
     for (int p = 0; p < m - 1; ++p) {
       for (int q = p + 1; q < m; ++q) {
         const double apq = A[p * m + q];
-        if (apq == 0.0) continue;
         const double app = A[p * m + p], aqq = A[q * m + q];
+        // negligible coupling: the rotation would change nothing at working precision
+        if (fabs(apq) <= 1e-18 * sqrt(fabs(app * aqq)) || apq == 0.0) continue;
         const double tau = (aqq - app) / (2.0 * apq);
         const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
         const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
@@ -256,9 +259,10 @@ __device__ void warp_eig_sorted(const double* G, double* work, double* V, double
 //   mbar < m: S = D V_k Lambda_k^-1/2            (SVQB on the kept directions)
 __global__ void k_w_phase1(const double* G0, int m, double rank_tol, double* ws, double* S,
                            int* out_mbar) {
+  extern __shared__ double eig_smem[];  // the Jacobi iterate and its rotations (2 m^2)
   double* G = ws + kWsG * kSq;
-  double* work = ws + kWsWork * kSq;
-  double* V = ws + kWsV * kSq;
+  double* work = eig_smem;
+  double* V = eig_smem + m * m;
   double* Vs = ws + kWsVs * kSq;
   double* L = ws + kWsL * kSq;
   double* Li = ws + kWsLi * kSq;
@@ -320,8 +324,9 @@ __global__ void k_w_phase2(const double* G, int m, double* ws, double* S, int* s
 // zero-padded to pad_cols(mkeep) squared. status: 0 ok, 1 E not positive definite.
 __global__ void k_w_phase3(double* E, int m, double theta, double* ws, double* ritz, double* T,
                            int* mkeep, double* Einv, int* status) {
-  double* work = ws + kWsWork * kSq;
-  double* V = ws + kWsV * kSq;
+  extern __shared__ double eig_smem[];  // the Jacobi iterate and its rotations (2 m^2)
+  double* work = eig_smem;
+  double* V = eig_smem + m * m;
   double* Vs = ws + kWsVs * kSq;
   double* L = ws + kWsL * kSq;
   double* Li = ws + kWsLi * kSq;
@@ -374,6 +379,15 @@ __global__ void k_w_phase3(double* E, int m, double theta, double* ws, double* r
 }
 
 // ------------------------------------------------------------------ host driver
+
+// Dynamic shared memory of the one-warp eigensolver (iterate and rotations, 2 m^2 doubles;
+// 64 KB at m = 64, above the default 48 KB, so the kernels are allowed it first).
+static size_t eig_smem_bytes(int m) {
+  const int bytes = 2 * kMaxM * kMaxM * (int)sizeof(double);
+  ESD_CUDA(cudaFuncSetAttribute(k_w_phase1, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  ESD_CUDA(cudaFuncSetAttribute(k_w_phase3, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  return 2 * (size_t)m * m * sizeof(double);
+}
 
 static void gram(int n, const double* X, int mx, const double* Y, int my, size_t ld, bool sym,
                  DevBuf& partials, double* out, unsigned int* ticket, cudaStream_t s) {
@@ -443,7 +457,7 @@ int build_aux(const esd_matrix* A, AuxBuild& b, const double* X, int m, bool ort
   const double* basis = X;
   if (orth) {
     gram(n, X, m, X, m, ld, true, b.partials, G0, tk, s);
-    k_w_phase1<<<1, 32, 0, s>>>(G0, m, rank_tol, ws, S, dints);
+    k_w_phase1<<<1, 32, eig_smem_bytes(m), s>>>(G0, m, rank_tol, ws, S, dints);
     ESD_CUDA(cudaGetLastError());
     ESD_CUDA(cudaMemcpyAsync(h_ints, dints, sizeof(int), cudaMemcpyDeviceToHost, s));
     ESD_CUDA(cudaStreamSynchronize(s));
@@ -467,7 +481,7 @@ int build_aux(const esd_matrix* A, AuxBuild& b, const double* X, int m, bool ort
   // AW = A W and E = W^T (A W) for the basis
   launch_spmm(A, basis, b.work2.as<double>(), ld, mcols, s);
   gram(n, basis, mcols, b.work2.as<double>(), mcols, ld, false, b.partials, E, tk, s);
-  k_w_phase3<<<1, 32, 0, s>>>(E, mcols, theta, ws, ritz, dT, dints + 2, Einv, dints + 3);
+  k_w_phase3<<<1, 32, eig_smem_bytes(mcols), s>>>(E, mcols, theta, ws, ritz, dT, dints + 2, Einv, dints + 3);
   ESD_CUDA(cudaGetLastError());
   ESD_CUDA(cudaMemcpyAsync(h_ints + 2, dints + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
   ESD_CUDA(cudaStreamSynchronize(s));

@@ -89,33 +89,48 @@ enum ValidBits { kBadRowptr = 1, kBadCol = 2, kUnsorted = 4, kNoDiag = 8, kSameC
 
 // Every index is checked before it is used, so malformed input sets error bits instead of
 // reading out of bounds.
+// One thread per row. The colour adjacency is collected as a mask of neighbour colours per
+// row, merged across the lanes of a warp that share a row colour, and written with one
+// atomic per (warp, colour pair): one atomic per entry on 64 words serialised the launch.
 __global__ void k_validate(int n, long long nnz, const int* rp, const int* ci, const int* cp,
                            int ncol, int* diagpos, unsigned* adj, int* err) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int b = rp[i], e = rp[i + 1];
-  unsigned bad = 0;
-  if (b < 0 || e < b || (long long)e > nnz) { bad |= kBadRowptr; b = 0; e = 0; }
-  int ci_row = colour_of(i, cp, ncol);
-  int dpos = -1, prev = -1;
-  for (int k = b; k < e; ++k) {
-    int j = ci[k];
-    if (j < 0 || j >= n) { bad |= kBadCol; continue; }
-    if (j <= prev) bad |= kUnsorted;
-    prev = j;
-    if (j == i) { dpos = k; continue; }
-    int cj = colour_of(j, cp, ncol);
-    if (cj == ci_row) bad |= kSameColour;
-    atomicOr(&adj[ci_row * ncol + cj], 1u);
-    // structural symmetry: (j, i) must exist
-    int jb = rp[j], je = rp[j + 1];
-    if (jb < 0 || je < jb || (long long)je > nnz || find_col(ci, jb, je, i) < 0) bad |= kNotSym;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = i < n;
+  unsigned long long mask = 0ull;  // neighbour colours (ncol <= 64)
+  int ci_row = -1;
+  if (active) {
+    int b = rp[i], e = rp[i + 1];
+    unsigned bad = 0;
+    if (b < 0 || e < b || (long long)e > nnz) { bad |= kBadRowptr; b = 0; e = 0; }
+    ci_row = colour_of(i, cp, ncol);
+    int dpos = -1, prev = -1;
+    for (int k = b; k < e; ++k) {
+      int j = ci[k];
+      if (j < 0 || j >= n) { bad |= kBadCol; continue; }
+      if (j <= prev) bad |= kUnsorted;
+      prev = j;
+      if (j == i) { dpos = k; continue; }
+      int cj = colour_of(j, cp, ncol);
+      if (cj == ci_row) bad |= kSameColour;
+      mask |= 1ull << cj;
+      // structural symmetry: (j, i) must exist
+      int jb = rp[j], je = rp[j + 1];
+      if (jb < 0 || je < jb || (long long)je > nnz || find_col(ci, jb, je, i) < 0) bad |= kNotSym;
+    }
+    if (dpos < 0) bad |= kNoDiag;
+    diagpos[i] = dpos < 0 ? b : dpos;
+    if (bad) {
+      atomicOr(&err[0], (int)bad);
+      atomicMin(&err[1], i);
+    }
   }
-  if (dpos < 0) bad |= kNoDiag;
-  diagpos[i] = dpos < 0 ? b : dpos;
-  if (bad) {
-    atomicOr(&err[0], (int)bad);
-    atomicMin(&err[1], i);
+  const unsigned peers = __match_any_sync(0xffffffffu, ci_row);
+  const unsigned lo = __reduce_or_sync(peers, (unsigned)(mask & 0xffffffffull));
+  const unsigned hi = __reduce_or_sync(peers, (unsigned)(mask >> 32));
+  if (ci_row >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) {
+    const unsigned long long all = ((unsigned long long)hi << 32) | lo;
+    for (int cj = 0; cj < ncol; ++cj)
+      if ((all >> cj) & 1ull) atomicOr(&adj[ci_row * ncol + cj], 1u);
   }
 }
 
