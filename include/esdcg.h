@@ -51,6 +51,13 @@ enum esd_precision {
   ESD_FP32_REFINE = 1  /* FP32 inner PCG inside an FP64 iterative refinement */
 };
 
+/* Which iterates a sampled solve (sample_m > 0) keeps, Section 4.2. */
+enum esd_sampling {
+  ESD_SAMPLING_A = 0,  /* Appendix A: a spread of iterations fixed only at the stop */
+  ESD_SAMPLING_B = 1   /* the iterate whose relative residual first reaches tol^(s/(m+1)),
+                          s = 1..m (an iteration reaching several levels kept once); FP64 only */
+};
+
 typedef struct esd_matrix esd_matrix;
 typedef struct esd_solver esd_solver;
 
@@ -163,9 +170,11 @@ typedef struct {
   int32_t max_outer;   /* ESD_FP32_REFINE: refinement steps allowed */
   int32_t resume_direction; /* ESD_FP32_REFINE: 1 = every step resumes CG with the kept search
                                direction (residual replacement), 0 = every step restarts CG */
+  int32_t sampling;    /* esd_sampling: which iterates a sampled solve keeps */
 } esd_params;
 
-/* Default parameters: IC(0), maxit_cap 20000, sample_cap 32, lmax 0, rank_tol 1e-12, FP64;
+/* Default parameters: IC(0), maxit_cap 20000, sample_cap 32, lmax 0, rank_tol 1e-12, FP64,
+ * sampling method A;
  * for ESD_FP32_REFINE inner_tol 0.1, max_outer 60, resume_direction 1. */
 void esd_params_default(esd_params* p);
 

@@ -55,6 +55,7 @@ class _System(C.Structure):
 class _SolveIO(C.Structure):
     _fields_ = [
         ("tol", C.c_double), ("maxit", C.c_int), ("sample_m", C.c_int), ("lmax", C.c_int),
+        ("sample_method", C.c_int),
         ("samples", C.c_void_p), ("sample_iter", C.c_void_p), ("alpha_hist", C.c_void_p),
         ("beta_hist", C.c_void_p), ("res_hist", C.c_void_p), ("wtr_hist", C.c_void_p),
         ("iters", C.c_int), ("relres", C.c_double), ("status", C.c_int),
@@ -270,17 +271,20 @@ class System:
         return z
 
     def solve(self, b, x0=None, tol: float = 1e-8, maxit: int = 20000, sample_m: int = 0,
-              lmax: int | None = None, history: bool = True):
+              lmax: int | None = None, history: bool = True, sample_method: int = 0):
         """PCG / deflated PCG (Algorithm PCG-con without the power method; Algorithm DPCG).
 
         Stops when ``||r_i||_2 <= tol ||b||_2``; the iteration count is the number of
-        alpha steps. ``sample_m > 0`` stores iterates by sampling method A (Appendix A).
+        alpha steps. ``sample_m > 0`` stores iterates by sampling method A (Appendix A;
+        ``sample_method = 0``) or B (Section 4.2, ``sample_method = 1``: the iterate whose
+        relative residual first reaches ``tol^(s/(m+1))``, s = 1..m; an iteration that first
+        reaches several levels is stored once; slots are filled in order).
         """
         n = self.prob.n
         b = _c(b, np.float64)
         x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
         io = _SolveIO()
-        io.tol, io.maxit, io.sample_m = tol, maxit, sample_m
+        io.tol, io.maxit, io.sample_m, io.sample_method = tol, maxit, sample_m, sample_method
         io.lmax = default_lmax(sample_m, maxit) if (sample_m > 1 and lmax is None) else (lmax or 0)
         samples = np.zeros((n, sample_m), order="F") if sample_m > 0 else None
         siter = np.zeros(max(sample_m, 1), dtype=np.int32)

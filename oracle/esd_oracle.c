@@ -12,7 +12,8 @@
  *   - deflated PCG (Algorithm "Deflated PCG") with P = I - W E^{-1} (AW)^T
  *     (Eq. deflation:projector), P^T A p formed explicitly as a vector and the final
  *     correction x = P x_i + W E^{-1} W^T b (Eq. x1);
- *   - sampling method A (Appendix A), samples taken only while the solve has not stopped.
+ *   - sampling method A (Appendix A) or B (Section 4.2, the relative residual levels),
+ *     samples taken only while the solve has not stopped.
  * Dot products use pairwise summation. E = W^T A W is applied through its dense
  * Cholesky factor. The paper's beta carries a spurious minus sign in Algorithm DPCG; the
  * oracle uses beta = +rho_{i+1}/rho_i, which is the standard CG recurrence.
@@ -223,6 +224,7 @@ typedef struct {
   int maxit;
   int sample_m;  /* 0: no sampling */
   int lmax;      /* sampling method A parameter, m^lmax > maxit */
+  int sample_method; /* 0: method A (Appendix A), 1: method B (residual levels) */
   double* samples;  /* n x sample_m column-major, or NULL */
   int* sample_iter; /* per slot: iteration whose iterate it holds (0 = empty) */
   double* alpha_hist; /* maxit entries or NULL */
@@ -282,6 +284,23 @@ static void sample_a(int i, int m, int lmax, int* h, long n, const double* x, do
   if (i == (*h) * m) *h *= 2;
 }
 
+/* Sampling method B (Section 4.2): with the stopping criterion ||r|| <= tol ||b||, the
+ * iterate whose relative residual first reaches tol^(s/(m+1)), s = 1..m, is stored. An
+ * iteration that first reaches several levels stores its iterate once, in the next slot.
+ * The test is made on squares, ||r||^2/||b||^2 <= (tol^2)^(s/(m+1)). reached counts the
+ * levels reached so far, used the slots filled. */
+static void sample_b(int i, int m, double rel2, double tol2, int* reached, int* used, long n, const double* x,
+                     double* samples, int* sample_iter) {
+  int lev = *reached;
+  while (lev < m && rel2 <= pow(tol2, (double)(lev + 1) / (double)(m + 1))) ++lev;
+  if (lev > *reached) {
+    memcpy(samples + (long)(*used) * n, x, sizeof(double) * n);
+    sample_iter[*used] = i;
+    *used += 1;
+    *reached = lev;
+  }
+}
+
 /* Iteration numbers at which sampling method A stores a vector when the solve converges at
  * iteration N (no sample at the converging iteration). slot_iter[m] receives, per slot, the
  * iteration of the vector it finally holds (0 = never filled). */
@@ -307,8 +326,9 @@ int orc_solve(const orc_system* s, const double* b, double* x, orc_solve_io* io)
   double* p = (double*)malloc(sizeof(double) * n);
   double* q = (double*)malloc(sizeof(double) * n);
   double* w = (double*)malloc(sizeof(double) * n);
-  int status = ORC_OK, h = 1, iters = 0;
-  double bn = sqrt(orc_dot(n, b, b));
+  int status = ORC_OK, h = 1, iters = 0, b_reached = 0, b_used = 0;
+  const double bb = orc_dot(n, b, b);
+  double bn = sqrt(bb);
   if (io->sample_iter)
     for (int k = 0; k < io->sample_m; ++k) io->sample_iter[k] = 0;
   if (io->sample_m > 0 && s->mode == 1) {
@@ -355,11 +375,18 @@ int orc_solve(const orc_system* s, const double* b, double* x, orc_solve_io* io)
       }
       rho_old = rho;
       iters = i;
-      rn = sqrt(orc_dot(n, r, r));
+      const double rr = orc_dot(n, r, r);
+      rn = sqrt(rr);
       if (io->res_hist) io->res_hist[i] = rn / bn;
       if (io->wtr_hist) io->wtr_hist[i] = wtr_max(s, r, bn);
       if (rn <= io->tol * bn) break;
-      if (io->sample_m > 0) sample_a(i, io->sample_m, io->lmax, &h, n, x, io->samples, io->sample_iter);
+      if (io->sample_m > 0) {
+        if (io->sample_method == 1)
+          sample_b(i, io->sample_m, rr / bb, io->tol * io->tol, &b_reached, &b_used, n, x, io->samples,
+                   io->sample_iter);
+        else
+          sample_a(i, io->sample_m, io->lmax, &h, n, x, io->samples, io->sample_iter);
+      }
       if (i == io->maxit) status = ORC_ERR_MAXIT;
     }
   }

@@ -21,7 +21,7 @@ from . import _build
 
 __all__ = [
     "lib", "EsdError", "Matrix", "Solver", "PLAIN", "DEFLATION", "SUBSPACE_CORRECTION",
-    "PRECOND_NONE", "PRECOND_IC0", "FP64", "FP32_REFINE", "EsdParams", "HEADER_SYMBOLS",
+    "PRECOND_NONE", "PRECOND_IC0", "FP64", "FP32_REFINE", "SAMPLING_A", "SAMPLING_B", "EsdParams", "HEADER_SYMBOLS",
     "esd_create_matrix", "esd_matrix_destroy", "esd_matrix_info", "esd_factor_ic0", "esd_matrix_spmv",
     "esd_matrix_apply_ic", "esd_pattern_grad", "esd_params_default", "esd_solver_create",
     "esd_solver_destroy", "esd_set_mode", "esd_solve", "esd_true_relres", "esd_last_solve_info",
@@ -39,6 +39,7 @@ ERR_INTERNAL = -10
 PLAIN, DEFLATION, SUBSPACE_CORRECTION = 0, 1, 2
 PRECOND_NONE, PRECOND_IC0 = 0, 1
 FP64, FP32_REFINE = 0, 1
+SAMPLING_A, SAMPLING_B = 0, 1
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "esdcg.h")
 
@@ -66,7 +67,8 @@ class EsdFvGrid(C.Structure):
 class EsdParams(C.Structure):
     _fields_ = [("precond", C.c_int32), ("maxit_cap", C.c_int32), ("sample_cap", C.c_int32),
                 ("lmax", C.c_int32), ("rank_tol", C.c_double), ("precision", C.c_int32),
-                ("inner_tol", C.c_double), ("max_outer", C.c_int32), ("resume_direction", C.c_int32)]
+                ("inner_tol", C.c_double), ("max_outer", C.c_int32), ("resume_direction", C.c_int32),
+                ("sampling", C.c_int32)]
 
 
 _lib = None
@@ -409,11 +411,13 @@ class Solver:
     """``esd_solver`` bound to a Matrix; keeps the matrix alive."""
 
     def __init__(self, matrix: Matrix, precond=PRECOND_IC0, maxit_cap=20000, sample_cap=32, lmax=0,
-                 rank_tol=1e-12, precision=FP64, inner_tol=0.1, max_outer=60, resume_direction=1):
+                 rank_tol=1e-12, precision=FP64, inner_tol=0.1, max_outer=60, resume_direction=1,
+                 sampling=SAMPLING_A):
         p = esd_params_default()
         p.precond, p.maxit_cap, p.sample_cap, p.lmax = precond, maxit_cap, sample_cap, lmax
         p.rank_tol, p.precision, p.inner_tol, p.max_outer = rank_tol, precision, inner_tol, max_outer
         p.resume_direction = resume_direction
+        p.sampling = sampling
         self.matrix = matrix
         self.maxit_cap = maxit_cap
         self._h = esd_solver_create(matrix.handle, p)

@@ -79,6 +79,9 @@ struct State {
   int guard;        // loop bodies started; a second, reduction-free bound on the loop
   int defer_sample; // resumed runs: a stopping run leaves its sample to the run that resumes
   int fresh_dir;    // the next direction update starts afresh (p = z) without resetting iter
+  int samp_method;  // 0: sampling method A, 1: method B (relative residual levels)
+  int sb_reached;   // method B: residual levels reached so far
+  int sb_used;      // method B: slots filled so far
   int slot_iter[kMaxM];
   double y[kMaxM];  // deflation: E^{-1} (AW)^T p
   double u[kMaxM];  // subspace correction / projection: E^{-1} f

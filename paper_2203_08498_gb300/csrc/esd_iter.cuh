@@ -132,6 +132,21 @@ __device__ __forceinline__ void sampling_a(State* st) {
   if (i == st->h * m) st->h *= 2;
 }
 
+// Sampling method B (Section 4.2): the iterate whose relative residual first reaches
+// tol^(s/(m+1)), s = 1..m, is kept; an iteration that reaches several new levels is kept
+// once, in the next slot. Compared on squares, rel2 = ||r||^2/||b||^2 and scal0 = tol^2.
+__device__ __forceinline__ void sampling_b(State* st, double rel2) {
+  const int m = st->samp_m;
+  int lev = st->sb_reached;
+  while (lev < m && rel2 <= pow(st->scal0, (double)(lev + 1) / (double)(m + 1))) ++lev;
+  if (lev > st->sb_reached) {
+    const int slot = st->sb_used++;
+    st->pend_slot = slot;
+    st->slot_iter[slot] = st->iter;
+    st->sb_reached = lev;
+  }
+}
+
 #define ESD_LOOP_SLICES(set)                                             \
   const int lane = lane_id();                                            \
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;           \
@@ -420,7 +435,10 @@ __global__ void __launch_bounds__(kBlock, M == 0 ? 4 : defl_minb<T, M>()) k_upda
       }
       // a run that will be resumed goes on sampling at its stop: the iterate is written by
       // the next run's first update, or the claim is undone if no run follows
-      if ((!stop || st->defer_sample) && do_update && st->samp_m > 0) sampling_a(st);
+      if ((!stop || st->defer_sample) && do_update && st->samp_m > 0) {
+        if (st->samp_method == 1) sampling_b(st, st->bb > 0.0 ? rr / st->bb : 0.0);
+        else sampling_a(st);
+      }
       st->fu = SCM > 0 ? fu_s : 0.0;
       if (PRE == ESD_PRECOND_IC0) st->rho_acc = (double)red[1];
       if (stop) {

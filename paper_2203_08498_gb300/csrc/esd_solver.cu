@@ -438,6 +438,7 @@ void esd_params_default(esd_params* p) {
   p->inner_tol = 0.1;
   p->max_outer = 60;
   p->resume_direction = 1;
+  p->sampling = ESD_SAMPLING_A;
 }
 
 int esd_solver_create(esd_matrix* A, const esd_params* params, esd_solver** out) {
@@ -450,6 +451,9 @@ int esd_solver_create(esd_matrix* A, const esd_params* params, esd_solver** out)
   ESD_CHECK(p.maxit_cap >= 1, ESD_ERR_INVALID, "maxit_cap must be >= 1");
   ESD_CHECK(p.sample_cap >= 0 && p.sample_cap <= kMaxM, ESD_ERR_INVALID, "sample_cap must be 0..64");
   ESD_CHECK(p.precision == ESD_FP64 || p.precision == ESD_FP32_REFINE, ESD_ERR_INVALID, "unknown precision");
+  ESD_CHECK(p.sampling == ESD_SAMPLING_A || p.sampling == ESD_SAMPLING_B, ESD_ERR_INVALID, "unknown sampling method");
+  ESD_CHECK(p.sampling == ESD_SAMPLING_A || p.precision == ESD_FP64, ESD_ERR_INVALID,
+            "sampling method B is defined on the FP64 solve's relative residual (use method A with refinement)");
   ESD_CHECK(p.precision == ESD_FP64 || (p.inner_tol > 0.0 && p.inner_tol < 1.0 && p.max_outer >= 1),
             ESD_ERR_INVALID, "refinement needs 0 < inner_tol < 1 and max_outer >= 1");
   ESD_CHECK(p.precond == ESD_PRECOND_NONE || A->factored, ESD_ERR_STATE, "IC(0) preconditioner needs esd_factor_ic0");
@@ -535,7 +539,7 @@ int esd_solve(esd_solver* S, const double* b, double* x, double tol, int32_t max
   ESD_CHECK(sample_m >= 0 && sample_m <= S->prm.sample_cap, ESD_ERR_INVALID, "sample_m must be 0..sample_cap");
   ESD_CHECK(sample_m == 0 || S->mode != ESD_DEFLATION, ESD_ERR_STATE,
             "sampling is defined on plain / subspace-correction iterates, not in deflation mode");
-  ESD_CHECK(sample_m != 1, ESD_ERR_INVALID, "sampling method A needs m >= 2");
+  ESD_CHECK(sample_m != 1 || S->prm.sampling == ESD_SAMPLING_B, ESD_ERR_INVALID, "sampling method A needs m >= 2");
   ESD_CHECK(S->prm.precond == ESD_PRECOND_NONE || S->A->factored, ESD_ERR_STATE,
             "the IC(0) factor is missing or stale (the matrix values changed): call esd_factor_ic0");
   ESD_CHECK(S->mode == ESD_PLAIN || S->w_values_version == S->A->values_version, ESD_ERR_STATE,
@@ -555,6 +559,7 @@ int esd_solve(esd_solver* S, const double* b, double* x, double tol, int32_t max
   h->lmax = S->prm.lmax > 0 ? S->prm.lmax : smallest_lmax(sample_m, maxit);
   h->h = 1;
   h->pend_slot = -1;
+  h->samp_method = S->prm.sampling;
   ESD_CUDA(cudaMemcpyAsync(S->state.get(), h, sizeof(State), cudaMemcpyHostToDevice, s));
   ESD_CUDA(cudaGraphLaunch(S->exec[S->mode], s));
   copy_out(S->vx.get(), x, sizeof(double) * n, s);

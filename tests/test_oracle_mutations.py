@@ -46,6 +46,10 @@ MUTANTS = {
     # subspace correction subtracted instead of added (Eq. mc)
     "sc_sign": ("    tall_vec_acc(n, s->m, s->W, u, 1.0, z);", "    tall_vec_acc(n, s->m, s->W, u, -1.0, z);",
                 pins.test_subspace_correction_shifts_small_eigenvalue_by_one),
+    # method B levels tol^(s/m) instead of tol^(s/(m+1))
+    "sampling_b_levels": ("  while (lev < m && rel2 <= pow(tol2, (double)(lev + 1) / (double)(m + 1))) ++lev;",
+                          "  while (lev < m && rel2 <= pow(tol2, (double)(lev + 1) / (double)m)) ++lev;",
+                          lambda: pins.test_sampling_b_samples_first_crossings("c1")),
     # residual update with the wrong sign
     "residual_sign": ("        r[k] -= alpha * q[k];", "        r[k] += alpha * q[k];",
                       pins.test_iccg_solves_the_system),

@@ -341,3 +341,46 @@ def test_modes_agree_on_solution(c1_sequences):
         x0 = seq[0][0][t]["x"]
         for m in (1, 2):
             assert np.linalg.norm(seq[m][0][t]["x"] - x0) <= 1e-6 * np.linalg.norm(x0)
+
+
+# ---- sampling method B (Section 4.2: the relative residual levels)
+
+def _levels_first_reached(res, tol, m, stop_iter):
+    """Per level s = 1..m, the first iteration i (1 <= i < stop_iter) with
+    ||r_i||/||b|| <= tol^(s/(m+1)) -- read off the residual history, squared as the
+    method compares."""
+    out = []
+    for s in range(1, m + 1):
+        lev2 = (tol * tol) ** (s / (m + 1))
+        hit = [i for i in range(1, stop_iter) if res[i] * res[i] <= lev2]
+        if hit:
+            out.append(hit[0])
+    return sorted(set(out))
+
+
+@pytest.mark.parametrize("name", ["c1", "small3d"])
+def test_sampling_b_samples_first_crossings(name):
+    """Method B stores exactly the iterates at which a new residual level is first reached
+    (an iteration reaching several levels once), none at the stopping iteration."""
+    p = wl.config_c1() if name == "c1" else wl.small_3d(9, seed=11)
+    b = p.source if p.source is not None else wl.random_rhs(p.n, 4)
+    m, tol = 8, 1e-8
+    out = oracle.System(p, oracle.IC0(p)).solve(b, tol=tol, sample_m=m, sample_method=1)
+    si = out["sample_iter"]
+    filled = sorted(int(v) for v in si if v > 0)
+    assert filled == _levels_first_reached(out["res"], tol, m, out["iters"])
+    assert list(si[:len(filled)]) == filled  # slots fill in order
+    assert np.all(si[len(filled):] == 0)
+
+
+def test_sampling_b_columns_are_the_iterates():
+    """Each stored column is the iterate after that many iterations (a rerun with maxit set
+    to the sample's iteration, same arithmetic)."""
+    p = wl.config_c1()
+    sysm = oracle.System(p, oracle.IC0(p))
+    out = sysm.solve(p.source, tol=1e-8, sample_m=6, sample_method=1)
+    for k, it in enumerate(out["sample_iter"]):
+        if it <= 0:
+            continue
+        xk = sysm.solve(p.source, tol=1e-300, maxit=int(it), history=False)["x"]
+        assert np.array_equal(out["samples"][:, k], xk), k
