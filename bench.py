@@ -52,6 +52,8 @@ L2_BYTES = 129e6
 # Per workload: grid, systems per step, sampled columns m, tolerance, mode, precision and
 # whether every forward solve is followed by its adjoint solve.
 CONFIGS = {
+    # 64 x 64 5-point, 4 squares of 1e3, red-black: tiny, L2-resident, latency-bound
+    "c1": dict(grid=64, systems=5, m=8, tol=1e-8, mode="deflation", precision="fp64", adjoint=False),
     # 128^3 7-point, 16 balls of 1e5: the headline sequence
     "c2": dict(grid=128, systems=20, m=16, tol=1e-8, mode="deflation", precision="fp64", adjoint=False),
     # 192^3 27-point anisotropic log-normal FE: the precision form to 1e-10
@@ -105,7 +107,9 @@ def workload(args):
 
 def _make_workload(args):
     import workloads as wl
-    r = args.grid / {"c2": 128.0, "c3": 192.0, "c4": 128.0, "c5": 256.0}[args.config]
+    r = args.grid / {"c1": 64.0, "c2": 128.0, "c3": 192.0, "c4": 128.0, "c5": 256.0}[args.config]
+    if args.config == "c1":
+        return wl.config_c1()
     if args.config == "c2":
         return wl.config_c2() if args.grid == 128 else wl.config_c2(N=args.grid, rmin=4 * r, rmax=8 * r)
     if args.config == "c3":
@@ -117,6 +121,7 @@ def _make_workload(args):
 
 def workload_name(args, p):
     base = {
+        "c1": "fv5_64x64_4squares_1e3_redblack_dt1e-2",
         "c2": f"fv7_{args.grid}cube_16balls_1e5_dt1e-3",
         "c3": f"fe27_{args.grid}cube_aniso1e-3_lognormal_s2_dt1e-3",
         "c4": f"fv7_{args.grid}cube_exp_theta_smooth4_steady",
@@ -192,6 +197,17 @@ class Clocks:
 
 
 # ---------------------------------------------------------------- GPU arm
+
+def max_over_ranks(value, device):
+    """The largest of every rank's value (the job's time is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
 
 def launch_count(info, mode_is, m, fp32, its, outer):
     """Kernels of this library launched by solves with these inner iteration counts and
@@ -294,11 +310,7 @@ def gpu_arm(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-        ms = e0.elapsed_time(e1)
-        if ws > 1:
-            tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            ms = float(tt.item())
+        ms = max_over_ranks(e0.elapsed_time(e1), dev)
         return ms, wall, out
 
     clocks = Clocks(local)
@@ -383,6 +395,30 @@ def gpu_arm(args):
         result["iteration"] = iteration_roofline(S, esd, p, args, x, b, src, peaks)
         # end to end through the C ABI with host buffers
         result["e2e"] = e2e(esd, p, args, torch)
+    elif args.config == "c1":
+        # latency-bound: per-iteration time of each mode through the solve graph against the
+        # sum of its kernels launched one by one
+        lat = {}
+        for name, md in modes_map.items():
+            S.set_mode(md)
+            x0 = torch.zeros_like(x)
+            S.solve(b, x0, args.tol, 20000, 0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            its_sum = 0
+            for _ in range(20):
+                x0.zero_()
+                st, it, rr = S.solve(b, x0, args.tol, 20000, 0)
+                its_sum += it
+            torch.cuda.synchronize()
+            per_it = (time.perf_counter() - t0) / its_sum
+            kern = S.profile_iterations(b, torch.zeros_like(x), reps=20)
+            lat[name] = {"iters": its_sum // 20, "us_per_iteration_graph": per_it * 1e6,
+                         "us_per_iteration_kernels_one_by_one": sum(t for _, t in kern) * 1e3,
+                         "kernels": len(kern)}
+        result["latency"] = lat
+        result["e2e"] = {"value": None, "unit": UNIT, "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                         "note": "end-to-end host-buffer timing is taken on the headline 128^3 sequence only"}
     else:
         # comparator: plain FP64 PCG on the same sequence (one timed pass)
         S64 = S if not fp32 else esd.Solver(A, maxit_cap=20000, sample_cap=max(args.m, 2))
@@ -390,6 +426,12 @@ def gpu_arm(args):
         result["fp64_plain"] = {"ms_per_step": ms64, "iterations": r64[-1][0],
                                 "ms_per_solve": ms64 / solves_per_step,
                                 "speedup_of_this_run": ms64 / ms_step}
+        if fp32:
+            # the precision form without the accelerator: FP32 inner plain PCG, FP64 refinement
+            ms32, _, r32 = timed(esd.PLAIN, 1, 0, S=S)
+            result["fp32_plain"] = {"ms_per_step": ms32, "iterations": r32[-1][0],
+                                    "ms_per_solve": ms32 / solves_per_step,
+                                    "speedup_vs_fp64_plain": ms64 / ms32}
         result["e2e"] = {"value": None, "unit": UNIT, "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
                          "note": "end-to-end host-buffer timing is taken on the headline 128^3 sequence only"}
     return result, modes

@@ -49,6 +49,7 @@ struct SellView {
   const int4* meta;
   const int* col;
   const T* val;
+  const uint2* ent = nullptr;  // FP32 copy: (value bits, column) per entry, one 8-byte load
 };
 
 // Device-resident scalar state of one solve. All Krylov scalars stay here; the host reads

@@ -43,6 +43,7 @@ struct Sell {
   DevBuf col;    // int per entry (padded)
   DevBuf val;    // double per entry
   DevBuf val32;  // float per entry (FP32 inner solves)
+  DevBuf ent32;  // uint2 per entry: (float bits, column), so an FP32 entry is one 8-byte load
   long long entries = 0;
   template <typename T> SellView<T> view() const;
 };
@@ -51,7 +52,7 @@ template <> inline SellView<double> Sell::view<double>() const {
   return {meta.as<int4>(), col.as<int>(), val.as<double>()};
 }
 template <> inline SellView<float> Sell::view<float>() const {
-  return {meta.as<int4>(), col.as<int>(), val32.as<float>()};
+  return {meta.as<int4>(), col.as<int>(), val32.as<float>(), ent32.as<uint2>()};
 }
 
 // Scratch for the grid-wide reductions of one stream of launches.
@@ -112,6 +113,10 @@ namespace esd {
 void copy_in(const void* src, void* dst_dev, size_t bytes, cudaStream_t s);   // device or host src
 void copy_out(const void* src_dev, void* dst, size_t bytes, cudaStream_t s);  // device or host dst
 bool is_device_ptr(const void* p);
+// Extremes of the CG Lanczos matrix from a[k], b[k-1] (out: lmin, lmax, lmax/lmin); scratch
+// holds 2 tables of stride >= k doubles (esd_noalloc.cu).
+void launch_lanczos_extremes(const double* a, const double* b, int k, double* scratch, size_t stride, double* out,
+                             cudaStream_t s);
 // After csr_val changed on the device: refill the sliced-ELL values of A, drop the factor.
 void matrix_values_changed(esd_matrix* A);
 void set_last_error(const std::string& msg);

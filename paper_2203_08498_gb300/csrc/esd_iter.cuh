@@ -42,6 +42,10 @@ enum { kModePlain = ESD_PLAIN, kModeDefl = ESD_DEFLATION, kModeSC = ESD_SUBSPACE
 #ifndef ESD_ROW_UNROLL
 #define ESD_ROW_UNROLL 4
 #endif
+// FP32 kernels read (value, column) as one 8-byte load per entry
+#ifndef ESD_F32_INTERLEAVED
+#define ESD_F32_INTERLEAVED 1
+#endif
 #ifndef ESD_ROW_UNROLL_F32
 #define ESD_ROW_UNROLL_F32 4
 #endif
@@ -63,7 +67,14 @@ __device__ __forceinline__ T row_fma(const SellView<T>& M, const int4& md, int l
   const int* cp = M.col + md.x + lane;
   const T* vp = M.val + md.x + lane;
   T acc = init;
-  if (sizeof(T) == 4) {
+  if (sizeof(T) == 4 && ESD_F32_INTERLEAVED && M.ent) {
+    const uint2* ep = M.ent + md.x + lane;
+    ESD_UNROLL(ESD_ROW_UNROLL_F32)
+    for (int k = 0; k < md.y; ++k) {
+      const uint2 e = __ldcs(ep + k * kSlice);
+      acc = fma((T)__uint_as_float(e.x), v[e.y], acc);
+    }
+  } else if (sizeof(T) == 4) {
     ESD_UNROLL(ESD_ROW_UNROLL_F32)
     for (int k = 0; k < md.y; ++k) acc = fma(ld_stream(vp + k * kSlice), v[ld_stream(cp + k * kSlice)], acc);
   } else {
@@ -82,8 +93,17 @@ __device__ __forceinline__ T row_fma_diff(const SellView<T>& M, const int4& md, 
   const int* cp = M.col + md.x + lane;
   const T* vp = M.val + md.x + lane;
   T acc = fma(si, vi, init);
-  ESD_UNROLL(ESD_ROW_UNROLL_F32)
-  for (int k = 0; k < md.y; ++k) acc = fma(ld_stream(vp + k * kSlice), v[ld_stream(cp + k * kSlice)] - vi, acc);
+  if (ESD_F32_INTERLEAVED && M.ent) {
+    const uint2* ep = M.ent + md.x + lane;
+    ESD_UNROLL(ESD_ROW_UNROLL_F32)
+    for (int k = 0; k < md.y; ++k) {
+      const uint2 e = __ldcs(ep + k * kSlice);
+      acc = fma((T)__uint_as_float(e.x), v[e.y] - vi, acc);
+    }
+  } else {
+    ESD_UNROLL(ESD_ROW_UNROLL_F32)
+    for (int k = 0; k < md.y; ++k) acc = fma(ld_stream(vp + k * kSlice), v[ld_stream(cp + k * kSlice)] - vi, acc);
+  }
   return acc;
 }
 
@@ -341,7 +361,7 @@ __global__ void __launch_bounds__(kBlock, M == 0 ? 4 : defl_minb<T, M>()) k_upda
   constexpr int DM = (MODE == kModeDefl) ? M : 0;
   constexpr int R = 2 + SCM;
   __shared__ T red[red_size<R>()];
-  __shared__ double ys[DM > 0 ? DM : 1];
+  __shared__ T ys[DM > 0 ? DM : 1];  // y in the kernel's type: converted once per block
   __shared__ double fu_s;
   pdl_enter();
   State* st = c.st;
@@ -350,7 +370,7 @@ __global__ void __launch_bounds__(kBlock, M == 0 ? 4 : defl_minb<T, M>()) k_upda
   const double alpha_d = st->alpha;
   const int pend = do_update ? st->pend_slot : -1;
   if (DM > 0) {
-    for (int k = threadIdx.x; k < DM; k += blockDim.x) ys[k] = st->y[k];
+    for (int k = threadIdx.x; k < DM; k += blockDim.x) ys[k] = (T)st->y[k];
     __syncthreads();
   }
   T acc[R];
@@ -380,7 +400,7 @@ __global__ void __launch_bounds__(kBlock, M == 0 ? 4 : defl_minb<T, M>()) k_upda
         }
         T t = c.q[i];
 #pragma unroll
-        for (int k = 0; k < DM; ++k) t = fma(-c.AW[wix<DM>(c, k, i, s, lane)], (T)ys[k], t);
+        for (int k = 0; k < DM; ++k) t = fma(-c.AW[wix<DM>(c, k, i, s, lane)], ys[k], t);
         ri = fma(-alpha, t, c.r[i]);
         c.r[i] = ri;
         acc[0] = fma(ri, ri, acc[0]);
@@ -500,14 +520,14 @@ __global__ void __launch_bounds__(kBlock, sweep_minb<T>()) k_fwd(IterCtx<T> c, S
 // only take the direction update.
 template <typename T, int SCM>
 __global__ void __launch_bounds__(kBlock, SCM == 0 ? sweep_minb<T>() : 1) k_bwd(IterCtx<T> c, SliceSet set, SliceSet elem) {
-  __shared__ double us[SCM > 0 ? SCM : 1];
+  __shared__ T us[SCM > 0 ? SCM : 1];  // u in the kernel's type: converted once per block
   pdl_enter();
   State* st = c.st;
   if (st->conv) return;
   const T beta = (T)st->beta;
   const bool first = st->iter == 0 || st->fresh_dir;
   if (SCM > 0) {
-    for (int k = threadIdx.x; k < SCM; k += blockDim.x) us[k] = st->u[k];
+    for (int k = threadIdx.x; k < SCM; k += blockDim.x) us[k] = (T)st->u[k];
     __syncthreads();
   }
   const int nsweep = set.total();
@@ -531,7 +551,7 @@ __global__ void __launch_bounds__(kBlock, SCM == 0 ? sweep_minb<T>() : 1) k_bwd(
       if (sweep) c.Y[i] = zic;
       T z = zic;
 #pragma unroll
-      for (int k = 0; k < SCM; ++k) z = fma(c.W[wix<SCM>(c, k, i, s, lane)], (T)us[k], z);
+      for (int k = 0; k < SCM; ++k) z = fma(c.W[wix<SCM>(c, k, i, s, lane)], us[k], z);
       c.p[i] = first ? z : fma(beta, pold, z);
     }
   }
@@ -540,14 +560,14 @@ __global__ void __launch_bounds__(kBlock, SCM == 0 ? sweep_minb<T>() : 1) k_bwd(
 // No preconditioner: p = r [+ W u] + beta p.
 template <typename T, int SCM>
 __global__ void __launch_bounds__(kBlock, SCM == 0 ? 4 : 1) k_dir(IterCtx<T> c, SliceSet set) {
-  __shared__ double us[SCM > 0 ? SCM : 1];
+  __shared__ T us[SCM > 0 ? SCM : 1];  // u in the kernel's type: converted once per block
   pdl_enter();
   State* st = c.st;
   if (st->conv) return;
   const T beta = (T)st->beta;
   const bool first = st->iter == 0 || st->fresh_dir;
   if (SCM > 0) {
-    for (int k = threadIdx.x; k < SCM; k += blockDim.x) us[k] = st->u[k];
+    for (int k = threadIdx.x; k < SCM; k += blockDim.x) us[k] = (T)st->u[k];
     __syncthreads();
   }
   ESD_LOOP_SLICES(set) {
@@ -558,7 +578,7 @@ __global__ void __launch_bounds__(kBlock, SCM == 0 ? 4 : 1) k_dir(IterCtx<T> c, 
       const int i = md.z + lane;
       T z = c.r[i];
 #pragma unroll
-      for (int k = 0; k < SCM; ++k) z = fma(c.W[wix<SCM>(c, k, i, s, lane)], (T)us[k], z);
+      for (int k = 0; k < SCM; ++k) z = fma(c.W[wix<SCM>(c, k, i, s, lane)], us[k], z);
       c.p[i] = first ? z : fma(beta, c.p[i], z);
     }
   }
@@ -648,10 +668,10 @@ template <typename T, int M>
 __global__ void __launch_bounds__(kBlock) k_tall_axpy(IterCtx<T> c, SliceSet set, const T* Z, T* v,
                                                       T sign, int norm) {
   __shared__ T red[red_size<1>()];
-  __shared__ double us[M];
+  __shared__ T us[M];  // u in the kernel's type: converted once per block
   pdl_enter();
   State* st = c.st;
-  for (int k = threadIdx.x; k < M; k += blockDim.x) us[k] = st->u[k];
+  for (int k = threadIdx.x; k < M; k += blockDim.x) us[k] = (T)st->u[k];
   __syncthreads();
   T acc[1] = {T(0)};
   ESD_LOOP_SLICES(set) {
@@ -662,7 +682,7 @@ __global__ void __launch_bounds__(kBlock) k_tall_axpy(IterCtx<T> c, SliceSet set
       const int i = md.z + lane;
       T t = T(0);
 #pragma unroll
-      for (int k = 0; k < M; ++k) t = fma(Z[wix<M>(c, k, i, s, lane)], (T)us[k], t);
+      for (int k = 0; k < M; ++k) t = fma(Z[wix<M>(c, k, i, s, lane)], us[k], t);
       const T vi = fma(sign, t, v[i]);
       v[i] = vi;
       acc[0] = fma(vi, vi, acc[0]);
@@ -678,10 +698,10 @@ __global__ void __launch_bounds__(kBlock) k_tall_axpy(IterCtx<T> c, SliceSet set
 // x64 += Z u (u = st->u): the correction summed in T, added to the FP64 iterate.
 template <typename T, int M>
 __global__ void __launch_bounds__(kBlock) k_tall_axpy64(IterCtx<T> c, SliceSet set, const T* Z) {
-  __shared__ double us[M];
+  __shared__ T us[M];  // u in the kernel's type: converted once per block
   pdl_enter();
   State* st = c.st;
-  for (int k = threadIdx.x; k < M; k += blockDim.x) us[k] = st->u[k];
+  for (int k = threadIdx.x; k < M; k += blockDim.x) us[k] = (T)st->u[k];
   __syncthreads();
   ESD_LOOP_SLICES(set) {
     int r;
@@ -691,7 +711,7 @@ __global__ void __launch_bounds__(kBlock) k_tall_axpy64(IterCtx<T> c, SliceSet s
       const int i = md.z + lane;
       T t = T(0);
 #pragma unroll
-      for (int k = 0; k < M; ++k) t = fma(Z[wix<M>(c, k, i, s, lane)], (T)us[k], t);
+      for (int k = 0; k < M; ++k) t = fma(Z[wix<M>(c, k, i, s, lane)], us[k], t);
       c.x64[i] += (double)t;
     }
   }

@@ -311,6 +311,19 @@ __global__ void k_rowsum(SellView<double> A, int nslices, double* s64, float* s3
   }
 }
 
+// FP32 entry (value, column) pairs of a sliced-ELL array
+__global__ void k_interleave(long long cnt, const int* col, const double* val, uint2* ent) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < cnt; e += (long long)gridDim.x * blockDim.x)
+    ent[e] = make_uint2(__float_as_uint((float)val[e]), (unsigned)col[e]);
+}
+
+static void interleave(Sell& M, cudaStream_t s) {
+  if (M.ent32.bytes() < (size_t)M.entries * sizeof(uint2)) M.ent32.alloc((size_t)std::max(M.entries, 1LL) * sizeof(uint2));
+  if (M.entries == 0) return;
+  k_interleave<<<max_grid_blocks(), kBlock, 0, s>>>(M.entries, M.col.as<int>(), M.val.as<double>(), M.ent32.as<uint2>());
+  ESD_CUDA(cudaGetLastError());
+}
+
 static void to_float(const DevBuf& src, DevBuf& dst, long long cnt, cudaStream_t s) {
   if (dst.bytes() < (size_t)cnt * sizeof(float)) dst.alloc((size_t)cnt * sizeof(float));
   if (cnt == 0) return;
@@ -335,6 +348,7 @@ void esd::matrix_values_changed(esd_matrix* A) {
 void esd_matrix::ensure_fp32() {
   if (a32_version != values_version || !A.val32.get()) {
     to_float(A.val, A.val32, A.entries, stream);
+    interleave(A, stream);
     if (!rowsum32.get()) {
       rowsum32.alloc(sizeof(float) * vec_stride());
       rowsum64.alloc(sizeof(double) * vec_stride());
@@ -350,6 +364,8 @@ void esd_matrix::ensure_fp32() {
   if (factored) {
     to_float(L.val, L.val32, L.entries, stream);
     to_float(U.val, U.val32, U.entries, stream);
+    interleave(L, stream);
+    interleave(U, stream);
     to_float(inv_d, inv_d32, (long long)vec_stride(), stream);
   }
   fp32_version = factor_version;

@@ -30,13 +30,16 @@ __device__ static int sturm_count_tab(const double* d, const double* e2, int k, 
   return cnt;
 }
 
-// Same multisection as the solver's estimate, reading T from the scratch table.
-__global__ void k_lanczos_extremes_tab(const double* a, const double* b, int k, double* scratch,
+// Extreme eigenvalues of the CG Lanczos matrix T (diag 1/a_j + b_{j-1}/a_{j-1}, off-diagonal
+// sqrt(b_j)/a_j) by multisection on Sturm counts: T's diagonal and squared off-diagonal are
+// tabulated first (d = scratch[0..k), e2 = scratch[stride..stride+k)), then every round the
+// 256 threads count the eigenvalues below 256 points of the current bracket.
+__global__ void k_lanczos_extremes_tab(const double* a, const double* b, int k, double* scratch, size_t stride,
                                        double* out) {
   __shared__ double lo_s, hi_s;
   __shared__ int cnt_s[256];
   double* d = scratch;
-  double* e2 = scratch + kNoAllocMaxK;
+  double* e2 = scratch + stride;
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
     double dj = 1.0 / a[j];
     double ej2 = 0.0;
@@ -96,6 +99,12 @@ __global__ void k_lanczos_extremes_tab(const double* a, const double* b, int k, 
   }
 }
 
+void launch_lanczos_extremes(const double* a, const double* b, int k, double* scratch, size_t stride, double* out,
+                             cudaStream_t s) {
+  k_lanczos_extremes_tab<<<1, 256, 0, s>>>(a, b, k, scratch, stride, out);
+  ESD_CUDA(cudaGetLastError());
+}
+
 }  // namespace esd
 
 using namespace esd;
@@ -119,8 +128,7 @@ extern "C" int esd_lanczos_extremes_noalloc(const double* alpha, const double* b
       }
       scratch = g_scratch_ptr[dev];
     }
-    k_lanczos_extremes_tab<<<1, 256, 0, (cudaStream_t)stream>>>(alpha, beta, k, scratch, out);
-    ESD_CUDA(cudaGetLastError());
+    launch_lanczos_extremes(alpha, beta, k, scratch, kNoAllocMaxK, out, (cudaStream_t)stream);
     return ESD_OK;
   } catch (const Error& e) {
     set_last_error(e.what());

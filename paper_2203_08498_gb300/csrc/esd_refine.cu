@@ -166,10 +166,6 @@ __global__ void k_d2f(long long cnt, const double* a, float* b) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cnt; i += (long long)gridDim.x * blockDim.x)
     b[i] = (float)a[i];
 }
-__global__ void k_f2d(long long cnt, const float* a, double* b) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cnt; i += (long long)gridDim.x * blockDim.x)
-    b[i] = (double)a[i];
-}
 
 // FP32 slice-major copy of a column-major n x M block: row i sits at lane (rowpos & 31) of
 // slice (rowpos >> 5); the M columns of one slice are stored one after another.
@@ -201,11 +197,6 @@ void round_to_f32(long long cnt, const double* a, double* b, cudaStream_t s) {
 void convert_d2f(long long cnt, const double* a, float* b, cudaStream_t s) {
   if (cnt <= 0) return;
   k_d2f<<<max_grid_blocks(), kBlock, 0, s>>>(cnt, a, b);
-  ESD_CUDA(cudaGetLastError());
-}
-void convert_f2d(long long cnt, const float* a, double* b, cudaStream_t s) {
-  if (cnt <= 0) return;
-  k_f2d<<<max_grid_blocks(), kBlock, 0, s>>>(cnt, a, b);
   ESD_CUDA(cudaGetLastError());
 }
 

@@ -13,5 +13,4 @@ void convert_d2f(long long cnt, const double* a, float* b, cudaStream_t s);
 void to_slice_major(int n, const int* rowpos, const double* X, size_t ld, int M, float* out, cudaStream_t s);
 // b = a rounded to the nearest FP32 value (kept in FP64)
 void round_to_f32(long long cnt, const double* a, double* b, cudaStream_t s);
-void convert_f2d(long long cnt, const float* a, double* b, cudaStream_t s);
 }  // namespace esd

@@ -15,79 +15,6 @@ namespace esd {
 
 // ------------------------------------------------------------------ small kernels
 
-// Extreme eigenvalues of the CG Lanczos matrix T (diag 1/a_j + b_{j-1}/a_{j-1}, off-diagonal
-// sqrt(b_j)/a_j) by multisection on Sturm counts: every round the 256 threads count the
-// eigenvalues below 256 points of the current bracket.
-__device__ int sturm_count(const double* a, const double* b, int k, double x) {
-  int cnt = 0;
-  double q = 1.0;
-  const double pivmin = 1e-300;
-  for (int j = 0; j < k; ++j) {
-    double d = 1.0 / a[j];
-    double e2 = 0.0;
-    if (j > 0) {
-      d += b[j - 1] / a[j - 1];
-      const double e = sqrt(b[j - 1]) / a[j - 1];
-      e2 = e * e;
-    }
-    q = (j == 0) ? d - x : d - x - e2 / q;
-    if (fabs(q) < pivmin) q = -pivmin;
-    if (q < 0.0) ++cnt;
-  }
-  return cnt;
-}
-
-__global__ void k_lanczos_extremes(const double* a, const double* b, int k, double* out) {
-  __shared__ double lo_s, hi_s;
-  __shared__ int cnt_s[256];
-  // Gershgorin bracket
-  if (threadIdx.x == 0) {
-    double lo = 1e300, hi = -1e300;
-    for (int j = 0; j < k; ++j) {
-      double d = 1.0 / a[j];
-      if (j > 0) d += b[j - 1] / a[j - 1];
-      double r = 0.0;
-      if (j > 0) r += fabs(sqrt(b[j - 1]) / a[j - 1]);
-      if (j + 1 < k) r += fabs(sqrt(b[j]) / a[j]);
-      lo = fmin(lo, d - r);
-      hi = fmax(hi, d + r);
-    }
-    const double pad = 1e-12 * fmax(fabs(lo), fabs(hi)) + 1e-300;
-    lo_s = lo - pad;
-    hi_s = hi + pad;
-  }
-  __syncthreads();
-  const double glo = lo_s, ghi = hi_s;
-  for (int which = 0; which < 2; ++which) {
-    // which 0: smallest eigenvalue (count goes 0 -> >=1); 1: largest (count k-1 -> k)
-    double lo = glo, hi = ghi;
-    const int target = which == 0 ? 1 : k;
-    for (int round = 0; round < 12; ++round) {
-      const double x = lo + (hi - lo) * (threadIdx.x + 1) / 257.0;
-      cnt_s[threadIdx.x] = sturm_count(a, b, k, x);
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        // first point whose count reaches the target
-        int t = 256;
-        for (int i = 0; i < 256; ++i)
-          if (cnt_s[i] >= target) { t = i; break; }
-        const double w = (hi - lo) / 257.0;
-        const double nlo = lo + w * t;
-        const double nhi = (t < 256) ? lo + w * (t + 1) : hi;
-        lo_s = nlo;
-        hi_s = nhi;
-      }
-      __syncthreads();
-      lo = lo_s;
-      hi = hi_s;
-      __syncthreads();
-      if (hi - lo <= 1e-15 * fmax(fabs(lo), fabs(hi))) break;
-    }
-    if (threadIdx.x == 0) out[which] = 0.5 * (lo + hi);
-    __syncthreads();
-  }
-}
-
 __global__ void k_pattern_grad(int n, const int* rp, const int* ci, const double* lam, const double* x,
                                double* grad) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -134,7 +61,7 @@ struct esd_solver {
   int mode = ESD_PLAIN;
   size_t ld = 0;
   DevBuf vb, vx, vr, vp, vq, vY, samples;
-  DevBuf W, AW, E, Einv, ritz, ahist, bhist, state, partials, rho_part, ext;
+  DevBuf W, AW, E, Einv, ritz, ahist, bhist, state, partials, rho_part, ext, lz;
   State* hst = nullptr;  // pinned host copy
   // FP32-inner / FP64-refinement form
   bool fp32 = false;
@@ -710,9 +637,9 @@ int esd_estimate_cond(esd_solver* S, double* lmin, double* lmax, double* kappa, 
   ESD_API_BEGIN
   ESD_CHECK(S, ESD_ERR_INVALID, "NULL solver");
   ESD_CHECK(S->last_iters >= 1, ESD_ERR_STATE, "the last solve took no CG step");
-  k_lanczos_extremes<<<1, 256, 0, S->stream>>>(S->ahist.as<double>(), S->bhist.as<double>(), S->last_iters,
-                                               S->ext.as<double>());
-  ESD_CUDA(cudaGetLastError());
+  if (S->lz.bytes() < sizeof(double) * 2 * (size_t)S->prm.maxit_cap) S->lz.alloc(sizeof(double) * 2 * S->prm.maxit_cap);
+  launch_lanczos_extremes(S->ahist.as<double>(), S->bhist.as<double>(), S->last_iters, S->lz.as<double>(),
+                          (size_t)S->prm.maxit_cap, S->ext.as<double>(), S->stream);
   double h[2];
   ESD_CUDA(cudaMemcpyAsync(h, S->ext.get(), sizeof(h), cudaMemcpyDeviceToHost, S->stream));
   double r0 = std::numeric_limits<double>::quiet_NaN();
