@@ -380,6 +380,19 @@ def gpu_arm(args):
                            "solves_per_s": args.systems / (ms_m / 1e3),
                            "mean_iters_2_to_T": float(np.mean(its_m[1:]))}
         result["modes"] = modes
+        # the W build alone (errors of the sampled solve, CholeskyQR2, AW, E, E^-1, Ritz values):
+        # solves/s with and without it
+        S.set_mode(esd.PLAIN)
+        xw = torch.zeros_like(x)
+        S.solve(b, xw, args.tol, 20000, args.m)
+        torch.cuda.synchronize()
+        tw = time.perf_counter()
+        S.sample_and_build_W()
+        torch.cuda.synchronize()
+        w_ms = (time.perf_counter() - tw) * 1e3
+        S.set_mode(mode)
+        result["w_build"] = {"ms": w_ms, "solves_per_s_without_w_build":
+                             args.systems / ((ms_step - w_ms) / 1e3)}
         # the precision form on the same sequence: FP32 inner PCG (resumed, inner_tol 0.1) inside
         # FP64 refinement to the same tolerance, against plain FP64 PCG
         S32 = esd.Solver(A, maxit_cap=20000, sample_cap=max(args.m, 2), precision=esd.FP32_REFINE)

@@ -196,3 +196,36 @@ def test_autograd_matches_finite_differences(c4_small):
         tm[c] -= step
         fd = (loss(tp) - loss(tm)) / (2 * step)
         assert abs(fd - g[c]) <= 1e-5 * np.abs(g).max(), (c, fd, g[c])
+
+
+@pytest.mark.slow
+def test_full_size_gradient_matches_oracle():
+    """The 128^3 log-normal workload at full size: the adjoint gradients through the autograd
+    API (deflation, m = 16, both solves at tol 1e-12) against the oracle's ICCG adjoint
+    gradient at tol 1e-12 (1e-7: the two FP64 runs each stop at 1e-12), and central finite
+    differences (step 1e-5) on 4 seeded cells to 1e-4."""
+    p, theta, xt = wl.config_c4(N=128)
+    model = FVDiffusion(p, mode=esd.DEFLATION, sample_cap=16)
+    th0 = dev(nat(theta))
+    b = dev(p.source)
+    model.build_W(th0, b, m=16, tol=1e-10)
+    th = th0.clone().requires_grad_(True)
+    x = fv_solve(th, b, model, tol=1e-12)
+    ((x - dev(xt)) ** 2).sum().backward()
+    g = th.grad.cpu().numpy()
+    ref = oracle.adjoint_gradient(p, theta, p.source, xt, tol=1e-12)
+    rt = nat(ref["grad_theta"])
+    assert np.abs(g - rt).max() <= 1e-7 * np.abs(rt).max()
+
+    def loss(t):
+        with torch.no_grad():
+            xx = fv_solve(t, b, model, tol=1e-12)
+            return float(((xx - dev(xt)) ** 2).sum())
+
+    step = 1e-5
+    for c in np.random.default_rng(9).choice(p.n, size=4, replace=False):
+        tp, tm = th0.clone(), th0.clone()
+        tp[c] += step
+        tm[c] -= step
+        fd = (loss(tp) - loss(tm)) / (2 * step)
+        assert abs(fd - g[c]) <= 1e-4 * np.abs(g).max(), (c, fd, g[c])
