@@ -78,6 +78,8 @@ def load(path: str):
     L.orc_solve.restype = i32
     L.orc_solve.argtypes = [C.POINTER(_System), vp, vp, C.POINTER(_SolveIO)]
     L.orc_sampling_a_schedule.argtypes = [i32, i32, i32, vp]
+    L.orc_power_method.restype = f64
+    L.orc_power_method.argtypes = [i32, vp, vp, vp, vp, i32, vp]
     return L
 
 
@@ -324,6 +326,34 @@ def estimate_cond(alpha, beta):
         return np.nan, np.nan, np.nan
     ev = sla.eigvalsh_tridiagonal(d, e) if len(d) > 1 else d
     return float(ev.min()), float(ev.max()), float(ev.max() / ev.min())
+
+
+def power_method(prob, v0, k: int):
+    """Power method of Algorithm PCG-con (Section 5.4) on A: ``v_0 = v0/||v0||``, then
+    ``v_i = A v_{i-1} / ||A v_{i-1}||`` for i = 1..k, and ``lambda_max = (v_k, A v_k)``.
+    In the algorithm each CG iteration takes one step (its SpMV multiplies ``(p_i, v_{i-1})``
+    together); the vectors do not depend on the CG iterates, so k steps here equal a
+    k-iteration solve. Returns (lambda_max, v_k); NaN when a norm vanishes."""
+    v = np.array(v0, dtype=np.float64, copy=True)
+    w = np.empty(prob.n)
+    rp, ci, va = _c(prob.rowptr, np.int32), _c(prob.colind, np.int32), _c(prob.val, np.float64)
+    lam = lib().orc_power_method(prob.n, _p(rp), _p(ci), _p(va), _p(v), int(k), _p(w))
+    return float(lam), v
+
+
+def pcg_cond_estimate(prob, b, v0, m: int, tol: float = 1e-8, maxit: int = 20000, precond: bool = True):
+    """Algorithm PCG-con (Section 5.4): PCG on ``A x = b`` (IC(0), or none with
+    ``precond=False``) with m iterates sampled (method A), the power method for
+    ``lambda_max`` (one step per iteration), the sampled errors made orthonormal (Eq. ek,
+    ekd) and the smallest Ritz value of ``E^T A E`` (Eq. Rayleigh-Ritz) for ``lambda_min``;
+    ``kappa = lambda_max / lambda_min``."""
+    sysm = System(prob, IC0(prob) if precond else None)
+    out = sysm.solve(b, tol=tol, maxit=maxit, sample_m=m, history=False)
+    lam_max, v = power_method(prob, v0, out["iters"])
+    aux, info = build_w(prob, out["x"], out["samples"], out["sample_iter"])
+    lam_min = float(info["ritz"][0])
+    return dict(x=out["x"], iters=out["iters"], lmax=lam_max, lmin=lam_min, kappa=lam_max / lam_min, v=v,
+                ritz=info["ritz"])
 
 
 # ------------------------------------------------------------------ sequence driver

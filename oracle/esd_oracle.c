@@ -13,7 +13,10 @@
  *     (Eq. deflation:projector), P^T A p formed explicitly as a vector and the final
  *     correction x = P x_i + W E^{-1} W^T b (Eq. x1);
  *   - sampling method A (Appendix A) or B (Section 4.2, the relative residual levels),
- *     samples taken only while the solve has not stopped.
+ *     samples taken only while the solve has not stopped;
+ *   - the power method of the same algorithm (Section 5.4), run on its own: its vectors
+ *     do not depend on the CG iterates, so k steps equal the k products of a k-iteration
+ *     solve.
  * Dot products use pairwise summation. E = W^T A W is applied through its dense
  * Cholesky factor. The paper's beta carries a spurious minus sign in Algorithm DPCG; the
  * oracle uses beta = +rho_{i+1}/rho_i, which is the standard CG recurrence.
@@ -49,6 +52,26 @@ void orc_spmv(int n, const int* rp, const int* ci, const double* va, const doubl
     for (int k = rp[i]; k < rp[i + 1]; ++k) s += va[k] * x[ci[k]];
     y[i] = s;
   }
+}
+
+/* Power method of Algorithm "PCG with condition number estimation" (Section 5.4): v is
+ * scaled to unit length, then k times v <- A v, v <- v / ||v||_2 (one step per CG
+ * iteration, the product the algorithm forms beside q = A p). Returns the estimate
+ * lambda_max = (v, A v) of the final unit vector; v holds that vector. work: n doubles.
+ * Returns NaN when a norm is zero or not finite. */
+double orc_power_method(int n, const int* rp, const int* ci, const double* va, double* v, int k,
+                        double* work) {
+  double nv = sqrt(orc_dot(n, v, v));
+  if (!(nv > 0.0) || !isfinite(nv)) return NAN;
+  for (int i = 0; i < n; ++i) v[i] /= nv;
+  for (int step = 0; step < k; ++step) {
+    orc_spmv(n, rp, ci, va, v, work);
+    nv = sqrt(orc_dot(n, work, work));
+    if (!(nv > 0.0) || !isfinite(nv)) return NAN;
+    for (int i = 0; i < n; ++i) v[i] = work[i] / nv;
+  }
+  orc_spmv(n, rp, ci, va, v, work);
+  return orc_dot(n, v, work);
 }
 
 /* ---------------------------------------------------------------- IC(0) */

@@ -50,6 +50,17 @@ MUTANTS = {
     "sampling_b_levels": ("  while (lev < m && rel2 <= pow(tol2, (double)(lev + 1) / (double)(m + 1))) ++lev;",
                           "  while (lev < m && rel2 <= pow(tol2, (double)(lev + 1) / (double)m)) ++lev;",
                           lambda: pins.test_sampling_b_samples_first_crossings("c1")),
+    # power method: the product kept without normalising it
+    "power_no_normalise": ("    for (int i = 0; i < n; ++i) v[i] = work[i] / nv;", "    for (int i = 0; i < n; ++i) v[i] = work[i];",
+                           lambda: pins.test_power_method_diagonal_closed_form(2)),
+    # power method: one step fewer than asked (the estimate of v_{k-1})
+    "power_step_count": ("  for (int step = 0; step < k; ++step) {\n    orc_spmv(n, rp, ci, va, v, work);",
+                         "  for (int step = 1; step < k; ++step) {\n    orc_spmv(n, rp, ci, va, v, work);",
+                         lambda: pins.test_power_method_diagonal_closed_form(5)),
+    # power method: the estimate taken as ||A v|| instead of (v, A v)
+    "power_norm_not_rq": ("  orc_spmv(n, rp, ci, va, v, work);\n  return orc_dot(n, v, work);",
+                          "  orc_spmv(n, rp, ci, va, v, work);\n  return sqrt(orc_dot(n, work, work));",
+                          lambda: pins.test_power_method_diagonal_closed_form(1)),
     # residual update with the wrong sign
     "residual_sign": ("        r[k] -= alpha * q[k];", "        r[k] += alpha * q[k];",
                       pins.test_iccg_solves_the_system),

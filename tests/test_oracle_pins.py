@@ -259,6 +259,62 @@ def test_lanczos_preconditioned_bounds():
 
 # ---------------------------------------------------------------- auxiliary matrix
 
+# ---------------------------------------------------------------- power method (Section 5.4)
+
+@pytest.mark.parametrize("k", [0, 1, 2, 5, 30])
+def test_power_method_diagonal_closed_form(k):
+    """On D = diag(d) the k-th power vector is D^k v0 / ||D^k v0|| and lambda_max is
+    sum d^(2k+1) v0^2 / sum d^(2k) v0^2 (written out here, not by the oracle's steps)."""
+    d = np.linspace(0.5, 3.0, 40)
+    p = wl.csr_of_dense(np.diag(d))
+    v0 = np.random.default_rng(11).standard_normal(40)
+    lam, v = oracle.power_method(p, v0, k)
+    w = v0 * d ** k
+    assert lam == pytest.approx(np.sum(d ** (2 * k + 1) * v0 ** 2) / np.sum(d ** (2 * k) * v0 ** 2), rel=1e-13)
+    np.testing.assert_allclose(v, w / np.linalg.norm(w), rtol=1e-12, atol=1e-15)
+
+
+def test_power_method_2d_laplacian_top_eigenvalue_and_monotone():
+    """5-point Laplacian on 8 x 8: the estimate reaches 4 + 4 cos(pi/9) (the simple top
+    eigenvalue; the next ratio is 0.955, so 400 steps leave ~1e-16), and the Rayleigh
+    quotients of the power vectors of an SPD matrix never decrease (the moment sequence
+    (v0, A^j v0) is log-convex) and never pass the top eigenvalue."""
+    p = wl.laplacian_2d(8)
+    v0 = np.random.default_rng(12).standard_normal(p.n)
+    top = 4 + 4 * np.cos(np.pi / 9)
+    lam, v = oracle.power_method(p, v0, 400)
+    assert lam == pytest.approx(top, rel=1e-12)
+    c = np.cos(np.arange(1, 9) * np.pi / 9)
+    lam_sorted = np.sort((4 - 2 * c[:, None] - 2 * c[None, :]).ravel())
+    assert lam_sorted[-2] < top * 0.96
+    seq = [oracle.power_method(p, v0, k)[0] for k in range(40)]
+    assert all(b >= a * (1 - 1e-15) for a, b in zip(seq, seq[1:]))
+    assert max(seq) <= top * (1 + 1e-15)
+
+
+@pytest.mark.parametrize("precond", [False, True])
+def test_pcg_cond_estimate_brackets_and_approximates_kappa(precond):
+    """Algorithm PCG-con: lambda_max from the power method lies at or below the top
+    eigenvalue, the smallest Ritz value of the sampled errors at or above the bottom one, so
+    the estimate never exceeds kappa(A). The power method takes one step per CG iteration.
+    Without a preconditioner the sampled errors are rich in the bottom eigenvectors of A
+    itself: after 101 steps lambda_max is exact to 1e-6 and lambda_min within 10 % on this
+    small problem (the paper's Table of condition estimates shows the same order of
+    agreement); with IC(0) the errors are rich in the bottom eigenvectors of M^-1 A instead
+    and only the bracket holds."""
+    p = wl.small_3d(6, seed=4, dt=np.inf)
+    ev = np.linalg.eigvalsh(p.scipy().toarray())
+    v0 = np.random.default_rng(13).standard_normal(p.n)
+    est = oracle.pcg_cond_estimate(p, p.source, v0, m=12, tol=1e-10, maxit=2000, precond=precond)
+    assert est["lmax"] <= ev[-1] * (1 + 1e-12) and est["lmin"] >= ev[0] * (1 - 1e-10)
+    assert est["kappa"] <= ev[-1] / ev[0] * (1 + 1e-10)
+    if not precond:
+        assert est["lmax"] == pytest.approx(ev[-1], rel=1e-6)
+        assert est["lmin"] == pytest.approx(ev[0], rel=0.1)
+    lam_k, _ = oracle.power_method(p, v0, est["iters"])
+    assert lam_k == est["lmax"]
+
+
 def test_build_w_basis_and_ritz_values():
     """Q is orthonormal, spans the error vectors (Eq. ek/ekd), E is W^T A W, and the Ritz
     values of unpreconditioned sampling lie inside the spectrum with the smallest one close
