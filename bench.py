@@ -408,6 +408,10 @@ def gpu_arm(args):
         result["iteration"] = iteration_roofline(S, esd, p, args, x, b, src, peaks)
         # end to end through the C ABI with host buffers
         result["e2e"] = e2e(esd, p, args, torch)
+        # the condition estimate of Algorithm PCG-con and the cost of its fused power product
+        result["power_method"] = power_method_report(esd, A, p, args, b, torch, peaks)
+        # sampling method A against method B (Table sampling B): W from each, deflated solves
+        result["sampling_a_vs_b"] = sampling_comparison(esd, A, p, args, b, torch)
     elif args.config == "c1":
         # latency-bound: per-iteration time of each mode through the solve graph against the
         # sum of its kernels launched one by one
@@ -527,7 +531,7 @@ FP32_NOMINAL_TFLOPS = 80.5  # 152 SMs x 128 FP32 FMA/clk x 2 x 2.07 GHz
 
 
 def kernel_model(name, p, args, mode, esd, lv):
-    """Algorithmic bytes and FMAs of one launch (per-kernel model); value
+    """Algorithmic bytes and FMAs of one launch, each array element counted once; value
     size s = 8 (FP64) or 4 (FP32 inner kernels, whose SpMV also reads s = A 1)."""
     n, nnz = p.n, p.nnz
     s = 4 if args.precision == "fp32" else 8
@@ -587,9 +591,75 @@ def read_traffic(kernel):
     return None
 
 
+def power_method_report(esd, A, p, args, b, torch, peaks):
+    """Algorithm PCG-con (Section 5.4) on one system of the sequence: ICCG with m sampled
+    iterates and the power method multiplied in the same SpMV pass, then lambda_max, the
+    smallest Ritz value of the sampled errors and kappa. Its cost: graph time per iteration
+    of the same sampled solve with and without the power product, and the fused SpMV's live
+    kernel time against its byte and FMA model (16 more bytes and nnz more FMAs per row)."""
+    import workloads as wl
+    S = esd.Solver(A, maxit_cap=20000, sample_cap=max(args.m, 2))
+    v0 = torch.from_numpy(np.random.default_rng(wl.SEED_BASE + 7).standard_normal(p.n)).to(b.device)
+
+    def timed_solve():
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, it, rr = S.solve(b, x, args.tol, 20000, args.m)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, it
+
+    timed_solve()  # graph capture
+    t_off, it_off = timed_solve()
+    k_off = dict(S.profile_iterations(b, torch.zeros_like(b), reps=20))
+    S.power_start(v0)
+    timed_solve()  # graph capture with the power product
+    S.power_start(v0)
+    t_on, it_on = timed_solve()
+    lmax, steps = S.power_estimate()
+    S.sample_and_build_W()
+    lmin = float(S.ritz_values()[0])
+    k_on = dict(S.profile_iterations(b, torch.zeros_like(b), reps=20))
+    S.power_start(None)
+    n, nnz = p.n, p.nnz
+    t_k = k_on["spmv_pq"] / 1e3
+    by = 12 * nnz + 20 * n + 16 * n
+    fmas = 2 * nnz + 2 * n
+    return {"lambda_max": lmax, "power_steps": steps, "ritz_min": lmin, "kappa": lmax / lmin,
+            "iterations": it_on, "us_per_iteration_without": t_off / it_off * 1e6,
+            "us_per_iteration_with": t_on / it_on * 1e6, "cost_frac": (t_on / it_on) / (t_off / it_off) - 1.0,
+            "spmv_pq_us_without": k_off["spmv_pq"] * 1e3, "spmv_pq_us_with": k_on["spmv_pq"] * 1e3,
+            "fused_spmv": {"model_bytes": by, "gbs": by / t_k / 1e9, "hbm_frac": by / t_k / 1e9 / peaks["hbm_gbs"],
+                           "fp64_tflops": 2 * fmas / t_k / 1e12,
+                           "fp64_frac": 2 * fmas / t_k / 1e12 / FP64_NOMINAL_TFLOPS}}
+
+
+def sampling_comparison(esd, A, p, args, b, torch):
+    """Sampling method A (Appendix A) against method B (Section 4.2) on the same first solve:
+    m sampled iterates each, W = Q from their errors, then the deflated and the SC solve of
+    another right-hand side (seeded uniform random, as the paper's later systems) from x = 0;
+    the paper compares the two methods by such counts."""
+    import workloads as wl
+    b2 = torch.from_numpy(wl.random_rhs(p.n, wl.SEED_BASE + 8)).to(b.device)
+    out = {}
+    for name, method in (("A", esd.SAMPLING_A), ("B", esd.SAMPLING_B)):
+        S = esd.Solver(A, maxit_cap=20000, sample_cap=max(args.m, 2), sampling=method)
+        x = torch.zeros_like(b)
+        st, it0, rr = S.solve(b, x, args.tol, 20000, args.m)
+        kept = S.sample_and_build_W()
+        row = {"first_solve_iterations": it0, "m_kept": kept, "ritz_min": float(S.ritz_values()[0])}
+        for mname, md in (("plain", esd.PLAIN), ("deflation", esd.DEFLATION), ("sc", esd.SUBSPACE_CORRECTION)):
+            S.set_mode(md)
+            x = torch.zeros_like(b2)
+            st, it, rr = S.solve(b2, x, args.tol, 20000, 0)
+            row[mname + "_iterations"] = it
+        out[name] = row
+    return out
+
+
 def iteration_roofline(S, esd, p, args, x, b, src, peaks):
     """Time per iteration of each mode (graph launches of system 2) against the paper's
-    per-iteration byte model (Eq. ticcg / tsciccg generalised)."""
+    per-iteration byte model (Eq. ticcg / tsciccg generalised to m columns)."""
     import torch
     out = {}
     n, nnz = p.n, p.nnz

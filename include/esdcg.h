@@ -198,8 +198,8 @@ int esd_set_mode(esd_solver* S, int32_t mode);
  *   relres    (host, may be NULL) final ||r_i||/||b|| of the recursive residual; in
  *             deflation mode r_i = P^T (b - A x_i), which equals the true residual of the
  *             returned x (Eq. x1/x2)
- * Plain / SC mode: PCG as in Algorithm "PCG with condition number estimation" without the
- * power method. Deflation: Algorithm "Deflated PCG" with beta = +rho_{i+1}/rho_i and the
+ * Plain / SC mode: PCG as in Algorithm "PCG with condition number estimation", with its
+ * power method once esd_power_start has been called (see there). Deflation: Algorithm "Deflated PCG" with beta = +rho_{i+1}/rho_i and the
  * final x = P x_i + W E^{-1} W^T b. b = 0 gives x = 0 and 0 iterations.
  * The whole solve is one CUDA graph launch (a device-side while loop); the call
  * synchronises once at the end to return iters and relres.
@@ -270,6 +270,35 @@ int esd_ritz_values(esd_solver* S, double* out, int32_t cap, int32_t* count);
  * estimate, Section 5.4) or NaN when there is no W.
  */
 int esd_estimate_cond(esd_solver* S, double* lmin, double* lmax, double* kappa, double* ritz_min);
+
+/*
+ * Power method of Algorithm "PCG with condition number estimation" (Section 5.4): from a start
+ * vector v_0, every CG iteration of the following FP64 plain or subspace-correction solves
+ * also forms v_i = A v_{i-1} / ||A v_{i-1}||_2 in the same pass over the matrix as q = A p
+ * (one read of each entry serves both products). The vector carries over from solve to
+ * solve (and through esd_profile_iterations) until the next esd_power_start. A solve in
+ * deflation mode is refused (ESD_ERR_STATE) while it runs; its iterations would not advance it.
+ *   v0   n doubles (device or host), any nonzero finite vector (the paper: a unit random
+ *        vector); it is normalised here. NULL stops the power method.
+ * Errors: ESD_ERR_STATE for an ESD_FP32_REFINE solver, ESD_ERR_INVALID for a zero or
+ * non-finite v0 (the method is then off).
+ * Costs per iteration: nnz FMAs and 16 bytes per row (read v_{i-1}, write v_i) on top of
+ * the SpMV.
+ */
+int esd_power_start(esd_solver* S, const double* v0);
+
+/*
+ * The power method's estimate lambda_max = (v_k, A v_k) of the current unit vector v_k, the
+ * paper's largest-eigenvalue estimate; with the smallest Ritz value of the errors sampled in
+ * the same solve (esd_sample_and_build_W with theta = +inf, then esd_ritz_values) it gives the
+ * paper's kappa = lambda_max / lambda_min. One pass over A; no iteration is taken.
+ *   lmax   (host, may be NULL) the estimate
+ *   steps  (host, may be NULL) k, the products taken since esd_power_start
+ *   v      (may be NULL) n doubles (device or host) receiving v_k
+ * Errors: ESD_ERR_STATE when not started, ESD_ERR_BREAKDOWN when the vector vanished or
+ * overflowed (A v = 0 for a singular A, or a non-finite product).
+ */
+int esd_power_estimate(esd_solver* S, double* lmax, int32_t* steps, double* v);
 
 /* alpha_j and beta_j of the last solve (host arrays of cap entries). */
 int esd_get_history(esd_solver* S, double* alpha, double* beta, int32_t cap, int32_t* count);

@@ -29,7 +29,7 @@ __all__ = [
     "esd_set_W", "esd_get_W", "esd_ritz_values", "esd_estimate_cond", "esd_get_history",
     "esd_get_samples", "esd_backward_euler_rhs", "esd_profile_iterations", "esd_last_error",
     "esd_lanczos_extremes_noalloc", "NOALLOC_MAX_K", "esd_matrix_set_values", "esd_fv_assemble",
-    "esd_fv_grad_theta", "esd_refresh_W", "EsdFvGrid",
+    "esd_fv_grad_theta", "esd_refresh_W", "EsdFvGrid", "esd_power_start", "esd_power_estimate",
 ]
 NOALLOC_MAX_K = 32768
 
@@ -114,6 +114,8 @@ def lib(build_if_missing: bool = True):
             "esd_fv_assemble": (i32, [vp, P(EsdFvGrid), vp, vp]),
             "esd_fv_grad_theta": (i32, [vp, P(EsdFvGrid), vp, vp, vp, vp, vp]),
             "esd_refresh_W": (i32, [vp]),
+            "esd_power_start": (i32, [vp, vp]),
+            "esd_power_estimate": (i32, [vp, P(f64), P(i32), vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -316,6 +318,18 @@ def esd_estimate_cond(h):
     return lo.value, hi.value, k.value, r.value
 
 
+def esd_power_start(h, v0):
+    """v0: n doubles (NumPy or CUDA tensor), or None to stop the power method."""
+    _check(lib().esd_power_start(h, None if v0 is None else _ptr(v0)))
+
+
+def esd_power_estimate(h, v=None):
+    """(lambda_max, steps); v (n doubles, optional) receives the unit power vector."""
+    lam, k = C.c_double(), C.c_int32()
+    _check(lib().esd_power_estimate(h, C.byref(lam), C.byref(k), None if v is None else _ptr(v)))
+    return lam.value, k.value
+
+
 def esd_get_history(h, cap):
     a, b = np.zeros(cap), np.zeros(cap)
     cnt = C.c_int32()
@@ -452,6 +466,27 @@ class Solver:
 
     def estimate_cond(self):
         return esd_estimate_cond(self._h)
+
+    def power_start(self, v0):
+        """Start (or, with None, stop) the power method of Algorithm PCG-con (Section 5.4)."""
+        v0 = np.ascontiguousarray(v0, dtype=np.float64) if isinstance(v0, np.ndarray) else v0
+        esd_power_start(self._h, v0)
+
+    def power_estimate(self, vector=False):
+        """(lambda_max, steps) of the power method, plus the unit vector when asked."""
+        if not vector:
+            return esd_power_estimate(self._h)
+        v = np.zeros(self.matrix.n)
+        lam, k = esd_power_estimate(self._h, v)
+        return lam, k, v
+
+    def paper_cond_estimate(self):
+        """Algorithm PCG-con's kappa = lambda_max / lambda_min: lambda_max from the power
+        method, lambda_min the smallest Ritz value of the current W (after
+        sample_and_build_W with theta = inf on the sampled solve). Returns (lmax, lmin, kappa)."""
+        lmax, _ = self.power_estimate()
+        lmin = float(self.ritz_values()[0])
+        return lmax, lmin, lmax / lmin
 
     def history(self):
         return esd_get_history(self._h, self.maxit_cap)

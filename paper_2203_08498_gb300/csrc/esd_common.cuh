@@ -92,6 +92,18 @@ struct State {
 
 enum Ticket { kTkSpmv = 0, kTkUpdate = 1, kTkSweep = 2, kTkAux = 3, kTkAux2 = 4 };
 
+// Power method of the condition estimate (Section 5.4). It lives across solves: each CG
+// iteration multiplies the power vector by A in the same matrix pass as A p. The vector is
+// kept unnormalised as w (the raw product) with its normalising factor: v = scale * w.
+struct PowerState {
+  double scale;  // 1 / ||w||_2 of the stored w
+  double ww;     // ||w||^2 of the last Rayleigh-quotient pass
+  double wAw;    // (w, A w) of the last Rayleigh-quotient pass
+  int steps;     // products taken since the start vector; w lives in buffer steps & 1
+  int failed;    // a norm was zero or not finite
+  unsigned int ticket;
+};
+
 // Device state of the FP64 iterative refinement around FP32 inner solves.
 struct RefineState {
   double bb;          // ||b||^2

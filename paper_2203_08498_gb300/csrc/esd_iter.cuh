@@ -49,6 +49,10 @@ enum { kModePlain = ESD_PLAIN, kModeDefl = ESD_DEFLATION, kModeSC = ESD_SUBSPACE
 #ifndef ESD_ROW_UNROLL_F32
 #define ESD_ROW_UNROLL_F32 4
 #endif
+// resident blocks per SM of the SpMV that also multiplies the power vector
+#ifndef ESD_POW_MINB
+#define ESD_POW_MINB 2
+#endif
 #define ESD_PRAGMA(x) _Pragma(#x)
 #define ESD_UNROLL(n) ESD_PRAGMA(unroll n)
 
@@ -105,6 +109,25 @@ __device__ __forceinline__ T row_fma_diff(const SellView<T>& M, const int4& md, 
     for (int k = 0; k < md.y; ++k) acc = fma(ld_stream(vp + k * kSlice), v[ld_stream(cp + k * kSlice)] - vi, acc);
   }
   return acc;
+}
+
+// Two FP64 row products with one read of the matrix row: au = A u, av = A v (the fused
+// SpMV of the power method, Section 5.4). au takes the FMAs in the order row_fma does.
+__device__ __forceinline__ void row_fma2(const SellView<double>& M, const int4& md, int lane,
+                                         const double* __restrict__ u, const double* __restrict__ v, double& au,
+                                         double& av) {
+  const int* cp = M.col + md.x + lane;
+  const double* vp = M.val + md.x + lane;
+  double a = 0.0, b = 0.0;
+  ESD_UNROLL(ESD_ROW_UNROLL)
+  for (int k = 0; k < md.y; ++k) {
+    const double val = ld_stream(vp + k * kSlice);
+    const int j = ld_stream(cp + k * kSlice);
+    a = fma(val, u[j], a);
+    b = fma(val, v[j], b);
+  }
+  au = a;
+  av = b;
 }
 
 // Index of W / AW entry (row i = lane l of slice s, column k) in the layout of this context:
@@ -274,9 +297,13 @@ constexpr int defl_minb() {
   return M == 0 ? sweep_minb<T>() : ((sizeof(T) == 4 ? M <= 32 : M <= 16) ? 2 : 1);
 }
 
-template <typename T, int M>
-__global__ void __launch_bounds__(kBlock, defl_minb<T, M>()) k_spmv_pq(IterCtx<T> c, SliceSet set) {
-  constexpr int R = 1 + M;
+// q = A p and (p, q) [+ h = (AW)^T p, y = E^-1 h in deflation]; the last block sets alpha.
+// POW (FP64, M = 0): the same matrix pass also forms w' = A v = scale * (A w) of the power
+// vector, with ||w'||^2 (Algorithm PCG-con's (q v) = A (p v)).
+template <typename T, int M, bool POW = false>
+__global__ void __launch_bounds__(kBlock, POW ? ESD_POW_MINB : defl_minb<T, M>()) k_spmv_pq(IterCtx<T> c, SliceSet set) {
+  static_assert(!POW || (M == 0 && sizeof(T) == 8), "the power method runs in the FP64 M = 0 product");
+  constexpr int R = 1 + M + (POW ? 1 : 0);
   __shared__ T red[red_size<R>()];
   __shared__ double hy_s;
   pdl_enter();
@@ -291,6 +318,15 @@ __global__ void __launch_bounds__(kBlock, defl_minb<T, M>()) k_spmv_pq(IterCtx<T
     }
   }
   if (st->conv) return;
+  const double* w_in = nullptr;
+  double* w_out = nullptr;
+  double w_scale = 0.0;
+  if (POW) {
+    const int k = c.pws->steps;
+    w_in = c.pw[k & 1];
+    w_out = c.pw[(k + 1) & 1];
+    w_scale = c.pws->scale;
+  }
   T acc[R];
 #pragma unroll
   for (int k = 0; k < R; ++k) acc[k] = T(0);
@@ -301,7 +337,10 @@ __global__ void __launch_bounds__(kBlock, defl_minb<T, M>()) k_spmv_pq(IterCtx<T
     const int i = md.z + lane;
     const bool valid = lane < md.w;
     T qi;
-    if (sizeof(T) == 4 && c.rowsum) {
+    double wi = 0.0;
+    if constexpr (POW) {
+      row_fma2(c.Av, md, lane, c.p, w_in, qi, wi);
+    } else if (sizeof(T) == 4 && c.rowsum) {
       const T pv = valid ? c.p[i] : T(0);
       qi = row_fma_diff(c.Av, md, lane, c.p, pv, valid ? c.rowsum[i] : T(0), T(0));
     } else {
@@ -313,9 +352,27 @@ __global__ void __launch_bounds__(kBlock, defl_minb<T, M>()) k_spmv_pq(IterCtx<T
       acc[0] = fma(pi, qi, acc[0]);
 #pragma unroll
       for (int k = 0; k < M; ++k) acc[1 + k] = fma(c.AW[wix<M>(c, k, i, s, lane)], pi, acc[1 + k]);
+      if constexpr (POW) {
+        const double wv = wi * w_scale;  // A v with v = scale * w
+        w_out[i] = wv;
+        acc[R - 1] = fma(wv, wv, acc[R - 1]);
+      }
     }
   }
   if (grid_sum_multi<R>(acc, red, (T*)c.partials, &st->ticket[kTkSpmv])) {
+    if constexpr (POW) {
+      if (threadIdx.x == 0) {
+        const double ww = red[R - 1];
+        PowerState* ps = c.pws;
+        ps->steps += 1;
+        if (ww > 0.0 && isfinite(ww)) {
+          ps->scale = 1.0 / sqrt(ww);
+        } else {
+          ps->scale = 0.0;
+          ps->failed = 1;
+        }
+      }
+    }
     if (M > 0) {
       if (threadIdx.x < 32) {
         double part = 0.0;
@@ -874,7 +931,17 @@ void launch_iteration(const IterCtx<T>& c, cudaStream_t s, KernelMarks* marks) {
   const SliceSet& all = c.A->all;
   const int Mm = (c.mode == ESD_DEFLATION) ? c.M : 0;
   if (marks) marks->mark(s, "start");
-  ESD_DISPATCH_M(Mm, { auto k = k_spmv_pq<T, MM>; ESD_LAUNCH(k, all.total(), s, c, all); });
+  if (c.pws) {
+    if constexpr (sizeof(T) == 8) {
+      if (Mm != 0) throw Error(ESD_ERR_STATE, "the power method runs in plain or subspace-correction mode");
+      auto k = k_spmv_pq<T, 0, true>;
+      ESD_LAUNCH(k, all.total(), s, c, all);
+    } else {
+      throw Error(ESD_ERR_STATE, "the power method runs in FP64 solves");
+    }
+  } else {
+    ESD_DISPATCH_M(Mm, { auto k = k_spmv_pq<T, MM>; ESD_LAUNCH(k, all.total(), s, c, all); });
+  }
   if (marks) marks->mark(s, "spmv_pq");
   const bool fin = c.pre == ESD_PRECOND_NONE || c.A->fwd_sets.empty();
   launch_update<T>(c, 1, fin ? 1 : 0, s, marks);

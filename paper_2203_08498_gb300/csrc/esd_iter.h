@@ -42,6 +42,9 @@ struct IterCtx {
   int pre = ESD_PRECOND_IC0;
   int x_zero = 0;  // the start vector is known to be zero (r0 = b without a product)
   int wsm = 0;     // W and AW slice-major: entry (row of slice s, lane l; column k) at (s M + k) 32 + l
+  // power method (FP64 plain / SC solves): w in pw[steps & 1], the next product into the other
+  double* pw[2] = {nullptr, nullptr};
+  PowerState* pws = nullptr;
 };
 
 // Optional event marks between the kernels of a launch sequence (profiling): mark() records
@@ -68,6 +71,12 @@ void launch_iteration(const IterCtx<T>& c, cudaStream_t s, KernelMarks* marks = 
 template <typename T> void launch_finish(const IterCtx<T>& c, cudaStream_t s);     // flush, correction
 // ||b - A x||^2 into st->true_rr
 void launch_true_residual(const IterCtx<double>& c, cudaStream_t s);
+// Power vector: ww = ||w||^2 and wAw = (w, A w) of the stored w (in pw[steps & 1]); with
+// set_scale also scale = 1/||w|| and steps = 0 (w is a new start vector).
+void launch_power_rq(const esd_matrix* A, double* const pw[2], PowerState* pws, double* partials, int set_scale,
+                     cudaStream_t s);
+// unit = w / ||w||, with ||w||^2 from the last launch_power_rq
+void launch_power_unit(const esd_matrix* A, const double* w, const PowerState* pws, double* unit, cudaStream_t s);
 // y = A X for an n x m block (column-major, stride ld), m columns
 void launch_spmm(const esd_matrix* A, const double* X, double* Y, size_t ld, int m, cudaStream_t s);
 // b = x * a + s_vec

@@ -42,6 +42,58 @@ void launch_axpby(int n, const double* x, double a, const double* sv, double* b,
   ESD_CUDA(cudaGetLastError());
 }
 
+// Rayleigh-quotient pass of the power vector (Section 5.4): ||w||^2 and (w, A w).
+__global__ void __launch_bounds__(kBlock, 4) k_power_rq(SellView<double> Av, SliceSet set, const double* w0,
+                                                      const double* w1, PowerState* ps, double* partials,
+                                                      int set_scale) {
+  constexpr int R = 2;
+  __shared__ double red[red_size<R>()];
+  pdl_enter();
+  const double* w = (ps->steps & 1) ? w1 : w0;
+  double acc[R] = {0.0, 0.0};
+  ESD_LOOP_SLICES(set) {
+    int r;
+    const int s = set.slice(g, &r);
+    const int4 md = Av.meta[s];
+    const double awi = row_fma(Av, md, lane, w, 0.0);
+    if (lane < md.w) {
+      const double wi = w[md.z + lane];
+      acc[0] = fma(wi, wi, acc[0]);
+      acc[1] = fma(wi, awi, acc[1]);
+    }
+  }
+  if (grid_sum_multi<R>(acc, red, partials, &ps->ticket)) {
+    if (threadIdx.x == 0) {
+      ps->ww = red[0];
+      ps->wAw = red[1];
+      if (set_scale) {  // a new start vector v_0 = w / ||w||
+        const bool ok = red[0] > 0.0 && isfinite(red[0]);
+        ps->scale = ok ? 1.0 / sqrt(red[0]) : 0.0;
+        ps->failed = ok ? 0 : 1;
+        ps->steps = 0;
+      }
+    }
+  }
+}
+
+// unit = w / ||w|| with ||w||^2 from the preceding k_power_rq
+__global__ void __launch_bounds__(kBlock) k_power_unit(int n, const double* w, const PowerState* ps, double* unit) {
+  const double sc = 1.0 / sqrt(ps->ww);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) unit[i] = w[i] * sc;
+}
+
+void launch_power_rq(const esd_matrix* A, double* const pw[2], PowerState* ps, double* partials, int set_scale,
+                     cudaStream_t s) {
+  auto k = k_power_rq;
+  ESD_LAUNCH(k, A->all.total(), s, A->A.view<double>(), A->all, (const double*)pw[0], (const double*)pw[1], ps,
+             partials, set_scale);
+}
+
+void launch_power_unit(const esd_matrix* A, const double* w, const PowerState* ps, double* unit, cudaStream_t s) {
+  k_power_unit<<<max_grid_blocks(), kBlock, 0, s>>>(A->n, w, ps, unit);
+  ESD_CUDA(cudaGetLastError());
+}
+
 void launch_true_residual(const IterCtx<double>& c, cudaStream_t s) {
   auto k = k_true_res<double>;
   ESD_LAUNCH(k, c.A->all.total(), s, c, c.A->all);

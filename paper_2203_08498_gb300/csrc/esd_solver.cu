@@ -74,8 +74,12 @@ struct esd_solver {
   bool have_W = false;
   int w_version = 0;
   int w_values_version = -1;  // the matrix values W's AW and E were formed for
+  // power method of the condition estimate: two vectors (stride ld) and its device state
+  DevBuf pw_v, pw_state;
+  bool pw_on = false;
   cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
   int exec_version[3] = {-1, -1, -1};
+  bool exec_pw[3] = {false, false, false};
   int last_iters = 0, last_status = 0, last_sample_m = 0, last_maxit = 0;
   double last_relres = 0.0, last_true = 0.0;
   AuxBuild aux;
@@ -159,11 +163,16 @@ struct esd_solver {
     c.rho_stride = (size_t)max_grid_blocks();
     c.st = state.as<State>();
     c.sflags = A->slice_flags.as<unsigned char>();
+    if (pw_on) {
+      c.pw[0] = pw_v.as<double>();
+      c.pw[1] = pw_v.as<double>() + ld;
+      c.pws = pw_state.as<PowerState>();
+    }
     return c;
   }
 
   void build_graph(int md) {
-    if (exec[md] && exec_version[md] == w_version) return;
+    if (exec[md] && exec_version[md] == w_version && exec_pw[md] == pw_on) return;
     if (exec[md]) {
       cudaGraphExecDestroy(exec[md]);
       exec[md] = nullptr;
@@ -182,6 +191,7 @@ struct esd_solver {
     ESD_CUDA(err);
     exec[md] = e;
     exec_version[md] = w_version;
+    exec_pw[md] = pw_on;
   }
 
   // r0, z0, p0 -> while (not stopped) { PCG iteration } -> correction, true residual
@@ -471,6 +481,8 @@ int esd_solve(esd_solver* S, const double* b, double* x, double tol, int32_t max
             "the IC(0) factor is missing or stale (the matrix values changed): call esd_factor_ic0");
   ESD_CHECK(S->mode == ESD_PLAIN || S->w_values_version == S->A->values_version, ESD_ERR_STATE,
             "the matrix values changed after W was built: call esd_refresh_W");
+  ESD_CHECK(!S->pw_on || S->mode != ESD_DEFLATION, ESD_ERR_STATE,
+            "the power method runs in plain or subspace-correction solves (esd_power_start(S, NULL) stops it)");
   cudaStream_t s = S->stream;
   const int n = S->A->n;
   if (S->fp32) S->A->ensure_fp32();
@@ -629,6 +641,62 @@ int esd_ritz_values(esd_solver* S, double* out, int32_t cap, int32_t* count) {
   ESD_CUDA(cudaMemcpyAsync(out, S->ritz.get(), sizeof(double) * k, cudaMemcpyDeviceToHost, S->stream));
   ESD_CUDA(cudaStreamSynchronize(S->stream));
   if (count) *count = S->m;
+  return ESD_OK;
+  ESD_API_END
+}
+
+int esd_power_start(esd_solver* S, const double* v0) {
+  ESD_API_BEGIN
+  ESD_CHECK(S, ESD_ERR_INVALID, "NULL solver");
+  if (!v0) {
+    S->pw_on = false;
+    return ESD_OK;
+  }
+  ESD_CHECK(!S->fp32, ESD_ERR_STATE, "the power method runs in FP64 solves");
+  cudaStream_t s = S->stream;
+  const size_t ld = S->ld;
+  if (!S->pw_v.get()) {
+    S->pw_v.alloc(sizeof(double) * 2 * ld);
+    ESD_CUDA(cudaMemsetAsync(S->pw_v.get(), 0, S->pw_v.bytes(), s));  // sentinels (index n) stay 0
+    S->pw_state.alloc(sizeof(PowerState));
+  }
+  S->pw_on = false;
+  ESD_CUDA(cudaMemsetAsync(S->pw_state.get(), 0, sizeof(PowerState), s));
+  copy_in(v0, S->pw_v.get(), sizeof(double) * S->A->n, s);
+  double* const pw[2] = {S->pw_v.as<double>(), S->pw_v.as<double>() + ld};
+  launch_power_rq(S->A, pw, S->pw_state.as<PowerState>(), S->partials.as<double>(), 1, s);
+  PowerState h;
+  ESD_CUDA(cudaMemcpyAsync(&h, S->pw_state.get(), sizeof(PowerState), cudaMemcpyDeviceToHost, s));
+  ESD_CUDA(cudaStreamSynchronize(s));
+  ESD_CHECK(!h.failed, ESD_ERR_INVALID, "the start vector is zero or not finite");
+  S->pw_on = true;
+  return ESD_OK;
+  ESD_API_END
+}
+
+int esd_power_estimate(esd_solver* S, double* lmax, int32_t* steps, double* v) {
+  ESD_API_BEGIN
+  ESD_CHECK(S, ESD_ERR_INVALID, "NULL solver");
+  ESD_CHECK(S->pw_on, ESD_ERR_STATE, "the power method was not started (esd_power_start)");
+  cudaStream_t s = S->stream;
+  const size_t ld = S->ld;
+  double* const pw[2] = {S->pw_v.as<double>(), S->pw_v.as<double>() + ld};
+  PowerState* ps = S->pw_state.as<PowerState>();
+  launch_power_rq(S->A, pw, ps, S->partials.as<double>(), 0, s);
+  PowerState h;
+  ESD_CUDA(cudaMemcpyAsync(&h, ps, sizeof(PowerState), cudaMemcpyDeviceToHost, s));
+  ESD_CUDA(cudaStreamSynchronize(s));
+  ESD_CHECK(!h.failed && h.ww > 0.0 && std::isfinite(h.ww), ESD_ERR_BREAKDOWN,
+            "the power vector vanished or overflowed");
+  if (lmax) *lmax = h.wAw / h.ww;
+  if (steps) *steps = h.steps;
+  if (v) {
+    // the buffer the next product writes is free until then
+    double* unit = pw[(h.steps + 1) & 1];
+    launch_power_unit(S->A, pw[h.steps & 1], ps, unit, s);
+    copy_out(unit, v, sizeof(double) * S->A->n, s);
+    ESD_CUDA(cudaStreamSynchronize(s));
+  }
   return ESD_OK;
   ESD_API_END
 }
