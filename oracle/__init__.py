@@ -114,6 +114,25 @@ def spmv(prob, x):
     return y
 
 
+def diag_scale(prob):
+    """Symmetric Jacobi scaling of the test matrices (Sections 5.1, 5.4): ``A^ = D^-1/2 A
+    D^-1/2`` with ``D = diag(A)``, entry by entry ``a^_ij = (a_ij d_i) d_j`` for
+    ``d_i = 1/sqrt(a_ii)``. Returns (a copy of the problem holding A^, d). A solve of
+    ``A x = b`` is the solve of ``A^ x^ = d * b`` with ``x = d * x^``."""
+    import copy
+    rp = np.asarray(prob.rowptr, dtype=np.int64)
+    ci = np.asarray(prob.colind, dtype=np.int64)
+    va = np.asarray(prob.val, dtype=np.float64)
+    rows = np.repeat(np.arange(prob.n), np.diff(rp))
+    diag = va[rows == ci]
+    if len(diag) != prob.n or not np.all(diag > 0) or not np.all(np.isfinite(diag)):
+        raise ValueError("diagonal scaling needs a positive finite diagonal entry in every row")
+    d = 1.0 / np.sqrt(diag)
+    out = copy.copy(prob)
+    out.val = (va * d[rows]) * d[ci]
+    return out, d
+
+
 class IC0:
     """IC(0) factor ``M = L L^T``, ``L`` on the pattern of tril(A) (diagonal last per row).
 

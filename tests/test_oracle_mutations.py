@@ -116,3 +116,34 @@ def test_planted_gradient_mistake_is_caught(name, monkeypatch):
     monkeypatch.setattr(oracle, attr, wrong)
     with pytest.raises(AssertionError):
         grad_pins.test_theta_gradient_matches_finite_differences("3d_3x4x2_steady")
+
+
+def _scale_with(dfun, two_sided):
+    def wrong(prob):
+        import copy
+        rp = np.asarray(prob.rowptr, dtype=np.int64)
+        ci = np.asarray(prob.colind, dtype=np.int64)
+        va = np.asarray(prob.val, dtype=np.float64)
+        rows = np.repeat(np.arange(prob.n), np.diff(rp))
+        d = dfun(va[rows == ci])
+        out = copy.copy(prob)
+        out.val = (va * d[rows]) * d[ci] if two_sided else va * d[rows] * d[rows]
+        return out, d
+    return wrong
+
+
+SCALE_MUTANTS = {
+    # d_i^2 applied on the row side only (not symmetric)
+    "scale_one_sided": (_scale_with(lambda a: 1.0 / np.sqrt(a), False),
+                        pins.test_diag_scaled_matrix_symmetric_unit_diagonal),
+    # d_i = 1/a_ii instead of 1/sqrt(a_ii)
+    "scale_no_sqrt": (_scale_with(lambda a: 1.0 / a, True), pins.test_diag_scaled_laplacian_closed_form),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SCALE_MUTANTS))
+def test_planted_scaling_mistake_is_caught(name, monkeypatch):
+    wrong, pin = SCALE_MUTANTS[name]
+    monkeypatch.setattr(oracle, "diag_scale", wrong)
+    with pytest.raises(AssertionError):
+        pin()

@@ -259,6 +259,66 @@ def test_lanczos_preconditioned_bounds():
 
 # ---------------------------------------------------------------- auxiliary matrix
 
+# ---------------------------------------------------------------- diagonal scaling
+
+def test_diag_scaled_laplacian_closed_form():
+    """tridiag(-1, 2, -1) scaled by its diagonal is tridiag(-1/2, 1, -1/2): unit diagonal and
+    eigenvalues 1 - cos(k pi/(n+1)); CG on it reaches those extremes in its Lanczos matrix."""
+    n = 40
+    p = wl.laplacian_1d(n)
+    ps, d = oracle.diag_scale(p)
+    np.testing.assert_array_equal(d, np.full(n, 1 / np.sqrt(2.0)))
+    A = ps.scipy().toarray()
+    np.testing.assert_allclose(np.diag(A), 1.0, rtol=1e-15)
+    np.testing.assert_array_equal(A, A.T)
+    ev = np.linalg.eigvalsh(A)
+    np.testing.assert_allclose(ev, np.sort(1 - np.cos(np.arange(1, n + 1) * np.pi / (n + 1))), atol=1e-14)
+    out = oracle.System(ps, None).solve(np.random.default_rng(2).standard_normal(n), tol=1e-14, maxit=200)
+    lmin, lmax, _ = oracle.estimate_cond(out["alpha"], out["beta"])
+    assert lmin == pytest.approx(1 - np.cos(np.pi / (n + 1)), rel=1e-8)
+    assert lmax == pytest.approx(1 - np.cos(n * np.pi / (n + 1)), rel=1e-8)
+
+
+def test_diag_scaled_matrix_symmetric_unit_diagonal():
+    """On variable coefficients (contrast 1e3): A^ keeps A's symmetry, has a unit diagonal,
+    and equals D^-1/2 A D^-1/2 formed as a dense product."""
+    p = wl.small_3d(7, seed=5)
+    ps, d = oracle.diag_scale(p)
+    A = p.scipy().toarray()
+    As = ps.scipy().toarray()
+    np.testing.assert_allclose(As, As.T, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(np.diag(As), 1.0, rtol=4.5e-16)  # (a d) d: two roundings
+    Dm = np.diag(1.0 / np.sqrt(np.diag(A)))
+    np.testing.assert_allclose(As, Dm @ A @ Dm, rtol=1e-15, atol=1e-16)
+
+
+def test_ic0_is_invariant_under_diag_scaling():
+    """IC(0) commutes with symmetric diagonal scaling: the factor of D^-1/2 A D^-1/2 is
+    D^-1/2 L (every product on the pattern scales by d_i d_j), so ICCG takes the same
+    iterations on A x = b and on A^ x^ = d b, and d x^ solves A x = b."""
+    p = wl.small_3d(7, seed=5)
+    ps, d = oracle.diag_scale(p)
+    L = oracle.IC0(p).dense_L()
+    Ls = oracle.IC0(ps).dense_L()
+    np.testing.assert_allclose(Ls, d[:, None] * L, rtol=1e-12, atol=1e-14 * np.abs(Ls).max())
+    b = p.source
+    out = oracle.System(p, oracle.IC0(p)).solve(b, tol=1e-10)
+    outs = oracle.System(ps, oracle.IC0(ps)).solve(d * b, tol=1e-10)
+    assert abs(out["iters"] - outs["iters"]) <= 1
+    x = d * outs["x"]
+    assert np.linalg.norm(b - p.scipy() @ x) <= 1e-8 * np.linalg.norm(b)
+
+
+def test_diag_scaling_rejects_nonpositive_diagonal():
+    p = wl.laplacian_1d(6)
+    bad = wl.laplacian_1d(6)
+    bad.val = p.val.copy()
+    rows = np.repeat(np.arange(6), np.diff(p.rowptr))
+    bad.val[np.flatnonzero(rows == p.colind)[2]] = -1.0
+    with pytest.raises(ValueError):
+        oracle.diag_scale(bad)
+
+
 # ---------------------------------------------------------------- power method (Section 5.4)
 
 @pytest.mark.parametrize("k", [0, 1, 2, 5, 30])
