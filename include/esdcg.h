@@ -67,6 +67,19 @@ const char* esd_last_error(void);
 /* ---------------------------------------------------------------- matrix */
 
 /*
+ * ESD_MATRIX_DIAG_SCALE: the library holds the symmetrically Jacobi-scaled matrix
+ * A^ = D^-1/2 A D^-1/2, D = diag(A), a^_ij = (a_ij d_i) d_j with d_i = 1/sqrt(a_ii) (the paper
+ * scales every test matrix this way, Sections 5.1 and 5.4). Every later call (SpMV, IC(0),
+ * solves, W, Ritz values, condition estimates, esd_matrix_set_values) works on A^, so a
+ * solve of A x = b is the solve of A^ x^ = d o b followed by x = d o x^ (esd_matrix_diag_scale
+ * returns d), with the stopping test on the scaled residual. A diagonal entry that is not
+ * positive and finite returns ESD_ERR_INVALID. The finite-volume assembly and its theta
+ * gradient refer to the unscaled operator and refuse a scaled matrix (ESD_ERR_STATE);
+ * esd_pattern_grad differentiates with respect to the entries of A^.
+ */
+#define ESD_MATRIX_DIAG_SCALE 1u
+
+/*
  * Create the library's copy of an SPD matrix A (the fixed matrix of the sequence
  * A x_k = b_k, Eq. ak2/ak3) from CSR.
  *   n           rows (= columns), 1 <= n < 2^31 - 64
@@ -77,7 +90,7 @@ const char* esd_last_error(void);
  *   colour_ptr  ncolours+1 int32: rows colour_ptr[c] .. colour_ptr[c+1]-1 form colour c;
  *               colour_ptr[0] = 0, colour_ptr[ncolours] = n (host)
  *   ncolours    1 .. 64; no two rows of one colour may be coupled (multicolour ordering)
- *   flags       reserved, pass 0
+ *   flags       0 or ESD_MATRIX_DIAG_SCALE (see there)
  *   stream      cudaStream_t on which all later work is ordered (0 = legacy default stream)
  * Requirements checked on the device: sorted in-range columns, a diagonal entry in every
  * row, a structurally symmetric pattern, no coupling inside a colour. Violations return
@@ -88,6 +101,11 @@ int esd_create_matrix(int32_t n, int64_t nnz, const int32_t* rowptr, const int32
                       const double* val, const int32_t* colour_ptr, int32_t ncolours,
                       uint32_t flags, void* stream, esd_matrix** out);
 int esd_matrix_destroy(esd_matrix* A);
+
+/* d_i = 1/sqrt(a_ii) of a matrix created with ESD_MATRIX_DIAG_SCALE, for the diagonal of the
+ * values last given (creation or esd_matrix_set_values). d: n doubles, host or device.
+ * ESD_ERR_STATE for an unscaled matrix. */
+int esd_matrix_diag_scale(const esd_matrix* A, double* d);
 
 /* Dimensions and the colour levels found at creation: a level is a set of colours with
  * no coupling among them, so one launch serves it (forward / backward). */
@@ -250,6 +268,17 @@ int esd_sample_and_build_W(esd_solver* S, double theta, int32_t* m_kept);
 /* Use a caller-supplied W (n x m column-major doubles, device or host, 1 <= m <= 64,
  * columns linearly independent); AW, E and E^{-1} are built as above. */
 int esd_set_W(esd_solver* S, const double* W, int32_t m);
+
+/*
+ * Switch an existing solver between ESD_FP64 and ESD_FP32_REFINE (the precision of
+ * esd_params) and set the inner tolerance of the refinement form (0 < inner_tol < 1; ignored
+ * for ESD_FP64). The first switch to the refinement form allocates its buffers and the FP32
+ * copies of the matrix. A W already built is kept: switching to the refinement form rounds it
+ * to FP32 and forms AW, E and E^-1 again for that W (as esd_set_W would); switching back keeps
+ * that W. Errors: ESD_ERR_INVALID for sampling method B with the refinement form,
+ * ESD_ERR_STATE while the power method runs (it needs FP64 solves).
+ */
+int esd_set_precision(esd_solver* S, int32_t precision, double inner_tol);
 
 /* AW, E = W^T A W, E^-1 and the Ritz values formed again for the current W and the current
  * values of A (after esd_matrix_set_values / esd_fv_assemble). ESD_ERR_STATE without W. */

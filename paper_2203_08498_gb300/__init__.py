@@ -30,7 +30,9 @@ __all__ = [
     "esd_get_samples", "esd_backward_euler_rhs", "esd_profile_iterations", "esd_last_error",
     "esd_lanczos_extremes_noalloc", "NOALLOC_MAX_K", "esd_matrix_set_values", "esd_fv_assemble",
     "esd_fv_grad_theta", "esd_refresh_W", "EsdFvGrid", "esd_power_start", "esd_power_estimate",
+    "esd_matrix_diag_scale", "MATRIX_DIAG_SCALE", "esd_set_precision",
 ]
+MATRIX_DIAG_SCALE = 1
 NOALLOC_MAX_K = 32768
 
 OK, ERR_INVALID, ERR_NOT_SPD, ERR_BREAKDOWN, ERR_MAXIT, ERR_STATE, ERR_RANK, ERR_CHOL_E, ERR_CUDA, ERR_NOMEM = (
@@ -115,6 +117,8 @@ def lib(build_if_missing: bool = True):
             "esd_fv_grad_theta": (i32, [vp, P(EsdFvGrid), vp, vp, vp, vp, vp]),
             "esd_refresh_W": (i32, [vp]),
             "esd_power_start": (i32, [vp, vp]),
+            "esd_matrix_diag_scale": (i32, [vp, vp]),
+            "esd_set_precision": (i32, [vp, i32, f64]),
             "esd_power_estimate": (i32, [vp, P(f64), P(i32), vp]),
         }
         for name, (res, args) in sig.items():
@@ -189,6 +193,11 @@ def esd_create_matrix(n, nnz, rowptr, colind, val, colour_ptr, ncolours, flags=0
 
 def esd_matrix_destroy(h):
     return _check(lib().esd_matrix_destroy(h))
+
+
+def esd_matrix_diag_scale(h, d):
+    """d (n doubles, NumPy or CUDA tensor) receives 1/sqrt(a_ii) of a scaled matrix."""
+    _check(lib().esd_matrix_diag_scale(h, _ptr(d)))
 
 
 def esd_matrix_info(h):
@@ -318,6 +327,10 @@ def esd_estimate_cond(h):
     return lo.value, hi.value, k.value, r.value
 
 
+def esd_set_precision(h, precision, inner_tol=0.1):
+    _check(lib().esd_set_precision(h, precision, inner_tol))
+
+
 def esd_power_start(h, v0):
     """v0: n doubles (NumPy or CUDA tensor), or None to stop the power method."""
     _check(lib().esd_power_start(h, None if v0 is None else _ptr(v0)))
@@ -374,17 +387,25 @@ def esd_lanczos_extremes_noalloc(alpha, beta, k, out, stream=None):
 class Matrix:
     """Library copy of an SPD CSR matrix in colour-major order (``esd_create_matrix``)."""
 
-    def __init__(self, rowptr, colind, val, colour_ptr, stream=None):
+    def __init__(self, rowptr, colind, val, colour_ptr, stream=None, diag_scale=False):
         n = len(rowptr) - 1
         nnz = len(colind)
         self.n, self.nnz = n, nnz
-        self._h = esd_create_matrix(n, nnz, rowptr, colind, val, colour_ptr, len(colour_ptr) - 1, 0, stream)
+        flags = MATRIX_DIAG_SCALE if diag_scale else 0
+        self._h = esd_create_matrix(n, nnz, rowptr, colind, val, colour_ptr, len(colour_ptr) - 1, flags, stream)
         self.shift = None
 
     @classmethod
-    def from_problem(cls, prob, stream=None):
+    def from_problem(cls, prob, stream=None, diag_scale=False):
         return cls(np.ascontiguousarray(prob.rowptr, np.int32), np.ascontiguousarray(prob.colind, np.int32),
-                   np.ascontiguousarray(prob.val, np.float64), prob.colour_ptr, stream)
+                   np.ascontiguousarray(prob.val, np.float64), prob.colour_ptr, stream, diag_scale)
+
+    def diag_scale(self):
+        """d = 1/sqrt(diag(A)) of a matrix created with diag_scale=True (the library holds
+        D^-1/2 A D^-1/2: solve with b^ = d b, then x = d x^)."""
+        d = np.zeros(self.n)
+        esd_matrix_diag_scale(self._h, d)
+        return d
 
     @property
     def handle(self):
@@ -438,6 +459,9 @@ class Solver:
 
     def set_mode(self, mode):
         esd_set_mode(self._h, mode)
+
+    def set_precision(self, precision, inner_tol=0.1):
+        esd_set_precision(self._h, precision, inner_tol)
 
     def solve(self, b, x, tol=1e-8, maxit=None, sample_m=0):
         return esd_solve(self._h, b, x, tol, maxit or self.maxit_cap, sample_m)

@@ -168,6 +168,7 @@ using namespace esd;
 extern "C" int esd_fv_assemble(esd_matrix* A, const esd_fv_grid* g, const double* theta, const int32_t* cell_row) {
   try {
     ESD_CHECK(A && theta && cell_row, ESD_ERR_INVALID, "NULL argument");
+    ESD_CHECK(!A->scaled, ESD_ERR_STATE, "the finite-volume assembly writes the unscaled operator");
     const FvDev d = fv_dev(g, A->n);
     cudaStream_t s = A->stream;
     DevBuf t0, t1, derr(sizeof(int)), vals(sizeof(double) * (size_t)A->nnz);
@@ -194,6 +195,7 @@ extern "C" int esd_fv_grad_theta(esd_matrix* A, const esd_fv_grid* g, const doub
                                  const double* lambda, const double* x, double* grad_theta) {
   try {
     ESD_CHECK(A && theta && cell_row && lambda && x && grad_theta, ESD_ERR_INVALID, "NULL argument");
+    ESD_CHECK(!A->scaled, ESD_ERR_STATE, "the theta gradient refers to the unscaled operator");
     const FvDev d = fv_dev(g, A->n);
     cudaStream_t s = A->stream;
     const size_t n = (size_t)A->n;

@@ -104,6 +104,8 @@ struct esd_matrix {
   int a32_version = -1;    // values_version of val32 / rowsum32
   int fp32_version = -1;
   double shift = 0.0;
+  bool scaled = false;       // ESD_MATRIX_DIAG_SCALE: the values held are D^-1/2 A D^-1/2
+  esd::DevBuf dscale;        // double: d_i = 1/sqrt(a_ii) of the last values given (scaled only)
   size_t vec_stride() const { return ((size_t)n + 1 + 31) / 32 * 32; }  // doubles per vector
   void ensure_fp32();
 };
@@ -119,6 +121,9 @@ void launch_lanczos_extremes(const double* a, const double* b, int k, double* sc
                              cudaStream_t s);
 // After csr_val changed on the device: refill the sliced-ELL values of A, drop the factor.
 void matrix_values_changed(esd_matrix* A);
+// Scaled matrices: dst = D^-1/2 src D^-1/2 for D = diag(src), and A->dscale = d. Checks the
+// diagonal (positive, finite) before it writes anything; src may equal dst.
+void scale_values(esd_matrix* A, const int* diagpos, const double* src, double* dst);
 void set_last_error(const std::string& msg);
 
 // Kernel launchers used across files (defined in esd_iter.cu).

@@ -335,6 +335,48 @@ static void to_float(const DevBuf& src, DevBuf& dst, long long cnt, cudaStream_t
 
 using namespace esd;
 
+// Symmetric Jacobi scaling of the test matrices (Sections 5.1, 5.4): d_i = 1/sqrt(a_ii).
+__global__ void k_scale_diag(int n, const int* diagpos, const double* val, double* d, int* err) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double a = val[diagpos[i]];
+    if (a > 0.0 && isfinite(a)) {
+      d[i] = 1.0 / sqrt(a);
+    } else {
+      d[i] = 0.0;
+      atomicMin(err, i);
+    }
+  }
+}
+
+// a^_ij = (a_ij d_i) d_j, one thread per row
+__global__ void k_scale_vals(int n, const int* rowptr, const int* colind, const double* d, const double* src,
+                             double* dst) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double di = d[i];
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) dst[k] = (src[k] * di) * d[colind[k]];
+  }
+}
+
+void esd::scale_values(esd_matrix* A, const int* diagpos, const double* src, double* dst) {
+  cudaStream_t s = A->stream;
+  const int n = A->n;
+  DevBuf d(sizeof(double) * A->vec_stride()), err(sizeof(int));
+  ESD_CUDA(cudaMemsetAsync(d.get(), 0, d.bytes(), s));
+  const int first_ok = INT32_MAX;
+  ESD_CUDA(cudaMemcpyAsync(err.get(), &first_ok, sizeof(int), cudaMemcpyHostToDevice, s));
+  const int G = std::min((n + 255) / 256, 4 * max_grid_blocks());
+  k_scale_diag<<<G, 256, 0, s>>>(n, diagpos, src, d.as<double>(), err.as<int>());
+  ESD_CUDA(cudaGetLastError());
+  int bad = 0;
+  ESD_CUDA(cudaMemcpyAsync(&bad, err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+  ESD_CUDA(cudaStreamSynchronize(s));
+  ESD_CHECK(bad == INT32_MAX, ESD_ERR_INVALID,
+            "diagonal scaling needs a positive finite diagonal (first bad row " + std::to_string(bad) + ")");
+  k_scale_vals<<<G, 256, 0, s>>>(n, A->csr_rowptr.as<int>(), A->csr_colind.as<int>(), d.as<double>(), src, dst);
+  ESD_CUDA(cudaGetLastError());
+  A->dscale = std::move(d);
+}
+
 void esd::matrix_values_changed(esd_matrix* A) {
   const int NS = A->nslices;
   k_fill_values<<<(NS * 32 + 255) / 256, 256, 0, A->stream>>>(NS, A->A.meta.as<int4>(), A->csr_rowptr.as<int>(),
@@ -472,7 +514,7 @@ int esd_create_matrix(int32_t n, int64_t nnz, const int32_t* rowptr, const int32
     ESD_CHECK(nnz >= n && nnz < (int64_t)INT32_MAX, ESD_ERR_INVALID, "nnz out of range");
     ESD_CHECK(rowptr && colind && val && colour_ptr, ESD_ERR_INVALID, "NULL array");
     ESD_CHECK(ncolours >= 1 && ncolours <= kMaxColours, ESD_ERR_INVALID, "ncolours must be 1..64");
-    ESD_CHECK(flags == 0, ESD_ERR_INVALID, "flags must be 0");
+    ESD_CHECK((flags & ~ESD_MATRIX_DIAG_SCALE) == 0, ESD_ERR_INVALID, "unknown flag");
     std::unique_ptr<esd_matrix> M(new esd_matrix());
     M->n = n;
     M->nnz = nnz;
@@ -523,6 +565,10 @@ int esd_create_matrix(int32_t n, int64_t nnz, const int32_t* rowptr, const int32
       if (herr[0] & kSameColour) why += " two rows of one colour are coupled;";
       if (herr[0] & kNotSym) why += " pattern not structurally symmetric;";
       throw Error(ESD_ERR_INVALID, "invalid matrix (first bad row " + std::to_string(herr[1]) + "):" + why);
+    }
+    if (flags & ESD_MATRIX_DIAG_SCALE) {
+      M->scaled = true;
+      scale_values(M.get(), diagpos.as<int>(), M->csr_val.as<double>(), M->csr_val.as<double>());
     }
 
     // slices: 32-row slices inside each colour
@@ -614,6 +660,19 @@ int esd_matrix_destroy(esd_matrix* A) {
   return ESD_OK;
 }
 
+int esd_matrix_diag_scale(const esd_matrix* A, double* d) {
+  try {
+    ESD_CHECK(A && d, ESD_ERR_INVALID, "NULL argument");
+    ESD_CHECK(A->scaled, ESD_ERR_STATE, "the matrix was created without ESD_MATRIX_DIAG_SCALE");
+    copy_out(A->dscale.get(), d, sizeof(double) * A->n, A->stream);
+    ESD_CUDA(cudaStreamSynchronize(A->stream));
+    return ESD_OK;
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.code;
+  }
+}
+
 int esd_matrix_info(const esd_matrix* A, int32_t* n, int64_t* nnz, int32_t* ncolours,
                     int32_t* fwd_levels, int32_t* bwd_levels) {
   if (!A) { set_last_error("NULL matrix"); return ESD_ERR_INVALID; }
@@ -628,6 +687,15 @@ int esd_matrix_info(const esd_matrix* A, int32_t* n, int64_t* nnz, int32_t* ncol
 int esd_matrix_set_values(esd_matrix* A, const double* val) {
   try {
     ESD_CHECK(A && val, ESD_ERR_INVALID, "NULL argument");
+    if (A->scaled) {
+      // the new values are scaled by their own diagonal; a bad diagonal leaves A unchanged
+      DevBuf raw(sizeof(double) * (size_t)A->nnz);
+      copy_in(val, raw.get(), sizeof(double) * A->nnz, A->stream);
+      scale_values(A, A->diagpos.as<int>(), raw.as<double>(), A->csr_val.as<double>());
+      matrix_values_changed(A);
+      ESD_CUDA(cudaStreamSynchronize(A->stream));
+      return ESD_OK;
+    }
     copy_in(val, A->csr_val.get(), sizeof(double) * A->nnz, A->stream);
     matrix_values_changed(A);
     ESD_CUDA(cudaStreamSynchronize(A->stream));

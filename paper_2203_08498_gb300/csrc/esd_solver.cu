@@ -275,6 +275,38 @@ struct esd_solver {
     ESD_CUDA(cudaStreamEndCapture(cap, &g));
   }
 
+  // Buffers of the refinement form (FP32 inner vectors, FP64 residual, inner and outer state)
+  // and the FP32 copies of the matrix; allocated once.
+  void enable_fp32() {
+    if (!b32.get()) {
+      const size_t fbytes = sizeof(float) * ld, vbytes = sizeof(double) * ld;
+      for (DevBuf* b : {&b32, &x32, &r32, &p32, &q32, &Y32}) {
+        b->alloc(fbytes);
+        ESD_CUDA(cudaMemsetAsync(b->get(), 0, fbytes, stream));
+      }
+      r64.alloc(vbytes);
+      ESD_CUDA(cudaMemsetAsync(r64.get(), 0, vbytes, stream));
+      state_in.alloc(sizeof(State));
+      ESD_CUDA(cudaMemsetAsync(state_in.get(), 0, sizeof(State), stream));
+      rstate.alloc(sizeof(RefineState));
+      ESD_CUDA(cudaMemsetAsync(rstate.get(), 0, sizeof(RefineState), stream));
+      ESD_CUDA(cudaMallocHost(&hst_in, sizeof(State)));
+      ESD_CUDA(cudaMallocHost(&hrs, sizeof(RefineState)));
+      std::memset(hst_in, 0, sizeof(State));
+      std::memset(hrs, 0, sizeof(RefineState));
+    }
+    fp32 = true;
+    A->ensure_fp32();
+  }
+
+  void drop_graphs() {
+    for (int md = 0; md < 3; ++md) {
+      if (exec[md]) cudaGraphExecDestroy(exec[md]);
+      exec[md] = nullptr;
+      exec_version[md] = -1;
+    }
+  }
+
   // FP32 slice-major copies of W and AW for the inner solves (padding lanes and columns 0)
   void refresh_w32() {
     if (!fp32 || !have_W) return;
@@ -423,25 +455,7 @@ int esd_solver_create(esd_matrix* A, const esd_params* params, esd_solver** out)
   ESD_CUDA(cudaStreamCreateWithFlags(&S->cap, cudaStreamNonBlocking));
   ESD_CUDA(cudaStreamCreateWithFlags(&S->cap2, cudaStreamNonBlocking));
   ESD_CUDA(cudaStreamCreateWithFlags(&S->cap3, cudaStreamNonBlocking));
-  if (p.precision == ESD_FP32_REFINE) {
-    S->fp32 = true;
-    const size_t fbytes = sizeof(float) * S->ld;
-    for (DevBuf* b : {&S->b32, &S->x32, &S->r32, &S->p32, &S->q32, &S->Y32}) {
-      b->alloc(fbytes);
-      ESD_CUDA(cudaMemsetAsync(b->get(), 0, fbytes, S->stream));
-    }
-    S->r64.alloc(vbytes);
-    ESD_CUDA(cudaMemsetAsync(S->r64.get(), 0, vbytes, S->stream));
-    S->state_in.alloc(sizeof(State));
-    ESD_CUDA(cudaMemsetAsync(S->state_in.get(), 0, sizeof(State), S->stream));
-    S->rstate.alloc(sizeof(RefineState));
-    ESD_CUDA(cudaMemsetAsync(S->rstate.get(), 0, sizeof(RefineState), S->stream));
-    ESD_CUDA(cudaMallocHost(&S->hst_in, sizeof(State)));
-    ESD_CUDA(cudaMallocHost(&S->hrs, sizeof(RefineState)));
-    std::memset(S->hst_in, 0, sizeof(State));
-    std::memset(S->hrs, 0, sizeof(RefineState));
-    A->ensure_fp32();
-  }
+  if (p.precision == ESD_FP32_REFINE) S->enable_fp32();
   ESD_CUDA(cudaStreamSynchronize(S->stream));
   *out = S.release();
   return ESD_OK;
@@ -599,6 +613,40 @@ int esd_set_W(esd_solver* S, const double* W, int32_t m) {
   for (int j = 0; j < m; ++j)
     copy_in(W + (size_t)j * n, S->aux.work1.as<double>() + (size_t)j * S->ld, sizeof(double) * n, S->stream);
   install_W(S, S->aux.work1.as<double>(), m, false, std::numeric_limits<double>::infinity());
+  return ESD_OK;
+  ESD_API_END
+}
+
+int esd_set_precision(esd_solver* S, int32_t precision, double inner_tol) {
+  ESD_API_BEGIN
+  ESD_CHECK(S, ESD_ERR_INVALID, "NULL solver");
+  ESD_CHECK(precision == ESD_FP64 || precision == ESD_FP32_REFINE, ESD_ERR_INVALID, "unknown precision");
+  if (precision == ESD_FP64) {
+    if (S->fp32) S->drop_graphs();
+    S->fp32 = false;
+    S->prm.precision = ESD_FP64;
+    return ESD_OK;
+  }
+  ESD_CHECK(inner_tol > 0.0 && inner_tol < 1.0, ESD_ERR_INVALID, "refinement needs 0 < inner_tol < 1");
+  ESD_CHECK(S->prm.sampling == ESD_SAMPLING_A, ESD_ERR_INVALID,
+            "sampling method B is defined on the FP64 solve's relative residual");
+  ESD_CHECK(!S->pw_on, ESD_ERR_STATE, "the power method runs in FP64 solves (esd_power_start(S, NULL) stops it)");
+  const bool was_fp32 = S->fp32;
+  S->prm.precision = ESD_FP32_REFINE;
+  S->prm.inner_tol = inner_tol;
+  if (was_fp32) return ESD_OK;
+  S->drop_graphs();
+  S->enable_fp32();
+  if (S->have_W) {
+    // the inner solves need W rounded to FP32 with AW, E, E^-1 formed for it (as esd_set_W)
+    S->aux.ensure(S->A->n, S->ld);
+    ESD_CUDA(cudaMemcpyAsync(S->aux.work1.get(), S->W.get(), sizeof(double) * S->ld * S->m, cudaMemcpyDeviceToDevice,
+                             S->stream));
+    const int mbar = S->mbar;
+    install_W(S, S->aux.work1.as<double>(), S->m, false, std::numeric_limits<double>::infinity());
+    S->mbar = mbar;
+  }
+  ESD_CUDA(cudaStreamSynchronize(S->stream));
   return ESD_OK;
   ESD_API_END
 }
