@@ -540,7 +540,10 @@ def kernel_model(name, p, args, mode, esd, lv):
     if name == "spmv_pq":
         mb = m if mode == esd.DEFLATION else 0
         extra = 4 * n if s == 4 else 0
-        return (s + 4) * nnz + (2 * s + 4) * n + extra + s * mb * n, nnz + n + mb * n
+        # FP64 deflation with up to 32 (padded) columns forms (AW)^T p in double-float on the
+        # FP32 pipe: only the matrix product and (p, q) are FP64 FMAs
+        df = s == 8 and 0 < mb and pad_m(mb) <= 32
+        return (s + 4) * nnz + (2 * s + 4) * n + extra + s * mb * n, nnz + n + (0 if df else mb * n)
     if name == "update":
         dm = m if mode == esd.DEFLATION else 0
         sm = m if mode == esd.SUBSPACE_CORRECTION else 0
@@ -548,8 +551,14 @@ def kernel_model(name, p, args, mode, esd, lv):
         # x read and written (FP64 in both forms: the refinement form keeps the iterate in
         # FP64), p and q read, r read and written
         base = 16 * n + 4 * s * n
-        return base + s * (dm + sm) * n + 2 * s * n0, 3 * n + (dm + sm) * n + 2 * n0
+        dm_fp64 = 0 if (s == 8 and 0 < dm and pad_m(dm) <= 32) else dm  # AW y in double-float
+        return base + s * (dm + sm) * n + 2 * s * n0, 3 * n + (dm_fp64 + sm) * n + 2 * n0
     return None, None
+
+
+def pad_m(m):
+    """The column count the library compiles for m columns of W."""
+    return 0 if m <= 0 else next(c for c in (8, 16, 24, 32, 64) if m <= c)
 
 
 def roofline(prof, p, args, mode, esd, peaks):

@@ -87,6 +87,8 @@ struct State {
   double y[kMaxM];  // deflation: E^{-1} (AW)^T p
   double u[kMaxM];  // subspace correction / projection: E^{-1} f
   double gacc[kMaxM];  // FP64-iterate deflation: (AW)^T x_i accumulated as sum alpha_k h_k
+  float2 ydf[kMaxM];   // FP64 deflation: y_k c_k 2^(1023-ey) as double-float pairs (c_k: AW column scales)
+  int ydf_exp;         // ey, a biased binary exponent
   unsigned int ticket[8];
 };
 
@@ -212,6 +214,22 @@ __device__ __forceinline__ void warp_sum_chunks(const T (&in)[R], T* red, int la
 // Block-wide sum of R values per thread (R <= 64) with one block barrier: a butterfly per
 // warp, then warp 0 adds the warp totals. On return red[0..R) holds the totals, visible to
 // warp 0 (and to every thread when R > 32). red needs (blockDim/32 + 1) * R entries.
+// Second stage of block_sum_multi: red[w * R + j] holds warp w's totals (written before a
+// block barrier); warp 0 adds them into red[0..R).
+template <int R, typename T>
+__device__ __forceinline__ void block_combine_warps(T* red) {
+  const int lane = lane_id(), warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  if (warp == 0) {
+    for (int j = lane; j < R; j += 32) {
+      T s = 0;
+      for (int w = 0; w < nwarp; ++w) s += red[w * R + j];
+      red[j] = s;
+    }
+    __syncwarp();
+  }
+  if (R > 32) __syncthreads();
+}
+
 template <int R, typename T>
 __device__ __forceinline__ void block_sum_multi(const T (&in)[R], T* red) {
   const int lane = lane_id(), warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -238,10 +256,27 @@ __host__ __device__ constexpr int red_size() {
 // partials[j * gridDim.x + blockIdx.x]; the last block to arrive adds them up in a fixed
 // order and returns true with the totals in red[0..R). No block ever waits for another.
 template <int R, typename T>
+__device__ __forceinline__ bool grid_sum_stage(T* red, T* partials, unsigned int* ticket);
+
+template <int R, typename T>
 __device__ __forceinline__ bool grid_sum_multi(const T (&in)[R], T* red, T* partials,
                                                unsigned int* ticket) {
-  __shared__ bool s_last;
   block_sum_multi<R>(in, red);
+  return grid_sum_stage<R>(red, partials, ticket);
+}
+
+// grid_sum_multi from warp totals already in red[w * R + j] (see block_combine_warps)
+template <int R, typename T>
+__device__ __forceinline__ bool grid_sum_from_warps(T* red, T* partials, unsigned int* ticket) {
+  __syncthreads();
+  block_combine_warps<R>(red);
+  return grid_sum_stage<R>(red, partials, ticket);
+}
+
+// Block totals in red[0..R) -> partials; the last block to arrive adds them up.
+template <int R, typename T>
+__device__ __forceinline__ bool grid_sum_stage(T* red, T* partials, unsigned int* ticket) {
+  __shared__ bool s_last;
   const int G = gridDim.x;
   if (threadIdx.x < R) {
     partials[threadIdx.x * G + blockIdx.x] = red[threadIdx.x];

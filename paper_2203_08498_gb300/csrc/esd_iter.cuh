@@ -49,6 +49,10 @@ enum { kModePlain = ESD_PLAIN, kModeDefl = ESD_DEFLATION, kModeSC = ESD_SUBSPACE
 #ifndef ESD_ROW_UNROLL_F32
 #define ESD_ROW_UNROLL_F32 4
 #endif
+// resident blocks per SM of the FP64 deflated SpMV (double-float W terms)
+#ifndef ESD_DF_MINB
+#define ESD_DF_MINB 2
+#endif
 // resident blocks per SM of the SpMV that also multiplies the power vector
 #ifndef ESD_POW_MINB
 #define ESD_POW_MINB 2
@@ -136,6 +140,151 @@ __device__ __forceinline__ void row_fma2(const SellView<double>& M, const int4& 
 template <int M, typename T>
 __device__ __forceinline__ size_t wix(const IterCtx<T>& c, int k, int i, int s, int lane) {
   return c.wsm ? ((size_t)s * M + k) * kSlice + lane : (size_t)k * c.ld + i;
+}
+
+// ------------------------------------------------------------------ double-float W terms
+// GB300 issues 2 FP64 FMAs per clock per SM and 128 FP32 ones, and its FP64 pipe also carries
+// the FP64 <-> FP32 conversions. The deflation terms (2m FMAs per row) therefore run on the
+// FP32 pipe in double-float arithmetic: a value is an unevaluated sum hi + lo of two floats
+// (about 48 significant bits), sums use Knuth's error-free two-sum and products Dekker's
+// splitting via FMA (TAOCP vol. 2, 4.2.2; Dekker, Numer. Math. 18, 1971). Doubles are split
+// with integer operations only, relative to a power-of-two reference, so every float stays
+// far inside its exponent range; parts more than 2^-100 below the reference are dropped,
+// which is below FP64's own rounding of the same sums.
+
+__device__ __forceinline__ int dexp(double v) {  // biased binary exponent of a double
+  return (int)((__double_as_longlong(v) >> 52) & 0x7ff);
+}
+
+// 2^(e - 1023) as a double (e in 1 .. 2046)
+__device__ __forceinline__ double dpow2(int e) { return __longlong_as_double((long long)e << 52); }
+
+// v 2^(1023 - eref) = hi + lo (truncated to 24 + 24 bits); eref >= dexp(v).
+__device__ __forceinline__ void df_split(double v, int eref, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7ff);
+  const int d = e - eref;  // exponent of the scaled value, <= 0
+  if (e == 0 || d < -100) {
+    hi = 0.f;
+    lo = 0.f;
+    return;
+  }
+  const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+  const unsigned long long m = b & 0xfffffffffffffull;  // 52 fraction bits
+  hi = __uint_as_float(sgn | ((unsigned)(d + 127) << 23) | (unsigned)(m >> 29));
+  const unsigned r = (unsigned)(m & 0x1fffffffu);  // the 29 bits below hi, unit 2^(d - 52)
+  const int t = 31 - __clz(r | 1u);                 // position of the leading bit of r
+  const int fe = t + d + 75;                        // biased float exponent of lo
+  if (r == 0 || fe < 1) {
+    lo = 0.f;
+    return;
+  }
+  const unsigned mn = (t >= 23) ? (r >> (t - 23)) : (r << (23 - t));
+  lo = __uint_as_float(sgn | ((unsigned)fe << 23) | (mn & 0x7fffffu));
+}
+
+// (sh, sl) += (ah + al)(bh + bl), the product's al*bl term (2^-48 relative) left out
+__device__ __forceinline__ void df_fma(float ah, float al, float bh, float bl, float& sh, float& sl) {
+  const float ph = __fmul_rn(ah, bh);
+  float pe = __fmaf_rn(ah, bh, -ph);  // exact error of ph
+  pe = __fmaf_rn(ah, bl, pe);
+  pe = __fmaf_rn(al, bh, pe);
+  const float s = __fadd_rn(sh, ph);  // two-sum of sh and ph
+  const float bb = __fsub_rn(s, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(ph, bb));
+  const float t = __fadd_rn(sl, __fadd_rn(err, pe));
+  sh = __fadd_rn(s, t);  // renormalise: |sl| <= ulp(sh)
+  sl = __fsub_rn(t, __fsub_rn(sh, s));
+}
+
+// 2^k as a float for k in -126 .. 0, else 0
+__device__ __forceinline__ float fpow2_neg(int k) { return k < -126 ? 0.f : __uint_as_float((unsigned)(127 + k) << 23); }
+
+// f 2^(eunit - 1023) as a double, widened with integer operations (exact) when the result is
+// a normal double; zeros stay zero, other cases take the FP64 multiply
+__device__ __forceinline__ double f2d_pow2(float f, int eunit) {
+  const unsigned u = __float_as_uint(f);
+  const int fe = (int)((u >> 23) & 0xffu);
+  const int de = fe - 127 + eunit;
+  if ((u & 0x7fffffffu) == 0u) return 0.0;
+  if (fe == 0 || fe == 255 || de <= 0 || de >= 2047 || eunit < 1 || eunit > 2046) return (double)f * dpow2(eunit < 1 ? 1 : (eunit > 2046 ? 2046 : eunit));
+  const unsigned long long b = ((unsigned long long)(u >> 31) << 63) | ((unsigned long long)de << 52) |
+                               ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)b);
+}
+
+// Asynchronous 16-byte global -> shared copies (completion by wait_group, no polling).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+extern __shared__ __align__(16) unsigned char esd_dyn_smem[];
+
+// Dynamic shared memory of the FP64 deflated SpMV: one slice block of AW (M x 32 float2) per warp.
+template <int M>
+__host__ __device__ constexpr int df_stage_bytes() {
+  return M <= 32 ? (kBlock / 32) * M * kSlice * (int)sizeof(float2) : 0;
+}
+
+// (ah, al) += (bh, bl)
+__device__ __forceinline__ void df_add(float& ah, float& al, float bh, float bl) {
+  const float s = __fadd_rn(ah, bh);
+  const float bb = __fsub_rn(s, ah);
+  const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+  const float t = __fadd_rn(__fadd_rn(al, bl), err);
+  ah = __fadd_rn(s, t);
+  al = __fsub_rn(t, __fsub_rn(ah, s));
+}
+
+// Warp sums of P double-float values per lane, by the halving butterfly of warp_sum_multi:
+// on return lane l holds (in h[0], l[0]) the total of value warp_sum_index<P>(l).
+template <int P>
+__device__ __forceinline__ void df_warp_sum_multi(float (&h)[P], float (&l)[P]) {
+  static_assert((P & (P - 1)) == 0 && P <= 32, "P must be a power of two <= 32");
+  const int lane = lane_id();
+  int half = P / 2;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    if (half >= 1) {
+      const bool upper = (lane & o) != 0;
+#pragma unroll
+      for (int k = 0; k < (P / 2 > 0 ? P / 2 : 1); ++k) {
+        if (k < half) {
+          const float sh = upper ? h[k] : h[k + half], sl = upper ? l[k] : l[k + half];
+          float kh = upper ? h[k + half] : h[k], kl = upper ? l[k + half] : l[k];
+          df_add(kh, kl, __shfl_xor_sync(0xffffffffu, sh, o), __shfl_xor_sync(0xffffffffu, sl, o));
+          h[k] = kh;
+          l[k] = kl;
+        }
+      }
+      half >>= 1;
+    } else {
+      df_add(h[0], l[0], __shfl_xor_sync(0xffffffffu, h[0], o), __shfl_xor_sync(0xffffffffu, l[0], o));
+    }
+  }
+}
+
+// Warp totals of the double-float values [C0, M) in power-of-two chunks, converted to double
+// times unit and written by one lane per value into red[warp * R + off + j].
+template <int C0, int M, int R>
+__device__ __forceinline__ void df_warp_sum_chunks(const float (&h)[M], const float (&l)[M], double unit, double* red,
+                                                   int off, int lane, int warp) {
+  if constexpr (C0 < M) {
+    constexpr int C = pow2_floor(M - C0);
+    float vh[C], vl[C];
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+      vh[k] = h[C0 + k];
+      vl[k] = l[C0 + k];
+    }
+    df_warp_sum_multi<C>(vh, vl);
+    const int idx = warp_sum_index<C>(lane);
+    if ((lane & ((32 / C) - 1)) == 0) red[warp * R + off + C0 + idx] = ((double)vh[0] + (double)vl[0]) * unit;
+    df_warp_sum_chunks<C0 + C, M, R>(h, l, unit, red, off, lane, warp);
+  }
 }
 
 __device__ __forceinline__ void end_loop(unsigned long long cond) {
@@ -234,6 +383,39 @@ inline void launch_pdl(void (*kernel)(KArgs...), int blocks, cudaStream_t s, Arg
   ESD_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
 }
 
+// Blocks of one wave for a kernel with dynamic shared memory (the limit raised once).
+inline int wave_blocks_smem(const void* kernel, int smem) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(kernel);
+  if (it != cache.end()) return it->second;
+  ESD_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  int per_sm = 0;
+  ESD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, smem));
+  const int w = std::max(1, std::min(per_sm, 4)) * (max_grid_blocks() / 4);
+  cache[kernel] = w;
+  return w;
+}
+
+// launch_pdl with dynamic shared memory
+template <typename... KArgs, typename... Args>
+inline void launch_pdl_smem(void (*kernel)(KArgs...), int slices, int smem, cudaStream_t s, Args&&... args) {
+  const int need = (slices * kSlice + kBlock - 1) / kBlock;
+  const int blocks = std::max(1, std::min(need, wave_blocks_smem((const void*)kernel, smem)));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(kBlock);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  ESD_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+}
+
 // Forward launches whose y_i^2 block totals the last forward launch adds up.
 struct RhoSlots {
   int n;
@@ -301,9 +483,12 @@ constexpr int defl_minb() {
 // POW (FP64, M = 0): the same matrix pass also forms w' = A v = scale * (A w) of the power
 // vector, with ||w'||^2 (Algorithm PCG-con's (q v) = A (p v)).
 template <typename T, int M, bool POW = false>
-__global__ void __launch_bounds__(kBlock, POW ? ESD_POW_MINB : defl_minb<T, M>()) k_spmv_pq(IterCtx<T> c, SliceSet set) {
+__global__ void __launch_bounds__(kBlock, POW ? ESD_POW_MINB
+                                             : ((sizeof(T) == 8 && df_cols(M)) ? (M <= 16 ? ESD_DF_MINB : 1) : defl_minb<T, M>()))
+    k_spmv_pq(IterCtx<T> c, SliceSet set) {
   static_assert(!POW || (M == 0 && sizeof(T) == 8), "the power method runs in the FP64 M = 0 product");
   constexpr int R = 1 + M + (POW ? 1 : 0);
+  constexpr bool DF = sizeof(T) == 8 && df_cols(M);  // h = (AW)^T p in double-float
   __shared__ T red[red_size<R>()];
   __shared__ double hy_s;
   pdl_enter();
@@ -330,14 +515,48 @@ __global__ void __launch_bounds__(kBlock, POW ? ESD_POW_MINB : defl_minb<T, M>()
   T acc[R];
 #pragma unroll
   for (int k = 0; k < R; ++k) acc[k] = T(0);
+  // double-float partial sums of h in units of 2^(et - 1023), et the largest exponent of p
+  // this warp has met (0: none yet)
+  float dh[DF ? M : 1], dl[DF ? M : 1];
+  int et = 0;
+#pragma unroll
+  for (int k = 0; k < (DF ? M : 1); ++k) dh[k] = dl[k] = 0.f;
+  constexpr bool STAGE = DF && df_stage_bytes<M>() > 0;  // AW slice blocks via cp.async
+  float2* aw_s = reinterpret_cast<float2*>(esd_dyn_smem) + (size_t)(threadIdx.x >> 5) * M * kSlice;
   ESD_LOOP_SLICES(set) {
     int r;
     const int s = set.slice(g, &r);
+    if constexpr (STAGE) {
+      // this slice's AW block (contiguous M x 256 bytes) lands in shared memory while the
+      // matrix product below waits on its own loads
+      __syncwarp();  // every lane is done with the previous block
+      const char* src = reinterpret_cast<const char*>(c.AWdf + (size_t)s * M * kSlice);
+      char* dst = reinterpret_cast<char*>(aw_s);
+#pragma unroll
+      for (int j = lane; j < M * kSlice * (int)sizeof(float2) / 16; j += 32) cp_async16(dst + 16 * j, src + 16 * j);
+      cp_async_commit();
+    }
     const int4 md = c.Av.meta[s];
     const int i = md.z + lane;
     const bool valid = lane < md.w;
     T qi;
     double wi = 0.0;
+    float ph = 0.f, pl = 0.f;
+    if constexpr (DF) {
+      // one reference exponent per warp, so the warp can add its partial sums in double-float
+      const double pv = valid ? (double)c.p[i] : 0.0;
+      const int ew = (int)__reduce_max_sync(0xffffffffu, (unsigned)dexp(pv));
+      if (ew > et) {  // a larger p: bring the partial sums to the new unit (exact)
+        const float f = fpow2_neg(et - ew);
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          dh[k] = __fmul_rn(dh[k], f);
+          dl[k] = __fmul_rn(dl[k], f);
+        }
+        et = ew;
+      }
+      df_split(pv, et, ph, pl);
+    }
     if constexpr (POW) {
       row_fma2(c.Av, md, lane, c.p, w_in, qi, wi);
     } else if (sizeof(T) == 4 && c.rowsum) {
@@ -346,12 +565,25 @@ __global__ void __launch_bounds__(kBlock, POW ? ESD_POW_MINB : defl_minb<T, M>()
     } else {
       qi = row_fma(c.Av, md, lane, c.p, T(0));
     }
+    if constexpr (STAGE) {
+      cp_async_wait_all();  // this lane's copies
+      __syncwarp();         // and the other lanes' copies, visible to the warp
+    }
     if (valid) {
       const T pi = c.p[i];
       c.q[i] = qi;
       acc[0] = fma(pi, qi, acc[0]);
+      if constexpr (DF) {
+        const float2* ap = (STAGE ? aw_s : c.AWdf + (size_t)s * M * kSlice) + lane;
 #pragma unroll
-      for (int k = 0; k < M; ++k) acc[1 + k] = fma(c.AW[wix<M>(c, k, i, s, lane)], pi, acc[1 + k]);
+        for (int k = 0; k < M; ++k) {
+          const float2 a = ap[k * kSlice];
+          df_fma(a.x, a.y, ph, pl, dh[k], dl[k]);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < M; ++k) acc[1 + k] = fma(c.AW[wix<M>(c, k, i, s, lane)], pi, acc[1 + k]);
+      }
       if constexpr (POW) {
         const double wv = wi * w_scale;  // A v with v = scale * w
         w_out[i] = wv;
@@ -359,7 +591,20 @@ __global__ void __launch_bounds__(kBlock, POW ? ESD_POW_MINB : defl_minb<T, M>()
       }
     }
   }
-  if (grid_sum_multi<R>(acc, red, (T*)c.partials, &st->ticket[kTkSpmv])) {
+  bool last;
+  if constexpr (DF) {
+    // warp totals: (p, q) in FP64, h in double-float converted once per warp
+    const int w = threadIdx.x >> 5;
+    double v = acc[0];
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane_id() == 0) red[w * R] = v;
+    df_warp_sum_chunks<0, M, R>(dh, dl, et > 0 ? dpow2(et) : 0.0, (double*)red, 1, lane_id(), w);
+    last = grid_sum_from_warps<R>(red, (T*)c.partials, &st->ticket[kTkSpmv]);
+  } else {
+    last = grid_sum_multi<R>(acc, red, (T*)c.partials, &st->ticket[kTkSpmv]);
+  }
+  if (last) {
     if constexpr (POW) {
       if (threadIdx.x == 0) {
         const double ww = red[R - 1];
@@ -375,6 +620,10 @@ __global__ void __launch_bounds__(kBlock, POW ? ESD_POW_MINB : defl_minb<T, M>()
     }
     if (M > 0) {
       if (threadIdx.x < 32) {
+        if constexpr (DF) {  // the double-float sums hold (AW 2^-e_k)^T p
+          for (int k = threadIdx.x; k < M; k += 32) red[1 + k] *= c.awscale[k];
+          __syncwarp();
+        }
         double part = 0.0;
         for (int i = threadIdx.x; i < M; i += 32) {
           double y = 0.0;
@@ -384,6 +633,20 @@ __global__ void __launch_bounds__(kBlock, POW ? ESD_POW_MINB : defl_minb<T, M>()
         }
         for (int o = 16; o >= 1; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
         if (threadIdx.x == 0) hy_s = part;
+        if constexpr (DF) {
+          // y_k 2^e_k as double-float pairs for the update, relative to their largest exponent
+          __syncwarp();
+          int e = 0;
+          for (int k = threadIdx.x; k < M; k += 32) e = max(e, dexp(st->y[k] * c.awscale[k]));
+          e = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
+          if (e == 0) e = 1023;
+          for (int k = threadIdx.x; k < M; k += 32) {
+            float h, l;
+            df_split(st->y[k] * c.awscale[k], e, h, l);
+            st->ydf[k] = make_float2(h, l);
+          }
+          if (threadIdx.x == 0) st->ydf_exp = e;
+        }
       }
       __syncthreads();
     }
@@ -417,8 +680,11 @@ __global__ void __launch_bounds__(kBlock, M == 0 ? 4 : defl_minb<T, M>()) k_upda
   constexpr int SCM = (MODE == kModeSC) ? M : 0;
   constexpr int DM = (MODE == kModeDefl) ? M : 0;
   constexpr int R = 2 + SCM;
+  constexpr bool DF = sizeof(T) == 8 && df_cols(DM);  // AW y in double-float
   __shared__ T red[red_size<R>()];
   __shared__ T ys[DM > 0 ? DM : 1];  // y in the kernel's type: converted once per block
+  __shared__ float2 ys2[DF ? DM : 1];
+  __shared__ int yexp;
   __shared__ double fu_s;
   pdl_enter();
   State* st = c.st;
@@ -427,7 +693,12 @@ __global__ void __launch_bounds__(kBlock, M == 0 ? 4 : defl_minb<T, M>()) k_upda
   const double alpha_d = st->alpha;
   const int pend = do_update ? st->pend_slot : -1;
   if (DM > 0) {
-    for (int k = threadIdx.x; k < DM; k += blockDim.x) ys[k] = (T)st->y[k];
+    if constexpr (DF) {
+      for (int k = threadIdx.x; k < DM; k += blockDim.x) ys2[k] = st->ydf[k];
+      if (threadIdx.x == 0) yexp = st->ydf_exp;
+    } else {
+      for (int k = threadIdx.x; k < DM; k += blockDim.x) ys[k] = (T)st->y[k];
+    }
     __syncthreads();
   }
   T acc[R];
@@ -456,8 +727,20 @@ __global__ void __launch_bounds__(kBlock, M == 0 ? 4 : defl_minb<T, M>()) k_upda
           c.x[i] = fma(alpha, c.p[i], xi);
         }
         T t = c.q[i];
+        if constexpr (DF) {
+          float th = 0.f, tl = 0.f;
+          const float2* ap = c.AWdf + (size_t)s * DM * kSlice + lane;
 #pragma unroll
-        for (int k = 0; k < DM; ++k) t = fma(-c.AW[wix<DM>(c, k, i, s, lane)], ys[k], t);
+          for (int k = 0; k < DM; ++k) {
+            const float2 a = ap[k * kSlice];
+            const float2 yk = ys2[k];
+            df_fma(a.x, a.y, yk.x, yk.y, th, tl);
+          }
+          t -= f2d_pow2(th, yexp) + f2d_pow2(tl, yexp);
+        } else {
+#pragma unroll
+          for (int k = 0; k < DM; ++k) t = fma(-c.AW[wix<DM>(c, k, i, s, lane)], ys[k], t);
+        }
         ri = fma(-alpha, t, c.r[i]);
         c.r[i] = ri;
         acc[0] = fma(ri, ri, acc[0]);
@@ -939,6 +1222,11 @@ void launch_iteration(const IterCtx<T>& c, cudaStream_t s, KernelMarks* marks) {
     } else {
       throw Error(ESD_ERR_STATE, "the power method runs in FP64 solves");
     }
+  } else if (sizeof(T) == 8 && df_cols(Mm)) {  // double-float deflation terms, AW staged in shared memory
+    ESD_DISPATCH_MPOS(Mm, {
+      auto k = k_spmv_pq<T, MM>;
+      launch_pdl_smem(k, all.total(), df_stage_bytes<MM>(), s, c, all);
+    });
   } else {
     ESD_DISPATCH_M(Mm, { auto k = k_spmv_pq<T, MM>; ESD_LAUNCH(k, all.total(), s, c, all); });
   }

@@ -9,6 +9,10 @@
 
 namespace esd {
 
+// FP64 deflation with double-float W terms for up to this many (padded) columns; beyond, the
+// 2M float accumulators of the SpMV no longer fit in registers and the terms stay FP64
+__host__ __device__ constexpr bool df_cols(int M) { return M > 0 && M <= 32; }
+
 template <typename T>
 struct IterCtx {
   const esd_matrix* A = nullptr;
@@ -42,6 +46,10 @@ struct IterCtx {
   int pre = ESD_PRECOND_IC0;
   int x_zero = 0;  // the start vector is known to be zero (r0 = b without a product)
   int wsm = 0;     // W and AW slice-major: entry (row of slice s, lane l; column k) at (s M + k) 32 + l
+  // FP64 deflation: AW as double-float pairs, slice-major ((s M + k) 32 + lane), column k
+  // scaled by 2^-e_k so that its largest entry lies in [1/2, 1); awscale[k] = 2^e_k
+  const float2* AWdf = nullptr;
+  const double* awscale = nullptr;
   // power method (FP64 plain / SC solves): w in pw[steps & 1], the next product into the other
   double* pw[2] = {nullptr, nullptr};
   PowerState* pws = nullptr;
@@ -75,6 +83,10 @@ void launch_true_residual(const IterCtx<double>& c, cudaStream_t s);
 // set_scale also scale = 1/||w|| and steps = 0 (w is a new start vector).
 void launch_power_rq(const esd_matrix* A, double* const pw[2], PowerState* pws, double* partials, int set_scale,
                      cudaStream_t s);
+// AWdf (nslices x 32 x M float2) and awscale (M doubles) from AW (n x m, column-major); cexp:
+// kMaxM ints of scratch
+void launch_aw_df(const esd_matrix* A, const double* AW, size_t ld, int m, int M, float2* out, double* awscale,
+                  int* cexp, cudaStream_t s);
 // unit = w / ||w||, with ||w||^2 from the last launch_power_rq
 void launch_power_unit(const esd_matrix* A, const double* w, const PowerState* pws, double* unit, cudaStream_t s);
 // y = A X for an n x m block (column-major, stride ld), m columns

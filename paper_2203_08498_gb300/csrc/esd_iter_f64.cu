@@ -94,6 +94,50 @@ void launch_power_unit(const esd_matrix* A, const double* w, const PowerState* p
   ESD_CUDA(cudaGetLastError());
 }
 
+// Largest binary exponent of each column of AW (n x m, column-major, stride ld).
+__global__ void k_aw_colexp(int n, const double* AW, size_t ld, int* cexp) {
+  const int k = blockIdx.y;
+  int e = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    e = max(e, dexp(AW[(size_t)k * ld + i]));
+  e = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
+  if ((threadIdx.x & 31) == 0 && e > 0) atomicMax(&cexp[k], e);
+}
+
+// AW 2^-e_k as double-float pairs in slice-major order; awscale[k] = 2^e_k (1 for a zero or
+// padding column)
+__global__ void k_aw_df(int n, const int* rowpos, const double* AW, size_t ld, int m, int M, const int* cexp,
+                        float2* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int pos = rowpos[i];
+    const size_t base = (size_t)(pos >> 5) * M * kSlice + (pos & 31);
+    for (int k = 0; k < m; ++k) {
+      float h, l;
+      df_split(AW[(size_t)k * ld + i], cexp[k], h, l);
+      out[base + (size_t)k * kSlice] = make_float2(h, l);
+    }
+  }
+}
+
+__global__ void k_aw_scale(int M, const int* cexp, double* awscale) {
+  for (int k = threadIdx.x; k < M; k += blockDim.x) awscale[k] = dpow2(cexp[k] > 0 ? cexp[k] : 1023);
+}
+
+void launch_aw_df(const esd_matrix* A, const double* AW, size_t ld, int m, int M, float2* out, double* awscale,
+                  int* cexp, cudaStream_t s) {
+  ESD_CUDA(cudaMemsetAsync(cexp, 0, sizeof(int) * kMaxM, s));
+  ESD_CUDA(cudaMemsetAsync(out, 0, sizeof(float2) * (size_t)A->nslices * kSlice * M, s));
+  if (m > 0) {
+    k_aw_colexp<<<dim3(std::min((A->n + 255) / 256, 2 * max_grid_blocks()), m), 256, 0, s>>>(A->n, AW, ld, cexp);
+    ESD_CUDA(cudaGetLastError());
+    k_aw_df<<<std::min((A->n + 255) / 256, 4 * max_grid_blocks()), 256, 0, s>>>(A->n, A->rowpos.as<int>(), AW, ld, m,
+                                                                               M, cexp, out);
+    ESD_CUDA(cudaGetLastError());
+  }
+  k_aw_scale<<<1, 64, 0, s>>>(M, cexp, awscale);
+  ESD_CUDA(cudaGetLastError());
+}
+
 void launch_true_residual(const IterCtx<double>& c, cudaStream_t s) {
   auto k = k_true_res<double>;
   ESD_LAUNCH(k, c.A->all.total(), s, c, c.A->all);

@@ -62,6 +62,7 @@ struct esd_solver {
   size_t ld = 0;
   DevBuf vb, vx, vr, vp, vq, vY, samples;
   DevBuf W, AW, E, Einv, ritz, ahist, bhist, state, partials, rho_part, ext, lz;
+  DevBuf AWdf, awscale, awexp;  // AW as double-float pairs for the FP64 deflated iteration
   State* hst = nullptr;  // pinned host copy
   // FP32-inner / FP64-refinement form
   bool fp32 = false;
@@ -154,6 +155,8 @@ struct esd_solver {
       c.AW = AW.as<double>();
       c.Einv = Einv.as<double>();
       c.M = M;
+      c.AWdf = AWdf.as<float2>();
+      c.awscale = awscale.as<double>();
     }
     c.samples = samples.get() ? samples.as<double>() : nullptr;
     c.ahist = ahist.as<double>();
@@ -569,6 +572,17 @@ static void install_W(esd_solver* S, const double* X, int m, bool orth, double t
     build_aux(S->A, S->aux, S->aux.work1.as<double>(), mkeep, false, S->prm.rank_tol,
               std::numeric_limits<double>::infinity(), S->W.as<double>(), S->AW.as<double>(),
               S->E.as<double>(), S->Einv.as<double>(), S->ritz.as<double>(), &unused, S->stream);
+  }
+  if (df_cols(pad_cols(mkeep))) {
+    const int Mp = pad_cols(mkeep);
+    const size_t need = sizeof(float2) * (size_t)S->A->nslices * kSlice * Mp;
+    if (S->AWdf.bytes() < need) S->AWdf.alloc(need);
+    if (!S->awscale.get()) {
+      S->awscale.alloc(sizeof(double) * kMaxM);
+      S->awexp.alloc(sizeof(int) * kMaxM);
+    }
+    launch_aw_df(S->A, S->AW.as<double>(), ld, mkeep, Mp, S->AWdf.as<float2>(), S->awscale.as<double>(),
+                 S->awexp.as<int>(), S->stream);
   }
   ESD_CUDA(cudaStreamSynchronize(S->stream));
   S->m = mkeep;
