@@ -319,6 +319,59 @@ def test_diag_scaling_rejects_nonpositive_diagonal():
         oracle.diag_scale(bad)
 
 
+# ---------------------------------------------------------------- other IC orderings
+
+def test_wavefront_ic0_is_natural_order_ic0():
+    """Rows on one wavefront x+y+z are uncoupled and every earlier neighbour of a row lies on
+    an earlier wavefront, so IC(0) in wavefront order is natural-order IC(0) up to the
+    symmetric permutation: M^-1 r agrees mapped to natural order, and ICCG takes the same
+    iterations to the same solution. (The natural order gives every cell its own colour, so
+    the oracle's sweeps take the rows one by one.)"""
+    p = wl.small_3d(7, seed=5)
+    pn = wl.reorder(p, np.arange(p.n))
+    pw = wl.reorder(p, wl.wavefront_colours(p.shape))
+    assert pw.ncolours == 3 * 7 - 2
+    r = np.random.default_rng(8).standard_normal(p.n)  # natural order
+    zn = oracle.IC0(pn).apply(r[pn.perm])
+    zw = oracle.IC0(pw).apply(r[pw.perm])
+    z_nat_n, z_nat_w = np.empty(p.n), np.empty(p.n)
+    z_nat_n[pn.perm], z_nat_w[pw.perm] = zn, zw
+    np.testing.assert_allclose(z_nat_w, z_nat_n, rtol=1e-12, atol=1e-14 * np.abs(z_nat_n).max())
+    on = oracle.System(pn, oracle.IC0(pn)).solve(pn.source, tol=1e-10)
+    ow = oracle.System(pw, oracle.IC0(pw)).solve(pw.source, tol=1e-10)
+    assert on["iters"] == ow["iters"]
+    xn, xw = np.empty(p.n), np.empty(p.n)
+    xn[pn.perm], xw[pw.perm] = on["x"], ow["x"]
+    np.testing.assert_allclose(xw, xn, rtol=1e-12, atol=1e-12 * np.abs(xn).max())
+    # and multicolour IC(0) is a different (weaker) preconditioner on this problem
+    om = oracle.System(p, oracle.IC0(p)).solve(p.source, tol=1e-10)
+    assert om["iters"] > on["iters"]
+
+
+def test_block_jacobi_ic0_factors_each_block_alone():
+    """Block-Jacobi IC (one IC(0) per block, couplings between blocks dropped): M^-1 r on each
+    block equals the IC(0) solve of that block's submatrix by itself, and the blocks share
+    no entry of the factor."""
+    p = wl.small_3d(8, seed=6)
+    b = 4
+    bid = wl.block_ids(p.shape, b)
+    pb = wl.reorder(p, wl.block_wavefront_colours(p.shape, b))
+    P = wl.block_diagonal_part(pb, bid)
+    assert P.nnz < pb.nnz
+    ic = oracle.IC0(P)
+    L = ic.dense_L()
+    brow = bid[pb.perm]
+    assert np.all(L[brow[:, None] != brow[None, :]] == 0)
+    r = np.random.default_rng(9).standard_normal(p.n)
+    z = ic.apply(r)
+    Pd = P.scipy().toarray()
+    for blk in np.unique(brow):
+        rows = np.flatnonzero(brow == blk)
+        sub = wl.csr_of_dense(Pd[np.ix_(rows, rows)], ncolours=len(rows))  # one row per colour
+        zs = oracle.IC0(sub).apply(r[rows])
+        np.testing.assert_allclose(z[rows], zs, rtol=1e-12, atol=1e-14 * np.abs(zs).max())
+
+
 # ---------------------------------------------------------------- power method (Section 5.4)
 
 @pytest.mark.parametrize("k", [0, 1, 2, 5, 30])

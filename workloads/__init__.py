@@ -30,7 +30,8 @@ __all__ = [
     "Problem", "fv_diffusion", "square_inclusions", "sphere_inclusions",
     "gaussian_source", "smooth_gaussian_field", "config_c1", "config_c2", "config_c4",
     "small_3d", "random_spd_dense", "laplacian_1d", "laplacian_2d", "csr_of_dense",
-    "random_rhs", "SEED_BASE",
+    "random_rhs", "SEED_BASE", "reorder", "wavefront_colours", "block_ids", "block_wavefront_colours",
+    "block_diagonal_part",
 ]
 
 SEED_BASE = 20220316
@@ -146,6 +147,65 @@ def fv_diffusion(coef: np.ndarray, h: float, dt: float, name: str = "") -> Probl
     return Problem(n=n, rowptr=A.indptr.astype(np.int32), colind=A.indices.astype(np.int32),
                    val=A.data.astype(np.float64), colour_ptr=colour_ptr, perm=perm, dt=dt,
                    shape=tuple(shape), h=h, coef=coef, name=name)
+
+
+def reorder(prob: Problem, colour_nat: np.ndarray, name: str = "") -> Problem:
+    """The same operator (and source, coefficients) in another multicolour ordering:
+    ``colour_nat[k]`` is the colour of natural cell k; rows are colour-major with natural
+    order inside a colour. A colour whose rows are coupled is allowed here (a single colour
+    is the natural order); the library's own check rejects it."""
+    colour_nat = np.asarray(colour_nat, dtype=np.int64).ravel()
+    inv = np.empty(prob.n, dtype=np.int64)
+    inv[prob.perm] = np.arange(prob.n)
+    perm2 = np.argsort(colour_nat, kind="stable").astype(np.int64)  # new -> natural
+    q = inv[perm2]                                                   # new -> old row
+    A = prob.scipy()[q][:, q].tocsr()
+    A.sort_indices()
+    ncol = int(colour_nat.max()) + 1
+    cp = np.concatenate([[0], np.cumsum(np.bincount(colour_nat, minlength=ncol))]).astype(np.int32)
+    out = dataclasses.replace(prob, rowptr=A.indptr.astype(np.int32), colind=A.indices.astype(np.int32),
+                              val=A.data.astype(np.float64), colour_ptr=cp, perm=perm2,
+                              name=name or prob.name)
+    if prob.source is not None:
+        out.source = np.ascontiguousarray(prob.source[q])
+    return out
+
+
+def wavefront_colours(shape) -> np.ndarray:
+    """Colour x + y (+ z) per natural cell: the wavefronts of natural-order IC(0) on a 5/7-point
+    stencil (a row's earlier neighbours all lie on the previous wavefront)."""
+    return np.indices(shape).sum(axis=0).ravel(order="F")
+
+
+def block_ids(shape, b: int) -> np.ndarray:
+    """Index of the b^d block holding each natural cell (blocks in natural order)."""
+    idx = np.indices(shape)
+    nb = [-(-s // b) for s in shape]
+    bid = np.zeros(shape, dtype=np.int64)
+    stride = 1
+    for ax in range(len(shape)):
+        bid += (idx[ax] // b) * stride
+        stride *= nb[ax]
+    return bid.ravel(order="F")
+
+
+def block_wavefront_colours(shape, b: int) -> np.ndarray:
+    """Wavefronts inside b^d blocks (local x + y + z): with the couplings between blocks
+    dropped from the preconditioner, IC(0) of each block in natural order (the paper's
+    block-Jacobi IC, one block per thread), all blocks advancing together."""
+    return (np.indices(shape) % b).sum(axis=0).ravel(order="F")
+
+
+def block_diagonal_part(prob: Problem, block_nat: np.ndarray) -> Problem:
+    """The block-diagonal part of ``prob``'s matrix: entries coupling cells of different blocks
+    (``block_nat`` per natural cell) dropped; same ordering."""
+    blk = np.asarray(block_nat)[prob.perm]
+    A = prob.scipy().tocoo()
+    keep = blk[A.row] == blk[A.col]
+    B = sp.csr_matrix((A.data[keep], (A.row[keep], A.col[keep])), shape=A.shape)
+    B.sort_indices()
+    return dataclasses.replace(prob, rowptr=B.indptr.astype(np.int32), colind=B.indices.astype(np.int32),
+                               val=B.data.astype(np.float64), name=prob.name + "_blockdiag")
 
 
 def square_inclusions(N: int, count: int, size: int, value: float, rng) -> np.ndarray:
