@@ -270,6 +270,18 @@ int esd_sample_and_build_W(esd_solver* S, double theta, int32_t* m_kept);
 int esd_set_W(esd_solver* S, const double* W, int32_t m);
 
 /*
+ * Precondition with the IC(0) factor of P instead of A's own: M = L_P L_P^T. P holds the same
+ * rows in the same colour-major order as A (same n and colour_ptr, so the same 32-row
+ * slices) and is factored (esd_factor_ic0). Its own couplings set the colour levels of the
+ * substitutions. The paper's parallel solver uses block-Jacobi IC (Section 5.3): P is the
+ * block-diagonal part of A, and colours that are coupled only across blocks share a launch.
+ * The products with A (SpMV, residuals, W) still use A. P must stay alive and factored
+ * while the solver uses it; NULL returns to A's factor.
+ * Errors: ESD_ERR_INVALID for other rows or colours, ESD_ERR_STATE for an unfactored P.
+ */
+int esd_solver_set_precond_matrix(esd_solver* S, esd_matrix* P);
+
+/*
  * Switch an existing solver between ESD_FP64 and ESD_FP32_REFINE (the precision of
  * esd_params) and set the inner tolerance of the refinement form (0 < inner_tol < 1; ignored
  * for ESD_FP64). The first switch to the refinement form allocates its buffers and the FP32

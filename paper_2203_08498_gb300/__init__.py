@@ -30,7 +30,7 @@ __all__ = [
     "esd_get_samples", "esd_backward_euler_rhs", "esd_profile_iterations", "esd_last_error",
     "esd_lanczos_extremes_noalloc", "NOALLOC_MAX_K", "esd_matrix_set_values", "esd_fv_assemble",
     "esd_fv_grad_theta", "esd_refresh_W", "EsdFvGrid", "esd_power_start", "esd_power_estimate",
-    "esd_matrix_diag_scale", "MATRIX_DIAG_SCALE", "esd_set_precision",
+    "esd_matrix_diag_scale", "MATRIX_DIAG_SCALE", "esd_set_precision", "esd_solver_set_precond_matrix",
 ]
 MATRIX_DIAG_SCALE = 1
 NOALLOC_MAX_K = 32768
@@ -119,6 +119,7 @@ def lib(build_if_missing: bool = True):
             "esd_power_start": (i32, [vp, vp]),
             "esd_matrix_diag_scale": (i32, [vp, vp]),
             "esd_set_precision": (i32, [vp, i32, f64]),
+            "esd_solver_set_precond_matrix": (i32, [vp, vp]),
             "esd_power_estimate": (i32, [vp, P(f64), P(i32), vp]),
         }
         for name, (res, args) in sig.items():
@@ -327,6 +328,10 @@ def esd_estimate_cond(h):
     return lo.value, hi.value, k.value, r.value
 
 
+def esd_solver_set_precond_matrix(h, P):
+    _check(lib().esd_solver_set_precond_matrix(h, P))
+
+
 def esd_set_precision(h, precision, inner_tol=0.1):
     _check(lib().esd_set_precision(h, precision, inner_tol))
 
@@ -462,6 +467,12 @@ class Solver:
 
     def set_precision(self, precision, inner_tol=0.1):
         esd_set_precision(self._h, precision, inner_tol)
+
+    def set_precond_matrix(self, P):
+        """Precondition with IC(0) of another Matrix P (same rows and colours as A), e.g. the
+        block-diagonal part of A for block-Jacobi IC; None returns to A's own factor."""
+        esd_solver_set_precond_matrix(self._h, None if P is None else P.handle)
+        self._precond_matrix = P  # keep it alive while the solver uses it
 
     def solve(self, b, x, tol=1e-8, maxit=None, sample_m=0):
         return esd_solve(self._h, b, x, tol, maxit or self.maxit_cap, sample_m)

@@ -23,7 +23,7 @@ constexpr int kSlice = 32;      // rows per slice (one warp, one row per lane)
 constexpr int kBlock = 512;     // threads per block of the streaming kernels
 constexpr int kMaxM = 64;       // maximum number of columns of W
 constexpr int kMaxRanges = 16;  // slice ranges one launch may cover
-constexpr int kMaxColours = 64;
+constexpr int kMaxColours = 2048;  // e.g. the 3N-2 wavefronts of natural-order IC(0) on N^3
 
 // A set of slice ranges processed by one launch (the colours of one level).
 struct SliceSet {

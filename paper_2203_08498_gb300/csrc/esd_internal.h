@@ -84,6 +84,7 @@ struct esd_matrix {
   std::vector<esd::SliceSet> fwd_all_sets; // all forward levels incl. level 0 (factor, apply)
   std::vector<esd::SliceSet> bwd_all_sets; // all backward levels incl. level 0 (apply)
   std::vector<esd::SliceSet> bwd0_sets;    // colours without later neighbours
+  esd::DevBuf fwd_grid64, fwd_grid32;      // int per forward launch: its grid (FP64 / FP32 kernel)
   esd::Sell A, L, U;  // L and U hold the strict factor entries negated (-l_ij)
   esd::DevBuf slice_flags;   // uint8 per slice: bit0 fwd level 0, bit1 bwd level 0
   esd::DevBuf rowpos;        // int per row: slice*32 + lane

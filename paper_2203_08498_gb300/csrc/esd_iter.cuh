@@ -416,11 +416,6 @@ inline void launch_pdl_smem(void (*kernel)(KArgs...), int slices, int smem, cuda
   ESD_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
 }
 
-// Forward launches whose y_i^2 block totals the last forward launch adds up.
-struct RhoSlots {
-  int n;
-  int G[kMaxColours];
-};
 
 // ------------------------------------------------------------------ plain kernels
 
@@ -815,9 +810,11 @@ __global__ void __launch_bounds__(kBlock, M == 0 ? 4 : defl_minb<T, M>()) k_upda
 
 // One forward colour level: y_i = (r_i - sum_k l_ik y_k) / l_ii and sum y_i^2. A launch that
 // is not the last stores its block totals in rho slot `slot`; the last launch adds its own
-// sum, the slots of the earlier launches and the level-0 part of the update, then sets beta.
+// sum, the slots of the nprev earlier launches (their grids in prevG) and the level-0 part of
+// the update, then sets beta.
 template <typename T>
-__global__ void __launch_bounds__(kBlock, sweep_minb<T>()) k_fwd(IterCtx<T> c, SliceSet set, int slot, RhoSlots prev) {
+__global__ void __launch_bounds__(kBlock, sweep_minb<T>())
+    k_fwd(IterCtx<T> c, SliceSet set, int slot, int nprev, const int* __restrict__ prevG) {
   __shared__ T red[red_size<1>()];
   __shared__ double own_s;
   pdl_enter();
@@ -847,9 +844,10 @@ __global__ void __launch_bounds__(kBlock, sweep_minb<T>()) k_fwd(IterCtx<T> c, S
   if (grid_sum_multi<1>(acc, red, (T*)c.partials, &st->ticket[kTkSweep])) {
     if (threadIdx.x == 0) own_s = (double)red[0];
     T acc2[1] = {T(0)};
-    for (int k = 0; k < prev.n; ++k)
-      for (int b = threadIdx.x; b < prev.G[k]; b += blockDim.x)
-        acc2[0] += __ldcg(&slots[(size_t)k * c.rho_stride + b]);
+    for (int k = 0; k < nprev; ++k) {
+      const int gk = prevG[k];
+      for (int b = threadIdx.x; b < gk; b += blockDim.x) acc2[0] += __ldcg(&slots[(size_t)k * c.rho_stride + b]);
+    }
     block_sum_multi<1>(acc2, red);
     if (threadIdx.x == 0) finalize_rho(st, own_s + (double)red[0] + st->rho_acc + st->fu, c.bhist, c.cond);
   }
@@ -1156,24 +1154,30 @@ static void launch_update(const IterCtx<T>& c, int do_update, int finalize, cuda
 
 // forward levels >= 1 then backward levels (with the direction update)
 template <typename T>
+std::vector<int> fwd_grids(const esd_matrix* P) {
+  std::vector<int> g;
+  auto kf = k_fwd<T>;
+  for (const SliceSet& set : P->fwd_sets) g.push_back(grid_for(kf, set.total()));
+  return g;
+}
+
+template <typename T>
 static void launch_precond(const IterCtx<T>& c, cudaStream_t s, KernelMarks* marks = nullptr) {
-  const esd_matrix* A = c.A;
+  const esd_matrix* A = c.P ? c.P : c.A;  // the preconditioning matrix (same slices as c.A)
   const int SCM = (c.mode == ESD_SUBSPACE_CORRECTION) ? c.M : 0;
   if (c.pre == ESD_PRECOND_NONE) {
     ESD_DISPATCH_M(SCM, { auto k = k_dir<T, MM>; ESD_LAUNCH(k, A->all.total(), s, c, A->all); });
     if (marks) marks->mark(s, "dir");
     return;
   }
-  RhoSlots prev{};
   const size_t nf = A->fwd_sets.size();
+  const int* dG = sizeof(T) == 8 ? A->fwd_grid64.as<int>() : A->fwd_grid32.as<int>();
   auto kf = k_fwd<T>;
   for (size_t l = 0; l < nf; ++l) {
     const SliceSet& set = A->fwd_sets[l];
     const int G = grid_for(kf, set.total());
     const bool last = l + 1 == nf;
-    if (!last && prev.n >= kMaxColours) throw Error(ESD_ERR_INVALID, "too many forward launches");
-    launch_pdl(kf, G, s, c, set, last ? -1 : prev.n, prev);
-    if (!last) prev.G[prev.n++] = G;
+    launch_pdl(kf, G, s, c, set, last ? -1 : (int)l, last ? (int)l : 0, dG);
     if (marks) marks->mark(s, ("fwd_" + std::to_string(l + 1)).c_str());
   }
   SliceSet none{};
@@ -1204,7 +1208,7 @@ void launch_init(const IterCtx<T>& c, cudaStream_t s) {
       ESD_LAUNCH(k, all.total(), s, c, all, (const T*)c.AW, c.r, T(-1), 1);
     });
   }
-  const bool fin = c.pre == ESD_PRECOND_NONE || c.A->fwd_sets.empty();
+  const bool fin = c.pre == ESD_PRECOND_NONE || (c.P ? c.P : c.A)->fwd_sets.empty();
   launch_update<T>(c, 0, fin ? 1 : 0, s);
   launch_precond<T>(c, s);
 }
@@ -1231,7 +1235,7 @@ void launch_iteration(const IterCtx<T>& c, cudaStream_t s, KernelMarks* marks) {
     ESD_DISPATCH_M(Mm, { auto k = k_spmv_pq<T, MM>; ESD_LAUNCH(k, all.total(), s, c, all); });
   }
   if (marks) marks->mark(s, "spmv_pq");
-  const bool fin = c.pre == ESD_PRECOND_NONE || c.A->fwd_sets.empty();
+  const bool fin = c.pre == ESD_PRECOND_NONE || (c.P ? c.P : c.A)->fwd_sets.empty();
   launch_update<T>(c, 1, fin ? 1 : 0, s, marks);
   launch_precond<T>(c, s, marks);
 }
@@ -1269,6 +1273,7 @@ void launch_finish(const IterCtx<T>& c, cudaStream_t s) {
 }
 
 #define ESD_INSTANTIATE_ITER(T)                                                        \
+  template std::vector<int> fwd_grids<T>(const esd_matrix*);                          \
   template void launch_init<T>(const IterCtx<T>&, cudaStream_t);                      \
   template void launch_iteration<T>(const IterCtx<T>&, cudaStream_t, KernelMarks*);   \
   template void launch_finish<T>(const IterCtx<T>&, cudaStream_t);

@@ -39,6 +39,7 @@ struct IterCtx {
   void* partials = nullptr;
   void* rho_part = nullptr;     // block totals of the forward launches before the last one
   size_t rho_stride = 0;        // entries per forward launch in rho_part
+  const esd_matrix* P = nullptr;  // matrix whose IC(0) factor and colour levels precondition (A)
   State* st = nullptr;
   const unsigned char* sflags = nullptr;
   unsigned long long cond = 0;  // graph conditional handle (0 = none)
@@ -71,6 +72,9 @@ struct KernelMarks {
     for (auto e : ev) cudaEventDestroy(e);
   }
 };
+
+// Grid of each forward launch of P's substitution (k_fwd<T>), in launch order.
+template <typename T> std::vector<int> fwd_grids(const esd_matrix* P);
 
 // Solve pieces, each a short sequence of kernel launches on stream s.
 template <typename T> void launch_init(const IterCtx<T>& c, cudaStream_t s);       // r0, z0, p0

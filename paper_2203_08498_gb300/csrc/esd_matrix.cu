@@ -5,6 +5,7 @@
 #include <numeric>
 
 #include "esd_internal.h"
+#include "esd_iter.h"
 
 namespace esd {
 
@@ -89,14 +90,20 @@ enum ValidBits { kBadRowptr = 1, kBadCol = 2, kUnsorted = 4, kNoDiag = 8, kSameC
 
 // Every index is checked before it is used, so malformed input sets error bits instead of
 // reading out of bounds.
-// One thread per row. The colour adjacency is collected as a mask of neighbour colours per
-// row, merged across the lanes of a warp that share a row colour, and written with one
-// atomic per (warp, colour pair): one atomic per entry on 64 words serialised the launch.
+// One thread per row. The colour adjacency is collected per row, merged across the lanes of a
+// warp, and written with one atomic per (warp, colour pair): one atomic per entry on a few
+// words serialised the launch. Up to 64 colours a row keeps a bit mask of its neighbour
+// colours; beyond, a list of its first kNbList distinct neighbour colours (further ones go
+// straight to their atomic).
+constexpr int kNbList = 8;
 __global__ void k_validate(int n, long long nnz, const int* rp, const int* ci, const int* cp,
                            int ncol, int* diagpos, unsigned* adj, int* err) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = i < n;
+  const bool wide = ncol > 64;
   unsigned long long mask = 0ull;  // neighbour colours (ncol <= 64)
+  int nb[kNbList];                 // neighbour colours (ncol > 64)
+  int nn = 0;
   int ci_row = -1;
   if (active) {
     int b = rp[i], e = rp[i + 1];
@@ -112,7 +119,16 @@ __global__ void k_validate(int n, long long nnz, const int* rp, const int* ci, c
       if (j == i) { dpos = k; continue; }
       int cj = colour_of(j, cp, ncol);
       if (cj == ci_row) bad |= kSameColour;
-      mask |= 1ull << cj;
+      if (!wide) {
+        mask |= 1ull << cj;
+      } else if (cj >= 0) {
+        bool seen = false;
+        for (int t = 0; t < nn; ++t) seen |= nb[t] == cj;
+        if (!seen) {
+          if (nn < kNbList) nb[nn++] = cj;
+          else atomicOr(&adj[ci_row * ncol + cj], 1u);
+        }
+      }
       // structural symmetry: (j, i) must exist
       int jb = rp[j], je = rp[j + 1];
       if (jb < 0 || je < jb || (long long)je > nnz || find_col(ci, jb, je, i) < 0) bad |= kNotSym;
@@ -123,6 +139,15 @@ __global__ void k_validate(int n, long long nnz, const int* rp, const int* ci, c
       atomicOr(&err[0], (int)bad);
       atomicMin(&err[1], i);
     }
+  }
+  if (wide) {  // (warp-uniform) one atomic per distinct (row colour, neighbour colour) of a list slot
+#pragma unroll
+    for (int t = 0; t < kNbList; ++t) {
+      const int key = (ci_row >= 0 && t < nn) ? ci_row * ncol + nb[t] : -1;
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      if (key >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicOr(&adj[key], 1u);
+    }
+    return;
   }
   const unsigned peers = __match_any_sync(0xffffffffu, ci_row);
   const unsigned lo = __reduce_or_sync(peers, (unsigned)(mask & 0xffffffffull));
@@ -513,7 +538,7 @@ int esd_create_matrix(int32_t n, int64_t nnz, const int32_t* rowptr, const int32
     ESD_CHECK(n >= 1 && n < INT32_MAX - 64, ESD_ERR_INVALID, "n out of range");
     ESD_CHECK(nnz >= n && nnz < (int64_t)INT32_MAX, ESD_ERR_INVALID, "nnz out of range");
     ESD_CHECK(rowptr && colind && val && colour_ptr, ESD_ERR_INVALID, "NULL array");
-    ESD_CHECK(ncolours >= 1 && ncolours <= kMaxColours, ESD_ERR_INVALID, "ncolours must be 1..64");
+    ESD_CHECK(ncolours >= 1 && ncolours <= kMaxColours, ESD_ERR_INVALID, "ncolours must be 1..2048");
     ESD_CHECK((flags & ~ESD_MATRIX_DIAG_SCALE) == 0, ESD_ERR_INVALID, "unknown flag");
     std::unique_ptr<esd_matrix> M(new esd_matrix());
     M->n = n;
@@ -627,6 +652,16 @@ int esd_create_matrix(int32_t n, int64_t nnz, const int32_t* rowptr, const int32
 
     // slice flags and launch sets
     build_level_sets(M.get(), hadj);
+    // grid of every forward launch (one table per kernel precision): the last forward launch
+    // of an iteration adds the block totals the earlier ones left
+    for (int prec = 0; prec < 2; ++prec) {
+      std::vector<int> g = prec == 0 ? fwd_grids<double>(M.get()) : fwd_grids<float>(M.get());
+      if (g.empty()) g.push_back(0);
+      DevBuf& dst = prec == 0 ? M->fwd_grid64 : M->fwd_grid32;
+      dst.alloc(sizeof(int) * g.size());
+      ESD_CUDA(cudaMemcpyAsync(dst.get(), g.data(), sizeof(int) * g.size(), cudaMemcpyHostToDevice, s));
+      ESD_CUDA(cudaStreamSynchronize(s));  // g is a local vector
+    }
     std::vector<unsigned char> sflags(NS, 0);
     for (int c = 0; c < ncolours; ++c)
       for (int sl = M->colour_first_slice[c]; sl < M->colour_first_slice[c + 1]; ++sl)

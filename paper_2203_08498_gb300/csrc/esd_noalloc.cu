@@ -15,7 +15,8 @@ constexpr int kNoAllocMaxK = ESD_NOALLOC_MAX_K;
 static __device__ __align__(256) double g_noalloc_scratch[2 * kNoAllocMaxK];
 
 // Device addresses of g_noalloc_scratch, one per device, looked up on the first call.
-static double* g_scratch_ptr[kMaxColours] = {};
+constexpr int kMaxDevices = 64;
+static double* g_scratch_ptr[kMaxDevices] = {};
 static std::mutex g_scratch_mutex;
 
 __device__ static int sturm_count_tab(const double* d, const double* e2, int k, double x) {
@@ -117,7 +118,7 @@ extern "C" int esd_lanczos_extremes_noalloc(const double* alpha, const double* b
               "k must be 1.." + std::to_string(kNoAllocMaxK) + " (size of the static scratch array)");
     int dev = 0;
     ESD_CUDA(cudaGetDevice(&dev));
-    ESD_CHECK(dev >= 0 && dev < kMaxColours, ESD_ERR_INVALID, "device ordinal out of range");
+    ESD_CHECK(dev >= 0 && dev < kMaxDevices, ESD_ERR_INVALID, "device ordinal out of range");
     double* scratch = nullptr;
     {
       std::lock_guard<std::mutex> lock(g_scratch_mutex);

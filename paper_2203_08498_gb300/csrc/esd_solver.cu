@@ -53,6 +53,8 @@ using namespace esd;
 
 struct esd_solver {
   esd_matrix* A = nullptr;
+  esd_matrix* P = nullptr;  // preconditioning matrix (its IC(0) factor and levels), nullptr = A
+  const esd_matrix* PM() const { return P ? P : A; }
   esd_params prm{};
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;   // private capture streams
@@ -99,10 +101,11 @@ struct esd_solver {
   IterCtx<float> ctx32(int md) const {
     IterCtx<float> c;
     c.A = A;
+    c.P = PM();
     c.Av = A->A.view<float>();
-    c.Lv = A->L.view<float>();
-    c.Uv = A->U.view<float>();
-    c.inv_d = A->inv_d32.as<float>();
+    c.Lv = PM()->L.view<float>();
+    c.Uv = PM()->U.view<float>();
+    c.inv_d = PM()->inv_d32.as<float>();
     c.rowsum = A->rowsum32.as<float>();
     c.b = b32.as<float>();
     c.x = x32.as<float>();
@@ -130,17 +133,18 @@ struct esd_solver {
     c.rho_part = rho_part.get();
     c.rho_stride = (size_t)max_grid_blocks();
     c.st = state_in.as<State>();
-    c.sflags = A->slice_flags.as<unsigned char>();
+    c.sflags = PM()->slice_flags.as<unsigned char>();
     return c;
   }
 
   IterCtx<double> ctx(int md) const {
     IterCtx<double> c;
     c.A = A;
+    c.P = PM();
     c.Av = A->A.view<double>();
-    c.Lv = A->L.view<double>();
-    c.Uv = A->U.view<double>();
-    c.inv_d = A->inv_d.as<double>();
+    c.Lv = PM()->L.view<double>();
+    c.Uv = PM()->U.view<double>();
+    c.inv_d = PM()->inv_d.as<double>();
     c.b = vb.as<double>();
     c.x = vx.as<double>();
     c.r = vr.as<double>();
@@ -165,7 +169,7 @@ struct esd_solver {
     c.rho_part = rho_part.get();
     c.rho_stride = (size_t)max_grid_blocks();
     c.st = state.as<State>();
-    c.sflags = A->slice_flags.as<unsigned char>();
+    c.sflags = PM()->slice_flags.as<unsigned char>();
     if (pw_on) {
       c.pw[0] = pw_v.as<double>();
       c.pw[1] = pw_v.as<double>() + ld;
@@ -448,7 +452,7 @@ int esd_solver_create(esd_matrix* A, const esd_params* params, esd_solver** out)
   S->state.alloc(sizeof(State));
   ESD_CUDA(cudaMemsetAsync(S->state.get(), 0, sizeof(State), S->stream));
   S->partials.alloc(sizeof(double) * (size_t)max_grid_blocks() * kMaxRed);
-  S->rho_part.alloc(sizeof(double) * (size_t)max_grid_blocks() * kMaxColours);
+  S->rho_part.alloc(sizeof(double) * (size_t)max_grid_blocks() * std::max<size_t>(1, A->fwd_sets.size()));
   S->E.alloc(sizeof(double) * kMaxM * kMaxM);
   S->Einv.alloc(sizeof(double) * kMaxM * kMaxM);
   S->ritz.alloc(sizeof(double) * kMaxM);
@@ -494,7 +498,7 @@ int esd_solve(esd_solver* S, const double* b, double* x, double tol, int32_t max
   ESD_CHECK(sample_m == 0 || S->mode != ESD_DEFLATION, ESD_ERR_STATE,
             "sampling is defined on plain / subspace-correction iterates, not in deflation mode");
   ESD_CHECK(sample_m != 1 || S->prm.sampling == ESD_SAMPLING_B, ESD_ERR_INVALID, "sampling method A needs m >= 2");
-  ESD_CHECK(S->prm.precond == ESD_PRECOND_NONE || S->A->factored, ESD_ERR_STATE,
+  ESD_CHECK(S->prm.precond == ESD_PRECOND_NONE || S->PM()->factored, ESD_ERR_STATE,
             "the IC(0) factor is missing or stale (the matrix values changed): call esd_factor_ic0");
   ESD_CHECK(S->mode == ESD_PLAIN || S->w_values_version == S->A->values_version, ESD_ERR_STATE,
             "the matrix values changed after W was built: call esd_refresh_W");
@@ -502,7 +506,10 @@ int esd_solve(esd_solver* S, const double* b, double* x, double tol, int32_t max
             "the power method runs in plain or subspace-correction solves (esd_power_start(S, NULL) stops it)");
   cudaStream_t s = S->stream;
   const int n = S->A->n;
-  if (S->fp32) S->A->ensure_fp32();
+  if (S->fp32) {
+    S->A->ensure_fp32();
+    if (S->P) S->P->ensure_fp32();
+  }
   S->build_graph(S->mode);
   copy_in(b, S->vb.get(), sizeof(double) * n, s);
   copy_in(x, S->vx.get(), sizeof(double) * n, s);
@@ -627,6 +634,25 @@ int esd_set_W(esd_solver* S, const double* W, int32_t m) {
   for (int j = 0; j < m; ++j)
     copy_in(W + (size_t)j * n, S->aux.work1.as<double>() + (size_t)j * S->ld, sizeof(double) * n, S->stream);
   install_W(S, S->aux.work1.as<double>(), m, false, std::numeric_limits<double>::infinity());
+  return ESD_OK;
+  ESD_API_END
+}
+
+int esd_solver_set_precond_matrix(esd_solver* S, esd_matrix* P) {
+  ESD_API_BEGIN
+  ESD_CHECK(S, ESD_ERR_INVALID, "NULL solver");
+  if (P) {
+    ESD_CHECK(P->n == S->A->n && P->cp == S->A->cp, ESD_ERR_INVALID,
+              "the preconditioning matrix needs the rows and colours of A (same n and colour_ptr)");
+    ESD_CHECK(P->factored, ESD_ERR_STATE, "the preconditioning matrix has no IC(0) factor (esd_factor_ic0)");
+  }
+  const esd_matrix* PM = P ? P : S->A;
+  const size_t need = sizeof(double) * (size_t)max_grid_blocks() * std::max<size_t>(1, PM->fwd_sets.size());
+  if (S->rho_part.bytes() < need) S->rho_part.alloc(need);
+  S->P = (P == S->A) ? nullptr : P;
+  if (S->fp32 && S->P) S->P->ensure_fp32();
+  S->drop_graphs();
+  ESD_CUDA(cudaStreamSynchronize(S->stream));
   return ESD_OK;
   ESD_API_END
 }
