@@ -412,6 +412,8 @@ def gpu_arm(args):
         result["power_method"] = power_method_report(esd, A, p, args, b, torch, peaks)
         # sampling method A against method B (Table sampling B): W from each, deflated solves
         result["sampling_a_vs_b"] = sampling_comparison(esd, A, p, args, b, torch)
+        # IC orderings: multicolour against the paper's block-Jacobi IC and natural order
+        result["ic_orderings"] = ordering_comparison(esd, p, args, torch, b.device)
     elif args.config == "c1":
         # latency-bound: per-iteration time of each mode through the solve graph against the
         # sum of its kernels launched one by one
@@ -663,6 +665,40 @@ def sampling_comparison(esd, A, p, args, b, torch):
             st, it, rr = S.solve(b2, x, args.tol, 20000, 0)
             row[mname + "_iterations"] = it
         out[name] = row
+    return out
+
+
+def ordering_comparison(esd, p, args, torch, device):
+    """The first system of the sequence (b = s, x0 = 0, plain FP64 ICCG) with IC(0) in three
+    orderings of the same operator: the configs' multicolour ordering; block-Jacobi IC with
+    natural order inside 16^3 blocks (the paper's parallel solver, Section 5.3, with the
+    blocks' wavefronts as launches); natural order (one launch per wavefront)."""
+    import workloads as wl
+    out = {}
+    cases = (("multicolour", None, None), ("block_jacobi_16", wl.block_wavefront_colours(p.shape, 16), 16),
+             ("natural", wl.wavefront_colours(p.shape), None))
+    for name, colours, blk in cases:
+        q = p if colours is None else wl.reorder(p, colours)
+        A = esd.Matrix.from_problem(q)
+        A.factor_ic0()
+        S = esd.Solver(A, maxit_cap=20000, sample_cap=0)
+        P = None
+        if blk is not None:
+            P = esd.Matrix.from_problem(wl.block_diagonal_part(q, wl.block_ids(p.shape, blk)))
+            P.factor_ic0()
+            S.set_precond_matrix(P)
+        levels = (P or A).info()["fwd_levels"]
+        bt = torch.from_numpy(q.source).to(device)
+        x = torch.zeros_like(bt)
+        S.solve(bt, x, args.tol, 20000, 0)  # graph capture
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, it, rr = S.solve(bt, x, args.tol, 20000, 0)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        out[name] = {"levels_per_sweep": levels, "iterations": it, "ms_per_solve": sec * 1e3,
+                     "us_per_iteration": sec / max(it, 1) * 1e6}
     return out
 
 
