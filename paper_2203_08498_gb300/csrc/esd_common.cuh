@@ -89,6 +89,8 @@ struct State {
   double gacc[kMaxM];  // FP64-iterate deflation: (AW)^T x_i accumulated as sum alpha_k h_k
   float2 ydf[kMaxM];   // FP64 deflation: y_k c_k 2^(1023-ey) as double-float pairs (c_k: AW column scales)
   int ydf_exp;         // ey, a biased binary exponent
+  float2 udf[kMaxM];   // FP64 subspace correction: u_k c_k 2^(1023-eu) as double-float pairs (c_k: W scales)
+  int udf_exp;         // eu
   unsigned int ticket[8];
 };
 

@@ -675,7 +675,8 @@ __global__ void __launch_bounds__(kBlock, M == 0 ? 4 : defl_minb<T, M>()) k_upda
   constexpr int SCM = (MODE == kModeSC) ? M : 0;
   constexpr int DM = (MODE == kModeDefl) ? M : 0;
   constexpr int R = 2 + SCM;
-  constexpr bool DF = sizeof(T) == 8 && df_cols(DM);  // AW y in double-float
+  constexpr bool DF = sizeof(T) == 8 && df_cols(DM);    // AW y in double-float
+  constexpr bool DFS = sizeof(T) == 8 && df_cols(SCM);  // f = W^T r in double-float
   __shared__ T red[red_size<R>()];
   __shared__ T ys[DM > 0 ? DM : 1];  // y in the kernel's type: converted once per block
   __shared__ float2 ys2[DF ? DM : 1];
@@ -699,10 +700,17 @@ __global__ void __launch_bounds__(kBlock, M == 0 ? 4 : defl_minb<T, M>()) k_upda
   T acc[R];
 #pragma unroll
   for (int k = 0; k < R; ++k) acc[k] = T(0);
+  // SC: double-float partial sums of f in units of 2^(et - 1023), et the largest exponent of r
+  // this warp has met
+  float fh[DFS ? SCM : 1], fl[DFS ? SCM : 1];
+  int et = 0;
+#pragma unroll
+  for (int k = 0; k < (DFS ? SCM : 1); ++k) fh[k] = fl[k] = 0.f;
   ESD_LOOP_SLICES(set) {
     int r;
     const int s = set.slice(g, &r);
     const int4 md = c.Av.meta[s];
+    double rv = 0.0;  // this lane's r_i for the double-float f (0: no row)
     if (lane < md.w) {
       const int i = md.z + lane;
       T ri;
@@ -742,8 +750,12 @@ __global__ void __launch_bounds__(kBlock, M == 0 ? 4 : defl_minb<T, M>()) k_upda
       } else {
         ri = c.r[i];
       }
+      if constexpr (DFS) {
+        rv = ri;
+      } else {
 #pragma unroll
-      for (int k = 0; k < SCM; ++k) acc[2 + k] = fma(c.W[wix<SCM>(c, k, i, s, lane)], ri, acc[2 + k]);
+        for (int k = 0; k < SCM; ++k) acc[2 + k] = fma(c.W[wix<SCM>(c, k, i, s, lane)], ri, acc[2 + k]);
+      }
       if (PRE == ESD_PRECOND_IC0) {
         const unsigned char f = c.sflags[s];
         if (f & 1) {
@@ -754,10 +766,55 @@ __global__ void __launch_bounds__(kBlock, M == 0 ? 4 : defl_minb<T, M>()) k_upda
         }
       }
     }
+    if constexpr (DFS) {
+      const int ew = (int)__reduce_max_sync(0xffffffffu, (unsigned)dexp(rv));
+      if (ew > et) {  // a larger r: bring the partial sums to the new unit (exact)
+        const float f = fpow2_neg(et - ew);
+#pragma unroll
+        for (int k = 0; k < SCM; ++k) {
+          fh[k] = __fmul_rn(fh[k], f);
+          fl[k] = __fmul_rn(fl[k], f);
+        }
+        et = ew;
+      }
+      if (lane < md.w) {
+        float rh, rl;
+        df_split(rv, et, rh, rl);
+        const float2* wp = c.Wdf + (size_t)s * SCM * kSlice + lane;
+#pragma unroll
+        for (int k = 0; k < SCM; ++k) {
+          const float2 w = wp[k * kSlice];
+          df_fma(w.x, w.y, rh, rl, fh[k], fl[k]);
+        }
+      }
+    }
   }
-  if (grid_sum_multi<R>(acc, red, (T*)c.partials, &st->ticket[kTkUpdate])) {
+  bool last;
+  if constexpr (DFS) {
+    // warp totals: ||r||^2 and the level-0 rho part in FP64, f in double-float converted once
+    const int w = threadIdx.x >> 5;
+    double v0 = acc[0], v1 = acc[1];
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+      v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+    }
+    if (lane_id() == 0) {
+      red[w * R] = v0;
+      red[w * R + 1] = v1;
+    }
+    df_warp_sum_chunks<0, SCM, R>(fh, fl, et > 0 ? dpow2(et) : 0.0, (double*)red, 2, lane_id(), w);
+    last = grid_sum_from_warps<R>(red, (T*)c.partials, &st->ticket[kTkUpdate]);
+  } else {
+    last = grid_sum_multi<R>(acc, red, (T*)c.partials, &st->ticket[kTkUpdate]);
+  }
+  if (last) {
     if (SCM > 0) {
       if (threadIdx.x < 32) {
+        if constexpr (DFS) {  // the double-float sums hold (W 2^-e_k)^T r
+          for (int k = threadIdx.x; k < SCM; k += 32) red[2 + k] *= c.wscale[k];
+          __syncwarp();
+        }
         double part = 0.0;
         for (int i = threadIdx.x; i < SCM; i += 32) {
           double u = 0.0;
@@ -767,6 +824,20 @@ __global__ void __launch_bounds__(kBlock, M == 0 ? 4 : defl_minb<T, M>()) k_upda
         }
         for (int o = 16; o >= 1; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
         if (threadIdx.x == 0) fu_s = part;
+        if constexpr (DFS) {
+          // u_k 2^e_k as double-float pairs for the backward sweep
+          __syncwarp();
+          int e = 0;
+          for (int k = threadIdx.x; k < SCM; k += 32) e = max(e, dexp(st->u[k] * c.wscale[k]));
+          e = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
+          if (e == 0) e = 1023;
+          for (int k = threadIdx.x; k < SCM; k += 32) {
+            float h, l;
+            df_split(st->u[k] * c.wscale[k], e, h, l);
+            st->udf[k] = make_float2(h, l);
+          }
+          if (threadIdx.x == 0) st->udf_exp = e;
+        }
       }
       __syncthreads();
     }
@@ -858,14 +929,22 @@ __global__ void __launch_bounds__(kBlock, sweep_minb<T>())
 // only take the direction update.
 template <typename T, int SCM>
 __global__ void __launch_bounds__(kBlock, SCM == 0 ? sweep_minb<T>() : 1) k_bwd(IterCtx<T> c, SliceSet set, SliceSet elem) {
+  constexpr bool DFS = sizeof(T) == 8 && df_cols(SCM);  // W u in double-float
   __shared__ T us[SCM > 0 ? SCM : 1];  // u in the kernel's type: converted once per block
+  __shared__ float2 us2[DFS ? SCM : 1];
+  __shared__ int uexp;
   pdl_enter();
   State* st = c.st;
   if (st->conv) return;
   const T beta = (T)st->beta;
   const bool first = st->iter == 0 || st->fresh_dir;
   if (SCM > 0) {
-    for (int k = threadIdx.x; k < SCM; k += blockDim.x) us[k] = (T)st->u[k];
+    if constexpr (DFS) {
+      for (int k = threadIdx.x; k < SCM; k += blockDim.x) us2[k] = st->udf[k];
+      if (threadIdx.x == 0) uexp = st->udf_exp;
+    } else {
+      for (int k = threadIdx.x; k < SCM; k += blockDim.x) us[k] = (T)st->u[k];
+    }
     __syncthreads();
   }
   const int nsweep = set.total();
@@ -888,8 +967,19 @@ __global__ void __launch_bounds__(kBlock, SCM == 0 ? sweep_minb<T>() : 1) k_bwd(
       const T zic = sweep ? raw * d : raw;
       if (sweep) c.Y[i] = zic;
       T z = zic;
+      if constexpr (DFS) {
+        float th = 0.f, tl = 0.f;
+        const float2* wp = c.Wdf + (size_t)s * SCM * kSlice + lane;
 #pragma unroll
-      for (int k = 0; k < SCM; ++k) z = fma(c.W[wix<SCM>(c, k, i, s, lane)], us[k], z);
+        for (int k = 0; k < SCM; ++k) {
+          const float2 w = wp[k * kSlice];
+          df_fma(w.x, w.y, us2[k].x, us2[k].y, th, tl);
+        }
+        z += f2d_pow2(th, uexp) + f2d_pow2(tl, uexp);
+      } else {
+#pragma unroll
+        for (int k = 0; k < SCM; ++k) z = fma(c.W[wix<SCM>(c, k, i, s, lane)], us[k], z);
+      }
       c.p[i] = first ? z : fma(beta, pold, z);
     }
   }
@@ -898,14 +988,22 @@ __global__ void __launch_bounds__(kBlock, SCM == 0 ? sweep_minb<T>() : 1) k_bwd(
 // No preconditioner: p = r [+ W u] + beta p.
 template <typename T, int SCM>
 __global__ void __launch_bounds__(kBlock, SCM == 0 ? 4 : 1) k_dir(IterCtx<T> c, SliceSet set) {
+  constexpr bool DFS = sizeof(T) == 8 && df_cols(SCM);  // W u in double-float
   __shared__ T us[SCM > 0 ? SCM : 1];  // u in the kernel's type: converted once per block
+  __shared__ float2 us2[DFS ? SCM : 1];
+  __shared__ int uexp;
   pdl_enter();
   State* st = c.st;
   if (st->conv) return;
   const T beta = (T)st->beta;
   const bool first = st->iter == 0 || st->fresh_dir;
   if (SCM > 0) {
-    for (int k = threadIdx.x; k < SCM; k += blockDim.x) us[k] = (T)st->u[k];
+    if constexpr (DFS) {
+      for (int k = threadIdx.x; k < SCM; k += blockDim.x) us2[k] = st->udf[k];
+      if (threadIdx.x == 0) uexp = st->udf_exp;
+    } else {
+      for (int k = threadIdx.x; k < SCM; k += blockDim.x) us[k] = (T)st->u[k];
+    }
     __syncthreads();
   }
   ESD_LOOP_SLICES(set) {
@@ -915,8 +1013,19 @@ __global__ void __launch_bounds__(kBlock, SCM == 0 ? 4 : 1) k_dir(IterCtx<T> c, 
     if (lane < md.w) {
       const int i = md.z + lane;
       T z = c.r[i];
+      if constexpr (DFS) {
+        float th = 0.f, tl = 0.f;
+        const float2* wp = c.Wdf + (size_t)s * SCM * kSlice + lane;
 #pragma unroll
-      for (int k = 0; k < SCM; ++k) z = fma(c.W[wix<SCM>(c, k, i, s, lane)], us[k], z);
+        for (int k = 0; k < SCM; ++k) {
+          const float2 w = wp[k * kSlice];
+          df_fma(w.x, w.y, us2[k].x, us2[k].y, th, tl);
+        }
+        z += f2d_pow2(th, uexp) + f2d_pow2(tl, uexp);
+      } else {
+#pragma unroll
+        for (int k = 0; k < SCM; ++k) z = fma(c.W[wix<SCM>(c, k, i, s, lane)], us[k], z);
+      }
       c.p[i] = first ? z : fma(beta, c.p[i], z);
     }
   }

@@ -51,6 +51,8 @@ struct IterCtx {
   // scaled by 2^-e_k so that its largest entry lies in [1/2, 1); awscale[k] = 2^e_k
   const float2* AWdf = nullptr;
   const double* awscale = nullptr;
+  const float2* Wdf = nullptr;     // W in the same form (FP64 subspace correction)
+  const double* wscale = nullptr;
   // power method (FP64 plain / SC solves): w in pw[steps & 1], the next product into the other
   double* pw[2] = {nullptr, nullptr};
   PowerState* pws = nullptr;
@@ -87,10 +89,10 @@ void launch_true_residual(const IterCtx<double>& c, cudaStream_t s);
 // set_scale also scale = 1/||w|| and steps = 0 (w is a new start vector).
 void launch_power_rq(const esd_matrix* A, double* const pw[2], PowerState* pws, double* partials, int set_scale,
                      cudaStream_t s);
-// AWdf (nslices x 32 x M float2) and awscale (M doubles) from AW (n x m, column-major); cexp:
-// kMaxM ints of scratch
-void launch_aw_df(const esd_matrix* A, const double* AW, size_t ld, int m, int M, float2* out, double* awscale,
-                  int* cexp, cudaStream_t s);
+// X (n x m, column-major, AW or W) as double-float pairs, nslices x 32 x M float2 in
+// slice-major order with column k scaled by 2^-e_k, and scale[k] = 2^e_k; cexp: kMaxM ints
+void launch_df_pairs(const esd_matrix* A, const double* X, size_t ld, int m, int M, float2* out, double* scale,
+                     int* cexp, cudaStream_t s);
 // unit = w / ||w||, with ||w||^2 from the last launch_power_rq
 void launch_power_unit(const esd_matrix* A, const double* w, const PowerState* pws, double* unit, cudaStream_t s);
 // y = A X for an n x m block (column-major, stride ld), m columns

@@ -94,7 +94,7 @@ void launch_power_unit(const esd_matrix* A, const double* w, const PowerState* p
   ESD_CUDA(cudaGetLastError());
 }
 
-// Largest binary exponent of each column of AW (n x m, column-major, stride ld).
+// Largest binary exponent of each column of AW or W (n x m, column-major, stride ld).
 __global__ void k_aw_colexp(int n, const double* AW, size_t ld, int* cexp) {
   const int k = blockIdx.y;
   int e = 0;
@@ -104,8 +104,8 @@ __global__ void k_aw_colexp(int n, const double* AW, size_t ld, int* cexp) {
   if ((threadIdx.x & 31) == 0 && e > 0) atomicMax(&cexp[k], e);
 }
 
-// AW 2^-e_k as double-float pairs in slice-major order; awscale[k] = 2^e_k (1 for a zero or
-// padding column)
+// X 2^-e_k (X = AW or W) as double-float pairs in slice-major order; scale[k] = 2^e_k (1 for a
+// zero or padding column)
 __global__ void k_aw_df(int n, const int* rowpos, const double* AW, size_t ld, int m, int M, const int* cexp,
                         float2* out) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -123,8 +123,8 @@ __global__ void k_aw_scale(int M, const int* cexp, double* awscale) {
   for (int k = threadIdx.x; k < M; k += blockDim.x) awscale[k] = dpow2(cexp[k] > 0 ? cexp[k] : 1023);
 }
 
-void launch_aw_df(const esd_matrix* A, const double* AW, size_t ld, int m, int M, float2* out, double* awscale,
-                  int* cexp, cudaStream_t s) {
+void launch_df_pairs(const esd_matrix* A, const double* AW, size_t ld, int m, int M, float2* out, double* awscale,
+                     int* cexp, cudaStream_t s) {
   ESD_CUDA(cudaMemsetAsync(cexp, 0, sizeof(int) * kMaxM, s));
   ESD_CUDA(cudaMemsetAsync(out, 0, sizeof(float2) * (size_t)A->nslices * kSlice * M, s));
   if (m > 0) {

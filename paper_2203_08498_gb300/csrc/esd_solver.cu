@@ -65,6 +65,7 @@ struct esd_solver {
   DevBuf vb, vx, vr, vp, vq, vY, samples;
   DevBuf W, AW, E, Einv, ritz, ahist, bhist, state, partials, rho_part, ext, lz;
   DevBuf AWdf, awscale, awexp;  // AW as double-float pairs for the FP64 deflated iteration
+  DevBuf Wdf, wscale;           // W likewise, for the FP64 subspace correction
   State* hst = nullptr;  // pinned host copy
   // FP32-inner / FP64-refinement form
   bool fp32 = false;
@@ -161,6 +162,8 @@ struct esd_solver {
       c.M = M;
       c.AWdf = AWdf.as<float2>();
       c.awscale = awscale.as<double>();
+      c.Wdf = Wdf.as<float2>();
+      c.wscale = wscale.as<double>();
     }
     c.samples = samples.get() ? samples.as<double>() : nullptr;
     c.ahist = ahist.as<double>();
@@ -583,13 +586,19 @@ static void install_W(esd_solver* S, const double* X, int m, bool orth, double t
   if (df_cols(pad_cols(mkeep))) {
     const int Mp = pad_cols(mkeep);
     const size_t need = sizeof(float2) * (size_t)S->A->nslices * kSlice * Mp;
-    if (S->AWdf.bytes() < need) S->AWdf.alloc(need);
+    if (S->AWdf.bytes() < need) {
+      S->AWdf.alloc(need);
+      S->Wdf.alloc(need);
+    }
     if (!S->awscale.get()) {
       S->awscale.alloc(sizeof(double) * kMaxM);
+      S->wscale.alloc(sizeof(double) * kMaxM);
       S->awexp.alloc(sizeof(int) * kMaxM);
     }
-    launch_aw_df(S->A, S->AW.as<double>(), ld, mkeep, Mp, S->AWdf.as<float2>(), S->awscale.as<double>(),
-                 S->awexp.as<int>(), S->stream);
+    launch_df_pairs(S->A, S->AW.as<double>(), ld, mkeep, Mp, S->AWdf.as<float2>(), S->awscale.as<double>(),
+                    S->awexp.as<int>(), S->stream);
+    launch_df_pairs(S->A, S->W.as<double>(), ld, mkeep, Mp, S->Wdf.as<float2>(), S->wscale.as<double>(),
+                    S->awexp.as<int>(), S->stream);
   }
   ESD_CUDA(cudaStreamSynchronize(S->stream));
   S->m = mkeep;

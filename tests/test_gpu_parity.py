@@ -194,9 +194,10 @@ def test_accelerated_solve_with_oracle_w(c1_oracle_w, mode):
     np.testing.assert_allclose(bb[:k - 1], out["beta"][:k - 1], rtol=1e-11)
 
 
+@pytest.mark.parametrize("mode", [esd.DEFLATION, esd.SUBSPACE_CORRECTION])
 @pytest.mark.parametrize("m", [3, 12, 20, 30, 40])
-def test_deflation_column_counts(m):
-    """Deflated PCG with m columns of a seeded orthonormal W against the oracle's DPCG: the
+def test_w_column_counts(m, mode):
+    """Deflated and SC PCG with m columns of a seeded orthonormal W against the oracle: the
     double-float W terms (m padded to 8, 16, 24, 32) and the FP64 ones (m = 40, padded to 64)
     give the same iterations (+-1), alpha to 1e-11 and x to 1e-9."""
     p = wl.small_3d(9, seed=11)
@@ -207,10 +208,10 @@ def test_deflation_column_counts(m):
     W = np.asfortranarray(W)
     S = esd.Solver(A, sample_cap=0)
     S.set_W(W)
-    S.set_mode(esd.DEFLATION)
+    S.set_mode(mode)
     x = np.zeros(p.n)
     st, it, rr = S.solve(p.source, x, tol=1e-10)
-    out = oracle.System(p, ic, oracle.DEFLATION, oracle.Aux.from_basis(p, W)).solve(p.source, tol=1e-10)
+    out = oracle.System(p, ic, mode, oracle.Aux.from_basis(p, W)).solve(p.source, tol=1e-10)
     assert st == esd.OK and abs(it - out["iters"]) <= 1, (it, out["iters"])
     assert rel(x, out["x"]) <= 1e-9
     a, _ = S.history()
