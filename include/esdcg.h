@@ -219,6 +219,10 @@ int esd_set_mode(esd_solver* S, int32_t mode);
  * Plain / SC mode: PCG as in Algorithm "PCG with condition number estimation", with its
  * power method once esd_power_start has been called (see there). Deflation: Algorithm "Deflated PCG" with beta = +rho_{i+1}/rho_i and the
  * final x = P x_i + W E^{-1} W^T b. b = 0 gives x = 0 and 0 iterations.
+ * Arithmetic of the FP64 form: FP64 throughout, except that with up to 32 (padded) columns of
+ * W the deflation and subspace-correction terms ((AW)^T p, AW y, W^T r, W u) are formed in
+ * double-float arithmetic on the FP32 pipe (float pairs, about 48 significant bits; terms
+ * 2^-100 below the largest dropped), below FP64's own rounding of these n-term sums.
  * The whole solve is one CUDA graph launch (a device-side while loop); the call
  * synchronises once at the end to return iters and relres.
  * Precision ESD_FP32_REFINE (not in the paper): x is refined in FP64. Each step forms
