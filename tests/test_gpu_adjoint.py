@@ -6,8 +6,8 @@
                  lambda and x to 1e-12;
   autograd       dL/dtheta and dL/db of L = ||x - x_target||^2 through AdjointSolve match
                  the oracle's ICCG adjoint gradient to 1e-8 (both solves at tol 1e-13) and
-                 central finite differences (step 1e-6) on sampled cells to 1e-5, with the
-                 forward and the adjoint solve deflated by the same W;
+                 central finite differences on 32 seeded cells in theta (step 1e-6) and 8 in
+                 b, to 1e-5, with the forward and the adjoint solve deflated by the same W;
   state          solves refuse a stale factor or a W formed for other matrix values.
 """
 import numpy as np
@@ -188,7 +188,7 @@ def test_autograd_matches_finite_differences(c4_small):
             xx = fv_solve(t, b, model, tol=1e-13)
             return float(((xx - dev(xt)) ** 2).sum())
 
-    cells = np.random.default_rng(7).choice(p.n, size=8, replace=False)
+    cells = np.random.default_rng(7).choice(p.n, size=32, replace=False)
     step = 1e-6
     for c in cells:
         tp, tm = th0.clone(), th0.clone()
@@ -196,6 +196,24 @@ def test_autograd_matches_finite_differences(c4_small):
         tm[c] -= step
         fd = (loss(tp) - loss(tm)) / (2 * step)
         assert abs(fd - g[c]) <= 1e-5 * np.abs(g).max(), (c, fd, g[c])
+    # dL/db against central differences in b on 8 cells
+    bb = b.clone().requires_grad_(True)
+    x = fv_solve(th0, bb, model, tol=1e-13)
+    ((x - dev(xt)) ** 2).sum().backward()
+    gb = bb.grad.cpu().numpy()
+
+    def loss_b(bv):
+        with torch.no_grad():
+            xx = fv_solve(th0, bv, model, tol=1e-13)
+            return float(((xx - dev(xt)) ** 2).sum())
+
+    hb = 1e-6 * float(b.abs().max())
+    for c in np.random.default_rng(8).choice(p.n, size=8, replace=False):
+        bp, bm = b.clone(), b.clone()
+        bp[c] += hb
+        bm[c] -= hb
+        fd = (loss_b(bp) - loss_b(bm)) / (2 * hb)
+        assert abs(fd - gb[c]) <= 1e-5 * np.abs(gb).max(), (c, fd, gb[c])
 
 
 @pytest.mark.slow

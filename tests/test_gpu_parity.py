@@ -217,6 +217,11 @@ def test_w_column_counts(m, mode):
     a, _ = S.history()
     k = min(it, out["iters"], 10)
     np.testing.assert_allclose(a[:k], out["alpha"][:k], rtol=1e-11)
+    if mode == esd.DEFLATION:
+        # the corrected deflation solution leaves no residual in range(W): W^T (b - A x) = 0
+        # holds for any iterate x_i, since W^T A P = 0 (Eq. x1)
+        res = p.source - p.scipy() @ x
+        assert np.abs(W.T @ res).max() <= 1e-11 * np.linalg.norm(p.source)
 
 
 def test_w_build_from_same_samples():
