@@ -164,6 +164,7 @@ struct esd_solver {
       c.awscale = awscale.as<double>();
       c.Wdf = Wdf.as<float2>();
       c.wscale = wscale.as<double>();
+      ESD_CHECK(!df_cols(M) || (c.AWdf && c.Wdf), ESD_ERR_INTERNAL, "the double-float copies of AW and W are missing");
     }
     c.samples = samples.get() ? samples.as<double>() : nullptr;
     c.ahist = ahist.as<double>();
@@ -307,6 +308,25 @@ struct esd_solver {
     }
     fp32 = true;
     A->ensure_fp32();
+  }
+
+  // AW and W as double-float pairs for the FP64 iteration (up to 32 padded columns); the
+  // refinement form reads its FP32 copies instead and needs none
+  void refresh_df() {
+    if (fp32 || !have_W || !df_cols(M)) return;
+    const size_t need = sizeof(float2) * (size_t)A->nslices * kSlice * M;
+    if (AWdf.bytes() < need) {
+      AWdf.alloc(need);
+      Wdf.alloc(need);
+    }
+    if (!awscale.get()) {
+      awscale.alloc(sizeof(double) * kMaxM);
+      wscale.alloc(sizeof(double) * kMaxM);
+      awexp.alloc(sizeof(int) * kMaxM);
+    }
+    launch_df_pairs(A, AW.as<double>(), ld, m, M, AWdf.as<float2>(), awscale.as<double>(), awexp.as<int>(), stream);
+    launch_df_pairs(A, W.as<double>(), ld, m, M, Wdf.as<float2>(), wscale.as<double>(), awexp.as<int>(), stream);
+    ESD_CUDA(cudaStreamSynchronize(stream));
   }
 
   void drop_graphs() {
@@ -583,23 +603,6 @@ static void install_W(esd_solver* S, const double* X, int m, bool orth, double t
               std::numeric_limits<double>::infinity(), S->W.as<double>(), S->AW.as<double>(),
               S->E.as<double>(), S->Einv.as<double>(), S->ritz.as<double>(), &unused, S->stream);
   }
-  if (df_cols(pad_cols(mkeep))) {
-    const int Mp = pad_cols(mkeep);
-    const size_t need = sizeof(float2) * (size_t)S->A->nslices * kSlice * Mp;
-    if (S->AWdf.bytes() < need) {
-      S->AWdf.alloc(need);
-      S->Wdf.alloc(need);
-    }
-    if (!S->awscale.get()) {
-      S->awscale.alloc(sizeof(double) * kMaxM);
-      S->wscale.alloc(sizeof(double) * kMaxM);
-      S->awexp.alloc(sizeof(int) * kMaxM);
-    }
-    launch_df_pairs(S->A, S->AW.as<double>(), ld, mkeep, Mp, S->AWdf.as<float2>(), S->awscale.as<double>(),
-                    S->awexp.as<int>(), S->stream);
-    launch_df_pairs(S->A, S->W.as<double>(), ld, mkeep, Mp, S->Wdf.as<float2>(), S->wscale.as<double>(),
-                    S->awexp.as<int>(), S->stream);
-  }
   ESD_CUDA(cudaStreamSynchronize(S->stream));
   S->m = mkeep;
   S->M = pad_cols(mkeep);
@@ -607,6 +610,7 @@ static void install_W(esd_solver* S, const double* X, int m, bool orth, double t
   S->have_W = true;
   S->w_version++;
   S->w_values_version = S->A->values_version;
+  S->refresh_df();
   S->refresh_w32();
   ESD_CUDA(cudaStreamSynchronize(S->stream));
 }
@@ -674,6 +678,7 @@ int esd_set_precision(esd_solver* S, int32_t precision, double inner_tol) {
     if (S->fp32) S->drop_graphs();
     S->fp32 = false;
     S->prm.precision = ESD_FP64;
+    S->refresh_df();  // the double-float copies of AW and W the FP64 iteration reads
     return ESD_OK;
   }
   ESD_CHECK(inner_tol > 0.0 && inner_tol < 1.0, ESD_ERR_INVALID, "refinement needs 0 < inner_tol < 1");
