@@ -47,7 +47,7 @@ enum esd_mode {
 enum esd_precond { ESD_PRECOND_NONE = 0, ESD_PRECOND_IC0 = 1 };
 
 enum esd_precision {
-  ESD_FP64 = 0,        /* every step in FP64 */
+  ESD_FP64 = 0,        /* FP64 (the W terms of up to 32 columns in double-float, see esd_solve) */
   ESD_FP32_REFINE = 1  /* FP32 inner PCG inside an FP64 iterative refinement */
 };
 
@@ -209,16 +209,18 @@ int esd_set_mode(esd_solver* S, int32_t mode);
  *   x         n doubles (device or host): initial guess on entry, solution on exit
  *   tol       relative tolerance > 0
  *   maxit     1 .. maxit_cap
- *   sample_m  0, or 1 .. sample_cap: store iterates by sampling method A (Appendix A) for
- *             a following esd_sample_and_build_W. Not allowed in deflation mode (its
- *             iterates live in the deflated space): ESD_ERR_STATE.
+ *   sample_m  0, or 1 .. sample_cap: store iterates by the solver's sampling method (A,
+ *             Appendix A, needs m >= 2; or B, Section 4.2) for a following
+ *             esd_sample_and_build_W. Not allowed in deflation mode (its iterates live in
+ *             the deflated space): ESD_ERR_STATE.
  *   iters     (host, may be NULL) alpha steps taken
  *   relres    (host, may be NULL) final ||r_i||/||b|| of the recursive residual; in
  *             deflation mode r_i = P^T (b - A x_i), which equals the true residual of the
  *             returned x (Eq. x1/x2)
  * Plain / SC mode: PCG as in Algorithm "PCG with condition number estimation", with its
- * power method once esd_power_start has been called (see there). Deflation: Algorithm "Deflated PCG" with beta = +rho_{i+1}/rho_i and the
- * final x = P x_i + W E^{-1} W^T b. b = 0 gives x = 0 and 0 iterations.
+ * power method once esd_power_start has been called (see there). Deflation: Algorithm
+ * "Deflated PCG" with beta = +rho_{i+1}/rho_i and the final x = P x_i + W E^{-1} W^T b.
+ * b = 0 gives x = 0 and 0 iterations.
  * Arithmetic of the FP64 form: FP64 throughout, except that with up to 32 (padded) columns of
  * W the deflation and subspace-correction terms ((AW)^T p, AW y, W^T r, W u) are formed in
  * double-float arithmetic on the FP32 pipe (float pairs, about 48 significant bits; terms
