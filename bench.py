@@ -406,6 +406,15 @@ def gpu_arm(args):
         result["precision_form"] = pf
         # time per iteration and model bandwidth per mode (single solves of system 2)
         result["iteration"] = iteration_roofline(S, esd, p, args, x, b, src, peaks)
+        # gamma of Eq. ganma: time per accelerated iteration over time per plain one, against
+        # the paper's byte model (T_sciccg / T_iccg), and the sequence speedups over plain
+        it_t = {k: v["ms_per_iter"] for k, v in result["iteration"].items()}
+        nnz_av = p.nnz / p.n
+        result["gamma"] = {"model": (116 + 16 * args.m + 24 * nnz_av) / (100 + 24 * nnz_av),
+                           "measured_deflation": it_t["deflation"] / it_t["plain"],
+                           "measured_sc": it_t["sc"] / it_t["plain"],
+                           "sequence_speedup_vs_plain": {k: modes["plain"]["ms_per_sequence"] / modes[k]["ms_per_sequence"]
+                                                         for k in ("deflation", "sc")}}
         # end to end through the C ABI with host buffers
         result["e2e"] = e2e(esd, p, args, torch)
         # the condition estimate of Algorithm PCG-con and the cost of its fused power product
@@ -795,10 +804,24 @@ def extrapolate(rates, its):
     return len(its) / sec
 
 
+def host_info():
+    """Host cores and CPU model of the machine that timed the oracle."""
+    import platform
+    model = platform.processor() or platform.machine()
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": platform.machine()}
+
+
 def cpu_baseline(p, args, its):
     k = 20 if p.nnz < 50_000_000 else 3  # keep the CPU sample to tens of seconds
     r = oracle_rates(p, args, iters_plain=k, iters_acc=k)
-    return {"value": extrapolate(r, its), "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": extrapolate(r, its), "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_info(),
             "sample": (f"{k} plain and {k} {args.mode} FP64 ICCG iterations of the {args.config} system "
                        f"(n={p.n}, m={args.m}, orthonormal W) on one host core, extrapolated with this "
                        f"run's iteration counts per solve"), "s_per_iter": r}
@@ -834,7 +857,7 @@ def reference_arm(args):
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(args, p), "grid": args.grid, "n": p.n, "nnz": p.nnz},
-            "cpu_baseline": {"value": v, "unit": UNIT, "kind": "oracle", "cores": 1,
+            "cpu_baseline": {"value": v, "unit": UNIT, "kind": "oracle", "cores": 1, "host": host_info(),
                              "sample": "5 plain and 5 accelerated oracle iterations per step, extrapolated "
                                        "with the oracle's own iteration counts of this sequence "
                                        "(oracle/data, written by oracle/sequence_counts.py)"},
