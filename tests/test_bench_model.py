@@ -1,0 +1,62 @@
+"""bench.py's algorithmic model (CPU only): the per-launch byte and FMA counts the roofline
+divides by, checked against the formulas written out here, and the reported host fields."""
+import types
+
+import numpy as np
+
+import bench
+
+ESD = types.SimpleNamespace(PLAIN=0, DEFLATION=1, SUBSPACE_CORRECTION=2)
+
+
+def _problem(n, nnz):
+    return types.SimpleNamespace(n=n, nnz=nnz)
+
+
+def test_pad_m_matches_the_compiled_column_counts():
+    assert [bench.pad_m(m) for m in (0, 1, 8, 9, 16, 17, 24, 25, 32, 33, 64)] == [0, 8, 8, 16, 16, 24, 24, 32, 32, 64, 64]
+
+
+def test_spmv_model_fp64_and_fp32():
+    n, nnz, m = 2_097_152, 14_581_760, 16
+    p = _problem(n, nnz)
+    lv = (np.array([n // 8]), None, None)
+    a64 = types.SimpleNamespace(precision="fp64", m=m)
+    by, fm = bench.kernel_model("spmv_pq", p, a64, ESD.DEFLATION, ESD, lv)
+    assert by == 12 * nnz + 20 * n + 8 * m * n  # A (value + column), p read, q written, AW
+    assert fm == nnz + n  # (AW)^T p runs in double-float on the FP32 pipe for m <= 32
+    by, fm = bench.kernel_model("spmv_pq", p, a64, ESD.PLAIN, ESD, lv)
+    assert (by, fm) == (12 * nnz + 20 * n, nnz + n)
+    a64w = types.SimpleNamespace(precision="fp64", m=40)  # padded to 64: FP64 W terms
+    by, fm = bench.kernel_model("spmv_pq", p, a64w, ESD.DEFLATION, ESD, lv)
+    assert fm == nnz + n + 40 * n
+    a32 = types.SimpleNamespace(precision="fp32", m=m)
+    by, fm = bench.kernel_model("spmv_pq", p, a32, ESD.DEFLATION, ESD, lv)
+    assert by == 8 * nnz + 12 * n + 4 * n + 4 * m * n  # FP32 pairs, s = A 1 read, FP32 AW
+    assert fm == nnz + n + m * n
+
+
+def test_update_model():
+    n, m = 1000, 16
+    p = _problem(n, 7 * n)
+    n0 = 125
+    lv = (np.array([n0]), None, None)
+    a = types.SimpleNamespace(precision="fp64", m=m)
+    by, fm = bench.kernel_model("update", p, a, ESD.DEFLATION, ESD, lv)
+    assert by == 16 * n + 32 * n + 8 * m * n + 16 * n0
+    assert fm == 3 * n + 2 * n0  # AW y in double-float
+    by, fm = bench.kernel_model("update", p, a, ESD.PLAIN, ESD, lv)
+    assert (by, fm) == (16 * n + 32 * n + 16 * n0, 3 * n + 2 * n0)
+
+
+def test_gamma_model_is_the_papers_ratio():
+    """Eq. ganma for the 128^3 7-point workload with m = 16: (116 + 16 m + 24 nnz_av) /
+    (100 + 24 nnz_av) = 2.02."""
+    nnz_av = 14_581_760 / 2_097_152
+    g = (116 + 16 * 16 + 24 * nnz_av) / (100 + 24 * nnz_av)
+    assert abs(g - 2.02) < 0.005
+
+
+def test_host_info_fields():
+    h = bench.host_info()
+    assert h["nproc"] >= 1 and isinstance(h["cpu_model"], str) and h["machine"]
