@@ -7,7 +7,21 @@ may be CUDA torch tensors, CPU torch tensors or NumPy arrays (host data is stage
 library). There is no fallback: without the compiled library every call raises.
 
 The functions keep the C names (``esd_create_matrix``, ``esd_solve`` ...); ``Matrix`` and
-``Solver`` own the handles.
+``Solver`` own the handles. A sequence as the paper runs it::
+
+    A = Matrix(rowptr, colind, val, colour_ptr)        # CSR in multicolour order
+    A.factor_ic0()                                     # IC(0), M = L L^T
+    S = Solver(A, sample_cap=16)
+    S.solve(b1, x1, tol=1e-8, sample_m=16)             # plain ICCG, 16 iterates sampled
+    S.sample_and_build_W()                             # W from the error vectors, E = W^T A W
+    S.set_mode(DEFLATION)                              # or SUBSPACE_CORRECTION
+    for b, x in later_systems:
+        status, iters, relres = S.solve(b, x, tol=1e-8)
+
+Options: ``Solver(..., precision=FP32_REFINE)`` (FP32 inner PCG in FP64 refinement),
+``sampling=SAMPLING_B``, ``power_start`` / ``paper_cond_estimate`` (the paper's condition
+estimate), ``set_precond_matrix`` (block-Jacobi IC), ``Matrix(..., diag_scale=True)``;
+``adjoint.fv_solve`` differentiates a solve through the adjoint.
 """
 from __future__ import annotations
 
