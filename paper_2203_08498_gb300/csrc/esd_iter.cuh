@@ -30,10 +30,10 @@ namespace esd {
 
 enum { kModePlain = ESD_PLAIN, kModeDefl = ESD_DEFLATION, kModeSC = ESD_SUBSPACE_CORRECTION };
 
-// Resident blocks per SM requested from the compiler for the slice kernels without W terms
-// (4 caps them at 32 registers per thread).
+// Resident blocks per SM requested from the compiler for the FP64 substitution kernels
+// (3: up to 42 registers per thread; measured 3-4 % faster per iteration than 4 blocks at 32)
 #ifndef ESD_SWEEP_MINB
-#define ESD_SWEEP_MINB 4
+#define ESD_SWEEP_MINB 3
 #endif
 // FP32 kernels move half the bytes per load, so they need more loads in flight per thread
 #ifndef ESD_SWEEP_MINB_F32
@@ -48,6 +48,15 @@ enum { kModePlain = ESD_PLAIN, kModeDefl = ESD_DEFLATION, kModeSC = ESD_SUBSPACE
 #endif
 #ifndef ESD_ROW_UNROLL_F32
 #define ESD_ROW_UNROLL_F32 4
+#endif
+// unroll of the FP64 row products of the substitution kernels (k_fwd, k_bwd): their rows
+// hold 2 to 6 factor entries, and 2 beat 4 by another 1-2 % per iteration
+#ifndef ESD_SWEEP_UNROLL
+#define ESD_SWEEP_UNROLL 2
+#endif
+// resident blocks per SM of the FP64 SpMV without W terms (plain and SC modes)
+#ifndef ESD_SPMV_MINB
+#define ESD_SPMV_MINB 4
 #endif
 // resident blocks per SM of the FP64 deflated SpMV (double-float W terms)
 #ifndef ESD_DF_MINB
@@ -68,8 +77,9 @@ constexpr int sweep_minb() {
 template <typename T>
 __device__ __forceinline__ T ld_stream(const T* p) { return __ldcs(p); }
 
-// init + sum_k val[s,k,lane] * v[col[s,k,lane]] for the row of this lane in slice md
-template <typename T>
+// init + sum_k val[s,k,lane] * v[col[s,k,lane]] for the row of this lane in slice md; SWEEP
+// selects the unroll of the substitution kernels for FP64
+template <typename T, bool SWEEP = false>
 __device__ __forceinline__ T row_fma(const SellView<T>& M, const int4& md, int lane, const T* __restrict__ v,
                                      T init) {
   const int* cp = M.col + md.x + lane;
@@ -84,6 +94,9 @@ __device__ __forceinline__ T row_fma(const SellView<T>& M, const int4& md, int l
     }
   } else if (sizeof(T) == 4) {
     ESD_UNROLL(ESD_ROW_UNROLL_F32)
+    for (int k = 0; k < md.y; ++k) acc = fma(ld_stream(vp + k * kSlice), v[ld_stream(cp + k * kSlice)], acc);
+  } else if (SWEEP) {
+    ESD_UNROLL(ESD_SWEEP_UNROLL)
     for (int k = 0; k < md.y; ++k) acc = fma(ld_stream(vp + k * kSlice), v[ld_stream(cp + k * kSlice)], acc);
   } else {
     ESD_UNROLL(ESD_ROW_UNROLL)
@@ -471,7 +484,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_bwd_plain(SellView<T> U, SliceSet
 // half the registers of FP64
 template <typename T, int M>
 constexpr int defl_minb() {
-  return M == 0 ? sweep_minb<T>() : ((sizeof(T) == 4 ? M <= 32 : M <= 16) ? 2 : 1);
+  return M == 0 ? (sizeof(T) == 8 ? ESD_SPMV_MINB : sweep_minb<T>()) : ((sizeof(T) == 4 ? M <= 32 : M <= 16) ? 2 : 1);
 }
 
 // q = A p and (p, q) [+ h = (AW)^T p, y = E^-1 h in deflation]; the last block sets alpha.
@@ -899,7 +912,7 @@ __global__ void __launch_bounds__(kBlock, sweep_minb<T>())
     const int i = md.z + lane;
     const bool valid = lane < md.w;
     const T d = valid ? c.inv_d[i] : T(0);
-    const T raw = row_fma(c.Lv, md, lane, c.Y, valid ? c.r[i] : T(0));
+    const T raw = row_fma<T, true>(c.Lv, md, lane, c.Y, valid ? c.r[i] : T(0));
     if (valid) {
       const T yv = raw * d;
       acc[0] = fma(yv, yv, acc[0]);
@@ -962,7 +975,7 @@ __global__ void __launch_bounds__(kBlock, SCM == 0 ? sweep_minb<T>() : 1) k_bwd(
     const bool valid = lane < md.w;
     const T d = (valid && sweep) ? c.inv_d[i] : T(1);
     const T pold = (valid && !first) ? c.p[i] : T(0);
-    const T raw = row_fma(c.Uv, md, lane, c.Y, valid ? c.Y[i] : T(0));
+    const T raw = row_fma<T, true>(c.Uv, md, lane, c.Y, valid ? c.Y[i] : T(0));
     if (valid) {
       const T zic = sweep ? raw * d : raw;
       if (sweep) c.Y[i] = zic;
