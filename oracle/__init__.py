@@ -2,10 +2,12 @@
 
 TEST INFRASTRUCTURE ONLY. It is imported by ``tests/``, by the package smoke check and by
 the benchmark's CPU-baseline leg; the library's product path never touches it. It shares
-no code with the CUDA path: the Krylov iterations, IC(0) and the substitutions are plain
-C loops (``esd_oracle.c``); the auxiliary-matrix construction and the Lanczos estimate are
-plain NumPy/SciPy (library primitives as single steps: ``eigh``, ``cholesky``, sparse
-matvec, tridiagonal eigenvalues).
+no code with the CUDA path: the Krylov iterations, IC(0), the substitutions and the power
+method are plain C loops (``esd_oracle.c``); the auxiliary-matrix construction, the Lanczos
+estimate, the diagonal scaling and the adjoint chain rule are plain NumPy/SciPy (library
+primitives as single steps: ``eigh``, ``cholesky``, sparse matvec, tridiagonal
+eigenvalues). Any IC(0) factor can precondition a ``System``, so block-Jacobi IC is
+``System(A, IC0(block-diagonal part of A))``.
 
 Every function cites the passage of arXiv 2203.08498 it follows. Where the paper is silent
 the reading is stated in the docstring.
