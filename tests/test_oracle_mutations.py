@@ -61,6 +61,14 @@ MUTANTS = {
     "power_norm_not_rq": ("  orc_spmv(n, rp, ci, va, v, work);\n  return orc_dot(n, v, work);",
                           "  orc_spmv(n, rp, ci, va, v, work);\n  return sqrt(orc_dot(n, work, work));",
                           lambda: pins.test_power_method_diagonal_closed_form(1)),
+    # Appendix A: i_t summed without the alternating sign (schedule routine)
+    "sampling_a_sign": ("      it += (l % 2 == 0) ? q : -q;", "      it += q;",
+                        lambda: [pins.test_sampling_a_alternating_sign(*r)
+                                 for r in pins._golden_sampling("sampling_method_a_sign.txt")]),
+    # the same slip in the sampling step of the solve
+    "sampling_a_sign_in_solve": ("    it += (l % 2 == 0) ? q : -q;\n    q /= m;\n  }\n  int slot",
+                                 "    it += q;\n    q /= m;\n  }\n  int slot",
+                                 pins.test_sampling_a_in_solve_follows_the_alternating_sign),
     # residual update with the wrong sign
     "residual_sign": ("        r[k] -= alpha * q[k];", "        r[k] += alpha * q[k];",
                       pins.test_iccg_solves_the_system),

@@ -19,9 +19,9 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 # ---------------------------------------------------------------- sampling method A
 
-def _golden_sampling():
+def _golden_sampling(name="sampling_method_a.txt"):
     rows = []
-    for line in open(os.path.join(GOLDEN, "sampling_method_a.txt")):
+    for line in open(os.path.join(GOLDEN, name)):
         if line.strip() and not line.startswith("#"):
             v = [int(t) for t in line.split()]
             rows.append((v[0], v[1], v[2:]))
@@ -34,6 +34,45 @@ def test_sampling_a_worked_example(m, N, kept):
     for lmax in (None, 8, 12):  # any l_max with m^l_max > N_max gives the same schedule
         got = sorted(oracle.sampling_a_schedule(m, N, lmax).tolist())
         assert got == kept
+
+
+@pytest.mark.parametrize("m,N,kept", _golden_sampling("sampling_method_a_sign.txt"))
+def test_sampling_a_alternating_sign(m, N, kept):
+    """Appendix A, Algorithm alg1: i_t carries the alternating sign (-1)^l. The rows were
+    worked by hand from the algorithm for (m, N) where the signed and the unsigned sums
+    keep different iterations (the derivations are in the file's header)."""
+    for lmax in (None, 6, 9):
+        got = sorted(oracle.sampling_a_schedule(m, N, lmax).tolist())
+        assert got == kept
+
+
+def test_sampling_a_in_solve_follows_the_alternating_sign():
+    """The same rule inside the oracle's solve: a 3-slot sampled ICCG run keeps the
+    iterations the hand-checked schedule gives for its iteration count, which with m = 3
+    differ from the unsigned reading's."""
+    p = wl.config_c1()
+    out = oracle.System(p, oracle.IC0(p)).solve(p.source, tol=1e-8, sample_m=3)
+    N = out["iters"]
+    want = oracle.sampling_a_schedule(3, N, oracle.default_lmax(3, 20000))
+    assert sorted(out["sample_iter"].tolist()) == sorted(want.tolist())
+    unsigned = _unsigned_schedule(3, N)
+    assert sorted(unsigned) != sorted(want.tolist()), "choose a run where the readings differ"
+
+
+def _unsigned_schedule(m, N):
+    """Algorithm alg1 with every term of i_t added (the reading the sign rows exclude)."""
+    h, slots = 1, [0] * m
+    for i in range(1, N):
+        if i % h:
+            continue
+        it, q = 0, i - 1
+        while q:
+            it += q
+            q //= m
+        slots[it % m] = i
+        if i == h * m:
+            h *= 2
+    return slots
 
 
 def test_sampling_a_brute_force_properties():
