@@ -26,6 +26,7 @@ import scipy.sparse as sp
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "esd_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "_build", "libesd_oracle.so")
+_OMP_PATH = os.path.join(_HERE, "_build", "libesd_oracle_omp.so")
 _lib = None
 _lock = threading.Lock()
 
@@ -33,15 +34,18 @@ OK, ERR_NOT_SPD, ERR_BREAKDOWN, ERR_MAXIT, ERR_STATE = 0, -2, -3, -4, -5
 PLAIN, DEFLATION, SUBSPACE_CORRECTION = 0, 1, 2
 
 
-def build(force: bool = False) -> str:
+def build(force: bool = False, openmp: bool = False) -> str:
     """Compile the C oracle into ``oracle/_build``: -O2 with floating-point contraction off,
-    so every product is rounded before it is added and x86 and Arm builds agree bit for bit."""
-    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    so every product is rounded before it is added and x86 and Arm builds agree bit for bit.
+    ``openmp`` builds the all-core variant of the same source (identical results)."""
+    path = _OMP_PATH if openmp else _LIB_PATH
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+        tmp = path + f".{os.getpid()}.tmp"
+        extra = ["-fopenmp"] if openmp else []
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", *extra, "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, path)
+    return path
 
 
 class _System(C.Structure):
@@ -49,6 +53,7 @@ class _System(C.Structure):
         ("n", C.c_int), ("rp", C.c_void_p), ("ci", C.c_void_p), ("va", C.c_void_p),
         ("ncol", C.c_int), ("cp", C.c_void_p), ("precond", C.c_int),
         ("Lrp", C.c_void_p), ("Lci", C.c_void_p), ("Lva", C.c_void_p),
+        ("Urp", C.c_void_p), ("Uj", C.c_void_p), ("Ua", C.c_void_p),
         ("mode", C.c_int), ("m", C.c_int), ("W", C.c_void_p), ("AW", C.c_void_p),
         ("LE", C.c_void_p),
     ]
@@ -75,7 +80,9 @@ def load(path: str):
     L.orc_ic0.argtypes = [i32, vp, vp, vp, i32, vp, vp, vp, C.POINTER(f64)]
     L.orc_tril_nnz.restype = C.c_long
     L.orc_tril_nnz.argtypes = [i32, vp, vp]
-    L.orc_ic_apply.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, vp]
+    L.orc_ic_apply.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.orc_ic_transpose.restype = C.c_long
+    L.orc_ic_transpose.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp]
     L.orc_precond.argtypes = [C.POINTER(_System), vp, vp, vp]
     L.orc_solve.restype = i32
     L.orc_solve.argtypes = [C.POINTER(_System), vp, vp, C.POINTER(_SolveIO)]
@@ -91,6 +98,29 @@ def lib():
         if _lib is None:
             _lib = load(build())
     return _lib
+
+
+class using:
+    """``with oracle.using(openmp_lib()):`` routes every oracle call to that library."""
+
+    def __init__(self, library):
+        self.library = library
+
+    def __enter__(self):
+        global _lib
+        self.saved, _lib = lib(), self.library
+        return self.library
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
+
+
+def openmp_lib():
+    """The OpenMP build of the same oracle (bit-identical results), for timing on all host
+    cores; OMP_NUM_THREADS sets its threads."""
+    return load(build(openmp=True))
 
 
 def _p(a):
@@ -158,6 +188,12 @@ class IC0:
             raise ArithmeticError("IC(0) breakdown: matrix not SPD enough for the shift rule")
         self.shift = sh.value
         self.colour_ptr = _c(prob.colour_ptr, np.int32)
+        # column index of L for the backward sweep (later colours first, rows ascending)
+        self.Urp = np.zeros(prob.n + 1, dtype=np.int32)
+        self.Uj = np.zeros(max(nl - prob.n, 1), dtype=np.int32)
+        self.Ua = np.zeros(max(nl - prob.n, 1), dtype=np.int32)
+        lib().orc_ic_transpose(prob.n, len(self.colour_ptr) - 1, _p(self.colour_ptr), _p(self.Lrp), _p(self.Lci),
+                               _p(self.Urp), _p(self.Uj), _p(self.Ua))
 
     def dense_L(self):
         return sp.csr_matrix((self.Lva, self.Lci, self.Lrp), shape=(self.n, self.n)).toarray()
@@ -168,7 +204,7 @@ class IC0:
         z = np.empty(self.n)
         y = np.empty(self.n)
         lib().orc_ic_apply(self.n, len(self.colour_ptr) - 1, _p(self.colour_ptr), _p(self.Lrp),
-                           _p(self.Lci), _p(self.Lva), _p(r), _p(z), _p(y))
+                           _p(self.Lci), _p(self.Lva), _p(self.Urp), _p(self.Uj), _p(self.Ua), _p(r), _p(z), _p(y))
         return z
 
 
@@ -280,6 +316,7 @@ class System:
         s.precond = 1 if ic is not None else 0
         if ic is not None:
             s.Lrp, s.Lci, s.Lva = _p(ic.Lrp), _p(ic.Lci), _p(ic.Lva)
+            s.Urp, s.Uj, s.Ua = _p(ic.Urp), _p(ic.Uj), _p(ic.Ua)
         s.mode = mode
         if aux is not None:
             s.m, s.W, s.AW, s.LE = aux.m, _p(aux.W), _p(aux.AW), _p(aux.LE)

@@ -3,7 +3,11 @@
  * (arXiv 2203.08498). TEST INFRASTRUCTURE ONLY: tests, the package smoke check and the
  * benchmark's CPU-baseline leg call it; the library never does.
  *
- * Plain, single-threaded, FP64 C loops written from the paper's definitions:
+ * Plain FP64 C loops written from the paper's definitions, single-threaded as built for the
+ * tests. The same source built with OpenMP (the benchmark's all-core timing, in the paper's
+ * C/OpenMP style) shares among threads the rows of one colour in the substitutions and the
+ * elements of the SpMV and vector loops; the dot products stay serial pairwise sums, so both
+ * builds give bit-identical results:
  *   - IC(0) on the pattern of tril(A) (preconditioner M = L L^T, Section 4.4 / 5.3);
  *   - forward / backward substitution taken colour by colour in the given order;
  *   - PCG as in Algorithm "PCG with condition number estimation" (without the power
@@ -47,6 +51,7 @@ double orc_dot(long n, const double* x, const double* y) { return pairwise_dot(x
 
 /* y = A x for CSR A */
 void orc_spmv(int n, const int* rp, const int* ci, const double* va, const double* x, double* y) {
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i) {
     double s = 0.0;
     for (int k = rp[i]; k < rp[i + 1]; ++k) s += va[k] * x[ci[k]];
@@ -161,33 +166,55 @@ int orc_ic0(int n, const int* rp, const int* ci, const double* va, int max_tries
   return ORC_ERR_NOT_SPD;
 }
 
+/* Transposed index of the strict part of L for the backward sweep: for every row k, the
+ * entries a with Lci[a] = k (so Lva[a] = l_jk for the row j owning a), ordered by the colour
+ * of j descending and then by j ascending. Urp: n+1 row pointers; Uj[e]: the row j; Ua[e]:
+ * the entry a. Returns the number of entries (the strict lower count). */
+long orc_ic_transpose(int n, int ncol, const int* cp, const int* Lrp, const int* Lci, int* Urp, int* Uj, int* Ua) {
+  for (int k = 0; k <= n; ++k) Urp[k] = 0;
+  for (int j = 0; j < n; ++j)
+    for (int a = Lrp[j]; a < Lrp[j + 1] - 1; ++a) Urp[Lci[a] + 1] += 1;
+  for (int k = 0; k < n; ++k) Urp[k + 1] += Urp[k];
+  int* fill = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+  for (int k = 0; k < n; ++k) fill[k] = Urp[k];
+  for (int c = ncol - 1; c >= 0; --c)
+    for (int j = cp[c]; j < cp[c + 1]; ++j)
+      for (int a = Lrp[j]; a < Lrp[j + 1] - 1; ++a) {
+        const int k = Lci[a];
+        Uj[fill[k]] = j;
+        Ua[fill[k]] = a;
+        fill[k] += 1;
+      }
+  free(fill);
+  return Urp[n];
+}
+
 /* z = (L L^T)^{-1} r. Forward: for colour c = 0..C-1, every row i of colour c:
  *   y_i = (r_i - sum_{k<i} l_ik y_k) / l_ii.
  * Backward: for colour c = C-1..0, every row i of colour c:
  *   z_i = (y_i - sum_{j>i} l_ji z_j) / l_ii,
- * the sum taken over column i of L. It is formed by subtraction: once the z_j of a colour are
- * final, each l_ji z_j is subtracted from the running right-hand side of row i < j. No two
- * rows of one colour are coupled, so inside a colour the order does not matter.
- * y is used as that running right-hand side and is overwritten. */
+ * the sum taken over column i of L (the transposed index of orc_ic_transpose), its terms
+ * subtracted one by one from y_i with the later colours first and, within a colour, the rows
+ * in ascending order. No two rows of one colour are coupled, so the rows of a colour are
+ * independent: with OpenMP they are shared among threads, which changes no result. */
 void orc_ic_apply(int n, int ncol, const int* cp, const int* Lrp, const int* Lci, const double* Lva,
-                  const double* r, double* z, double* y) {
+                  const int* Urp, const int* Uj, const int* Ua, const double* r, double* z, double* y) {
   (void)n;
-  for (int c = 0; c < ncol; ++c)
+  for (int c = 0; c < ncol; ++c) {
+#pragma omp parallel for schedule(static)
     for (int i = cp[c]; i < cp[c + 1]; ++i) {
       double s = r[i];
       int e = Lrp[i + 1] - 1;
       for (int a = Lrp[i]; a < e; ++a) s -= Lva[a] * y[Lci[a]];
       y[i] = s / Lva[e];
     }
-  double* t = y;
+  }
   for (int c = ncol - 1; c >= 0; --c) {
-    for (int j = cp[c]; j < cp[c + 1]; ++j) {
-      int e = Lrp[j + 1] - 1;
-      z[j] = t[j] / Lva[e];
-    }
-    for (int j = cp[c]; j < cp[c + 1]; ++j) {
-      int e = Lrp[j + 1] - 1;
-      for (int a = Lrp[j]; a < e; ++a) t[Lci[a]] -= Lva[a] * z[j];
+#pragma omp parallel for schedule(static)
+    for (int i = cp[c]; i < cp[c + 1]; ++i) {
+      double s = y[i];
+      for (int e = Urp[i]; e < Urp[i + 1]; ++e) s -= Lva[Ua[e]] * z[Uj[e]];
+      z[i] = s / Lva[Lrp[i + 1] - 1];
     }
   }
 }
@@ -210,11 +237,13 @@ static void chol_solve(int m, const double* LE, const double* f, double* u) {
 
 /* out[k] = sum_i X[i + k n] v[i] for an n x m column-major X */
 static void tall_t_vec(long n, int m, const double* X, const double* v, double* out) {
+#pragma omp parallel for schedule(static)
   for (int k = 0; k < m; ++k) out[k] = pairwise_dot(X + (long)k * n, v, n);
 }
 
 /* y += sign * X u */
 static void tall_vec_acc(long n, int m, const double* X, const double* u, double sign, double* y) {
+#pragma omp parallel for schedule(static)
   for (long i = 0; i < n; ++i) {
     double s = 0.0;
     for (int k = 0; k < m; ++k) s += X[i + (long)k * n] * u[k];
@@ -235,6 +264,9 @@ typedef struct {
   const int* Lrp;
   const int* Lci;
   const double* Lva;
+  const int* Urp; /* transposed index of L (orc_ic_transpose) */
+  const int* Uj;
+  const int* Ua;
   int mode; /* 0 plain, 1 deflation, 2 subspace correction */
   int m;
   const double* W;  /* n x m column-major */
@@ -263,7 +295,7 @@ typedef struct {
 void orc_precond(const orc_system* s, const double* r, double* z, double* work) {
   int n = s->n;
   if (s->precond == 1)
-    orc_ic_apply(n, s->ncol, s->cp, s->Lrp, s->Lci, s->Lva, r, z, work);
+    orc_ic_apply(n, s->ncol, s->cp, s->Lrp, s->Lci, s->Lva, s->Urp, s->Uj, s->Ua, r, z, work);
   else
     memcpy(z, r, sizeof(double) * n);
   if (s->mode == 2 && s->m > 0) {
@@ -365,6 +397,7 @@ int orc_solve(const orc_system* s, const double* b, double* x, orc_solve_io* io)
   }
   /* r0 = b - A x0 (deflation: r0 = P^T (b - A x0)) */
   orc_spmv(n, s->rp, s->ci, s->va, x, q);
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i) r[i] = b[i] - q[i];
   if (s->mode == 1) apply_PT(s, r);
   double rn = sqrt(orc_dot(n, r, r));
@@ -380,6 +413,7 @@ int orc_solve(const orc_system* s, const double* b, double* x, orc_solve_io* io)
       } else {
         double beta = rho / rho_old;
         if (io->beta_hist) io->beta_hist[i - 2] = beta;
+#pragma omp parallel for schedule(static)
         for (int k = 0; k < n; ++k) p[k] = z[k] + beta * p[k];
       }
       orc_spmv(n, s->rp, s->ci, s->va, p, q);
@@ -392,6 +426,7 @@ int orc_solve(const orc_system* s, const double* b, double* x, orc_solve_io* io)
       }
       double alpha = rho / pq;
       if (io->alpha_hist) io->alpha_hist[i - 1] = alpha;
+#pragma omp parallel for schedule(static)
       for (int k = 0; k < n; ++k) {
         x[k] += alpha * p[k];
         r[k] -= alpha * q[k];

@@ -36,12 +36,14 @@ MUTANTS = {
     "ic0_pivot": ("    for (int a = Lrp[i]; a < row_end; ++a) d -= Lva[a] * Lva[a];", "",
                   pins.test_ic0_is_exact_cholesky_on_full_pattern),
     # forward substitution in the reverse colour order
-    "fwd_colour_order": ("  for (int c = 0; c < ncol; ++c)\n    for (int i = cp[c]; i < cp[c + 1]; ++i) {",
-                         "  for (int c = ncol - 1; c >= 0; --c)\n    for (int i = cp[c]; i < cp[c + 1]; ++i) {",
+    "fwd_colour_order": ("  for (int c = 0; c < ncol; ++c) {\n#pragma omp parallel for schedule(static)\n"
+                         "    for (int i = cp[c]; i < cp[c + 1]; ++i) {\n      double s = r[i];",
+                         "  for (int c = ncol - 1; c >= 0; --c) {\n#pragma omp parallel for schedule(static)\n"
+                         "    for (int i = cp[c]; i < cp[c + 1]; ++i) {\n      double s = r[i];",
                          lambda: pins.test_ic_apply_is_M_inverse("c1")),
     # backward substitution with L instead of L^T (row i's own entries)
-    "bwd_transposed": ("      for (int a = Lrp[j]; a < e; ++a) t[Lci[a]] -= Lva[a] * z[j];",
-                       "      for (int a = Lrp[j]; a < e; ++a) t[j] -= Lva[a] * z[Lci[a]];",
+    "bwd_transposed": ("      for (int e = Urp[i]; e < Urp[i + 1]; ++e) s -= Lva[Ua[e]] * z[Uj[e]];",
+                       "      for (int a = Lrp[i]; a < Lrp[i + 1] - 1; ++a) s -= Lva[a] * z[Lci[a]];",
                        lambda: pins.test_ic_apply_is_M_inverse("small3d")),
     # subspace correction subtracted instead of added (Eq. mc)
     "sc_sign": ("    tall_vec_acc(n, s->m, s->W, u, 1.0, z);", "    tall_vec_acc(n, s->m, s->W, u, -1.0, z);",
