@@ -110,6 +110,17 @@ void launch_lanczos_extremes(const double* a, const double* b, int k, double* sc
 
 using namespace esd;
 
+// True when p is device (or managed) memory that the given device can address as its own.
+static bool on_device(const void* p, int dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
 extern "C" int esd_lanczos_extremes_noalloc(const double* alpha, const double* beta, int32_t k, double* out,
                                             void* stream) {
   try {
@@ -119,6 +130,11 @@ extern "C" int esd_lanczos_extremes_noalloc(const double* alpha, const double* b
     int dev = 0;
     ESD_CUDA(cudaGetDevice(&dev));
     ESD_CHECK(dev >= 0 && dev < kMaxDevices, ESD_ERR_INVALID, "device ordinal out of range");
+    // The kernel reads alpha and beta and writes out directly: each must be memory of the
+    // current device (a host array would be read through a host address on the GPU).
+    ESD_CHECK(on_device(alpha, dev), ESD_ERR_INVALID, "alpha is not device memory of the current device");
+    ESD_CHECK(k == 1 || on_device(beta, dev), ESD_ERR_INVALID, "beta is not device memory of the current device");
+    ESD_CHECK(on_device(out, dev), ESD_ERR_INVALID, "out is not device memory of the current device");
     double* scratch = nullptr;
     {
       std::lock_guard<std::mutex> lock(g_scratch_mutex);
