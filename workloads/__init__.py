@@ -29,7 +29,7 @@ import scipy.sparse as sp
 __all__ = [
     "Problem", "fv_diffusion", "square_inclusions", "sphere_inclusions",
     "gaussian_source", "smooth_gaussian_field", "config_c1", "config_c2", "config_c4",
-    "small_3d", "random_spd_dense", "laplacian_1d", "laplacian_2d", "csr_of_dense",
+    "small_3d", "random_spd_dense", "laplacian_1d", "ic0_breakdown_spd", "laplacian_2d", "csr_of_dense",
     "random_rhs", "SEED_BASE", "reorder", "wavefront_colours", "block_ids", "block_wavefront_colours",
     "block_diagonal_part",
 ]
@@ -433,6 +433,19 @@ def csr_of_dense(a: np.ndarray, ncolours: int = 1) -> Problem:
     cp = np.linspace(0, n, ncolours + 1).astype(np.int32)
     return Problem(n=n, rowptr=m.indptr.astype(np.int32), colind=m.indices.astype(np.int32),
                    val=m.data.astype(np.float64), colour_ptr=cp, perm=np.arange(n))
+
+
+def ic0_breakdown_spd(n: int = 24, seed: int = 7, margin: float = 1e-3) -> Problem:
+    """A sparse SPD matrix that is not an M-matrix (off-diagonal entries of both signs, about
+    15 % density), shifted so that its smallest eigenvalue is ``margin``; one row per colour.
+    With the defaults IC(0) of A meets a non-positive pivot and succeeds on A + s diag(A)
+    only from s = 8e-3."""
+    rng = np.random.default_rng(seed)
+    b = sp.random(n, n, density=0.15, random_state=rng, data_rvs=lambda k: rng.uniform(-1, 1, k)).toarray()
+    s = b + b.T
+    np.fill_diagonal(s, 0.0)
+    a = s + np.eye(n) * (margin - np.linalg.eigvalsh(s).min())
+    return csr_of_dense(a, ncolours=n)
 
 
 def laplacian_1d(n: int) -> Problem:
