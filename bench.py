@@ -1,30 +1,32 @@
 #!/usr/bin/env python3
 """Benchmark of the hot path.
 
-Headline (default, --config c2): 3D 7-point finite-volume diffusion on a 128^3 grid
-(n = 2,097,152, nnz = 14,581,760), background coefficient 1 and 16 seeded balls of radius
-4-8 cells with coefficient 1e5, Dirichlet boundaries, 8-colour ordering, FP64 CSR; a
-backward-Euler sequence of 20 systems b_t = x_{t-1}/dt + Gaussian source (dt = 1e-3,
-x_0 = 0); IC(0)-PCG to relative residual 1e-8; W from m = 16 error vectors sampled
-(method A) during system 1; systems 2..20 deflated.
+Headline (default, --config c5): 3D 7-point finite-volume diffusion on a 256^3 grid
+(n = 16,777,216, nnz = 117,047,296), background coefficient 1 and 64 seeded balls of radius
+8-16 cells with coefficient 1e6, Dirichlet boundaries, 8-colour ordering; a backward-Euler
+sequence b_t = x_{t-1}/dt + Gaussian source (dt = 1e-3, x_0 = 0), every forward solve followed
+by its adjoint A lambda = 2 (x_t - x_target); the precision form (FP32 inner IC(0)-PCG inside
+FP64 iterative refinement) to a true FP64 residual of 1e-8; W from m = 32 error vectors
+sampled (method A) during system 1.
 
-One step = one whole sequence: IC(0) factorisation, system 1 with sampling, the W build
-(CholeskyQR2, AW, E, E^-1), the Lanczos condition estimate, systems 2..20 in the selected
-mode, with the backward-Euler right-hand sides formed on the device. value = systems solved
-per second (all ranks). Inputs are resident in HBM when the timed region starts; the
-working set is larger than L2, so no flush is needed between steps.
+One step = one system of the sequence: the right-hand side on the device, the forward solve,
+the adjoint right-hand side and the adjoint solve. x, lambda and W carry over from step to
+step; the first warm-up step is system 1 (sampling and the W build). value = solves per
+second (forward and adjoint solves, all ranks). The mode is the fastest correct one on this
+workload (plain: on this 7-point operator the W terms cost more per iteration than the
+iterations they save, Eq. ganma); deflation and subspace correction with the same W, and
+plain FP64 PCG resumed until its true residual meets the tolerance, are timed beside it on
+two more systems of the same sequence. Inputs are resident in HBM when the timed region
+starts; the working set is larger than L2, so no flush is needed between steps.
 
-Other workloads (--config): c3 = 192^3 27-point anisotropic log-normal Q1 FE, 10 systems
-to 1e-10 in the precision form (FP32 inner PCG in FP64 refinement), deflation m = 24;
-c4 = 128^3 log-normal exp(theta) diffusion, one optimisation step (theta update, device
-assembly, IC(0), forward and adjoint solve through the autograd API), deflation m = 16;
-c5 = 256^3 7-point with 64 balls of 1e6, 50 systems in the precision form, deflation
-m = 32, each forward solve followed by its adjoint. Each reports plain FP64 PCG on the
-same work beside it.
+Other workloads (--config): c2 = the 128^3 sequence of 20 systems in FP64 (one step = the
+whole sequence), c3 = 192^3 27-point anisotropic log-normal Q1 FE, 10 systems to 1e-10 in
+the precision form with deflation m = 24, c4 = 128^3 log-normal exp(theta) diffusion, one
+optimisation step through the autograd API, c1 = the 64 x 64 five-system sequence.
 
---impl reference times the CPU oracle (the FP64 C restatement of the method) on the
-headline workload, a bounded number of iterations per step, extrapolated to solves per
-second.
+--impl reference times the CPU oracle (the FP64 C restatement of the method) on the same
+workload: a bounded number of iterations per step, extrapolated to solves per second with
+the oracle's own iteration counts.
 """
 from __future__ import annotations
 
@@ -53,25 +55,30 @@ L2_BYTES = 129e6
 # whether every forward solve is followed by its adjoint solve.
 CONFIGS = {
     # 64 x 64 5-point, 4 squares of 1e3, red-black: tiny, L2-resident, latency-bound
-    "c1": dict(grid=64, systems=5, m=8, tol=1e-8, mode="deflation", precision="fp64", adjoint=False),
+    "c1": dict(grid=64, systems=5, m=8, tol=1e-8, mode="deflation", precision="fp64", adjoint=False,
+               mtilde=None, inner_tol=0.1),
     # 128^3 7-point, 16 balls of 1e5: the headline sequence
-    "c2": dict(grid=128, systems=20, m=16, tol=1e-8, mode="deflation", precision="fp64", adjoint=False),
+    "c2": dict(grid=128, systems=20, m=16, tol=1e-8, mode="deflation", precision="fp64", adjoint=False,
+               mtilde=None, inner_tol=0.1),
     # 192^3 27-point anisotropic log-normal FE: the precision form to 1e-10
-    "c3": dict(grid=192, systems=10, m=24, tol=1e-10, mode="deflation", precision="fp32", adjoint=False),
+    "c3": dict(grid=192, systems=10, m=24, tol=1e-10, mode="deflation", precision="fp32", adjoint=False,
+               mtilde=None, inner_tol=0.1),
     # 128^3 log-normal exp(theta): one optimisation step = theta update + forward + adjoint
-    "c4": dict(grid=128, systems=1, m=16, tol=1e-8, mode="deflation", precision="fp64", adjoint=True),
+    "c4": dict(grid=128, systems=1, m=16, tol=1e-8, mode="deflation", precision="fp64", adjoint=True,
+               mtilde=None, inner_tol=0.1),
     # 256^3 7-point, 64 balls of 1e6: precision form, each forward solve with its adjoint
-    "c5": dict(grid=256, systems=50, m=32, tol=1e-8, mode="deflation", precision="fp32", adjoint=True),
+    "c5": dict(grid=256, systems=50, m=32, tol=1e-8, mode="plain", precision="fp32", adjoint=True,
+               mtilde=None, inner_tol=0.1),
 }
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="esdcg", choices=["esdcg", "reference"])
-    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
+    ap.add_argument("--config", default="c5", choices=sorted(CONFIGS))
     ap.add_argument("--mode", default=None, choices=["plain", "deflation", "sc"])
     ap.add_argument("--grid", type=int, default=None)
     ap.add_argument("--systems", type=int, default=None)
@@ -79,6 +86,10 @@ def parse():
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32"],
                     help="fp32: FP32 inner PCG inside FP64 iterative refinement")
+    ap.add_argument("--mtilde", type=int, default=None,
+                    help="keep the Ritz vectors of the k smallest Ritz values of the sampled W (theta filter)")
+    ap.add_argument("--inner-tol", dest="inner_tol", type=float, default=None,
+                    help="residual reduction of each FP32 inner solve in the refinement form")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, comparison modes and CPU baseline")
     a = ap.parse_args()
     for k, v in CONFIGS[a.config].items():
@@ -240,6 +251,8 @@ def gpu_arm(args):
         dist.init_process_group("nccl", device_id=dev)
     if args.config == "c4":
         return c4_arm(args, esd, torch, dev, ws, rank)
+    if args.config == "c5":
+        return system_arm(args, esd, torch, dev, ws, rank)
     p = workload(args)
     n, nnz = p.n, p.nnz
     modes_map = {"plain": esd.PLAIN, "deflation": esd.DEFLATION, "sc": esd.SUBSPACE_CORRECTION}
@@ -465,6 +478,277 @@ def gpu_arm(args):
     return result, modes
 
 
+def build_w(S, args):
+    """W from the sampled solve: all m columns (theta = inf), or with --mtilde k the Ritz
+    vectors of the k smallest Ritz values (theta between the k-th and (k+1)-th, Eq. bk)."""
+    kept = S.sample_and_build_W()
+    if args.mtilde and args.mtilde < kept:
+        r = np.sort(S.ritz_values())
+        kept = S.sample_and_build_W(0.5 * (r[args.mtilde - 1] + r[args.mtilde]))
+    return kept
+
+
+def system_arm(args, esd, torch, dev, ws, rank):
+    """One step = one system of the backward-Euler sequence: b_t = x_{t-1}/dt + s on the
+    device, the forward solve in the configured mode, then its adjoint A lambda = 2 (x_t -
+    x_target) (warm-started from lambda_{t-1}). x, lambda and W carry over from step to step;
+    the first warm-up step is system 1 (the sampling solve and the W build), so the timed
+    steps are later systems of the same sequence (continuing past its 50 systems when more
+    steps are asked for). After the timed steps, two more systems are solved once more in the
+    same mode and by plain FP64 PCG from the same b_t and x_{t-1}, timed per solve; the FP64
+    comparator is resumed (esd_solve again from its own x) until its true residual
+    ||b - A x|| / ||b|| recomputed in FP64 meets the tolerance."""
+    p = workload(args)
+    n = p.n
+    modes_map = {"plain": esd.PLAIN, "deflation": esd.DEFLATION, "sc": esd.SUBSPACE_CORRECTION}
+    mode = modes_map[args.mode]
+    fp32 = args.precision == "fp32"
+    A = esd.Matrix.from_problem(p)
+    A.factor_ic0()
+    S = esd.Solver(A, maxit_cap=20000, sample_cap=max(args.m, 2), precision=esd.FP32_REFINE if fp32 else esd.FP64,
+                   inner_tol=args.inner_tol)
+    src = torch.from_numpy(p.source).to(dev)
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    b = torch.empty_like(x)
+    xt = np.random.default_rng(20220316 + 7).standard_normal(n) * float(np.abs(p.source).max()) * 1e-3
+    neg2xt = torch.from_numpy(-2.0 * xt).to(dev)
+    lam = torch.zeros_like(x)
+    g = torch.empty_like(x)
+    inv_dt = 1.0 / p.dt
+    info = A.info()
+    state = {"t": 0, "kept": 0, "cond": None}
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def one_system(marks=None, save=None):
+        """Forward and adjoint solve of the next system; marks: 3 events (start, after the
+        forward solve, after the adjoint); save: dict receiving copies of b, x_{t-1}, g and
+        lambda_{t-1} (outside any timed region)."""
+        t = state["t"]
+        state["t"] += 1
+        if marks:
+            marks[0].record()
+        S.backward_euler_rhs(x, src, inv_dt, b)
+        if save is not None:
+            save.update(b=b.clone(), x0=x.clone())
+        if t == 0:
+            # system 1 samples m iterates in any mode, so that W exists for the accelerated
+            # modes (this one, or the ones compared beside it)
+            S.set_mode(esd.PLAIN)
+            st, it, rr = S.solve(b, x, args.tol, 20000, args.m)
+            state["cond"] = S.estimate_cond()
+            state["kept"] = build_w(S, args)
+            S.set_mode(mode)
+        else:
+            st, it, rr = S.solve(b, x, args.tol, 20000, 0)
+        fwd = S.last_solve_info()
+        if st != esd.OK:
+            raise RuntimeError(f"solve of system {t + 1} returned {st}")
+        if marks:
+            marks[1].record()
+        S.backward_euler_rhs(x, neg2xt, 2.0, g)
+        if save is not None:
+            save.update(g=g.clone(), lam0=lam.clone())
+        st, ita, rr = S.solve(g, lam, args.tol, 20000, 0)
+        adj = S.last_solve_info()
+        if st != esd.OK:
+            raise RuntimeError(f"adjoint solve of system {t + 1} returned {st}")
+        if marks:
+            marks[2].record()
+        return {"system": t + 1, "iters": it, "adjoint_iters": ita, "outer": fwd["outer_steps"],
+                "adjoint_outer": adj["outer_steps"], "true_relres": fwd["true_relres"],
+                "adjoint_true_relres": adj["true_relres"], "restarts": fwd["restarts"] + adj["restarts"]}
+
+    for _ in range(args.warmup):
+        one_system()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(dev.index if dev.index is not None else 0)
+    marks = [[ev(), ev(), ev()] for _ in range(args.steps)]
+    t0 = time.perf_counter()
+    rows = [one_system(marks[k]) for k in range(args.steps)]
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    ms = max_over_ranks(marks[0][0].elapsed_time(marks[-1][2]), dev)
+    fwd_ms = [mk[0].elapsed_time(mk[1]) for mk in marks]
+    adj_ms = [mk[1].elapsed_time(mk[2]) for mk in marks]
+    value = 2 * args.steps * ws / (ms / 1e3)
+    ms_step = ms / args.steps
+
+    launches = 0
+    for r in rows:
+        launches += 2  # right-hand sides
+        launches += launch_count(info, args.mode, args.m, fp32, [r["iters"], r["adjoint_iters"]],
+                                 [r["outer"], r["adjoint_outer"]])
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if not fp32 else "f32 inner, f64 refinement", "data": "synthetic",
+        "config": {"workload": workload_name(args, p), "config": args.config, "grid": args.grid, "n": n,
+                   "nnz": p.nnz, "systems_in_sequence": args.systems,
+                   "step": "one system of the sequence: forward solve + adjoint solve",
+                   "m": args.m, "m_kept": state["kept"], "mode": args.mode, "tol": args.tol,
+                   "precision": args.precision, "inner_tol": args.inner_tol if fp32 else None,
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (matrix, factor, W and vectors > 129 MB)"},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "wall_s_timed": wall,
+        "time_to_tol_ms_per_system": {"forward": float(np.mean(fwd_ms)), "adjoint": float(np.mean(adj_ms)),
+                                      "per_solve": ms_step / 2},
+        "systems": [r["system"] for r in rows],
+        "iterations": [r["iters"] for r in rows],
+        "adjoint_iterations": [r["adjoint_iters"] for r in rows],
+        "refinement_steps": [r["outer"] for r in rows] if fp32 else None,
+        "true_relres_max": max(max(r["true_relres"], r["adjoint_true_relres"]) for r in rows),
+        "cond_estimate_system1": {"lmin": state["cond"][0], "lmax": state["cond"][1], "kappa": state["cond"][2]}
+        if state["cond"] else None,
+    }
+    if rank != 0 or args.no_extras:
+        return result, None
+
+    # roofline of the dominant kernel from live per-kernel times of the same kernels
+    S.set_mode(mode)
+    prof = S.profile_iterations(b, x.clone(), reps=10)
+    peaks = read_peaks()
+    result["roofline"], result["kernel_times_ms"] = roofline(prof, p, args, mode, esd, peaks)
+
+    # the next two systems: this mode (advancing the sequence), then from the same b_t and
+    # x_{t-1} (and g_t, lambda_{t-1}) the other modes of this precision form with the same W,
+    # and plain FP64 PCG resumed until its true residual meets the tolerance
+    S64 = esd.Solver(A, maxit_cap=20000, sample_cap=0)
+    S64.solve(b, x.clone(), args.tol, 20000, 0)  # graph capture
+    others = [k for k in ("plain", "deflation", "sc") if k != args.mode]
+    for name in others:  # graph capture of the other modes
+        S.set_mode(modes_map[name])
+        S.solve(b, x.clone(), args.tol, 20000, 0)
+    S.set_mode(mode)
+
+    def timed_solve(solver, bv, x0):
+        xv = x0.clone()
+        e0, e1 = ev(), ev()
+        torch.cuda.synchronize()
+        e0.record()
+        st, its, rr = solver.solve(bv, xv, args.tol, 20000, 0)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), its, solver.last_solve_info()
+
+    cmp_rows = []
+    for _ in range(2):
+        saved = {}
+        mk = [ev(), ev(), ev()]
+        r = one_system(mk, save=saved)
+        torch.cuda.synchronize()
+        row = {"system": r["system"], "this": {"forward_ms": mk[0].elapsed_time(mk[1]),
+                                               "adjoint_ms": mk[1].elapsed_time(mk[2]),
+                                               "iters": r["iters"], "adjoint_iters": r["adjoint_iters"],
+                                               "true_relres": r["true_relres"],
+                                               "adjoint_true_relres": r["adjoint_true_relres"]}}
+        for name in others:
+            S.set_mode(modes_map[name])
+            fms, fit, finfo = timed_solve(S, saved["b"], saved["x0"])
+            ams, ait, ainfo = timed_solve(S, saved["g"], saved["lam0"])
+            row[name] = {"forward_ms": fms, "adjoint_ms": ams, "iters": fit, "adjoint_iters": ait,
+                         "true_relres": max(finfo["true_relres"], ainfo["true_relres"])}
+        S.set_mode(mode)
+        for name, bv, x0 in (("forward", saved["b"], saved["x0"]), ("adjoint", saved["g"], saved["lam0"])):
+            xv = x0.clone()
+            e0, e1 = ev(), ev()
+            torch.cuda.synchronize()
+            e0.record()
+            st, its, rr = S64.solve(bv, xv, args.tol, 20000, 0)
+            first_true = S64.true_relres()
+            resumed = 0
+            while S64.true_relres() > args.tol and resumed < 10:
+                st, it2, rr = S64.solve(bv, xv, args.tol, 20000, 0)
+                its += it2
+                resumed += 1
+            e1.record()
+            torch.cuda.synchronize()
+            row["fp64_plain_" + name] = {"ms": e0.elapsed_time(e1), "iters": its, "resumed": resumed,
+                                         "true_relres_first_stop": first_true, "true_relres": S64.true_relres()}
+        cmp_rows.append(row)
+    this_ms = float(np.mean([c["this"]["forward_ms"] + c["this"]["adjoint_ms"] for c in cmp_rows]))
+    f64_ms = float(np.mean([c["fp64_plain_forward"]["ms"] + c["fp64_plain_adjoint"]["ms"] for c in cmp_rows]))
+    result["vs_fp64_plain"] = {"systems": cmp_rows, "ms_per_system_this": this_ms / 2,
+                               "ms_per_system_fp64_plain_to_true_tol": f64_ms / 2,
+                               "speedup_vs_fp64_plain": f64_ms / this_ms}
+    # every mode of this precision form on the same systems (W from m samples of system 1)
+    modes_out = {args.mode: {"ms_per_solve": this_ms / 2,
+                             "iters_per_solve": float(np.mean([(c["this"]["iters"] + c["this"]["adjoint_iters"]) / 2
+                                                               for c in cmp_rows]))}}
+    for name in others:
+        ms_o = float(np.mean([c[name]["forward_ms"] + c[name]["adjoint_ms"] for c in cmp_rows]))
+        modes_out[name] = {"ms_per_solve": ms_o / 2,
+                           "iters_per_solve": float(np.mean([(c[name]["iters"] + c[name]["adjoint_iters"]) / 2
+                                                             for c in cmp_rows]))}
+    base = modes_out["plain"]
+    for name, v in modes_out.items():
+        v["speedup_vs_fp64_plain"] = (f64_ms / 2) / v["ms_per_solve"]
+        v["ms_per_iter"] = v["ms_per_solve"] / v["iters_per_solve"]
+        if name != "plain":
+            # Eq. ganma: an accelerated mode wins when its iteration cut exceeds its cost ratio
+            v["gamma_measured"] = v["ms_per_iter"] / base["ms_per_iter"]
+            v["iteration_ratio"] = v["iters_per_solve"] / base["iters_per_solve"]
+    result["modes"] = {"m_kept": state["kept"], "by_mode": modes_out,
+                       "fastest": min(modes_out, key=lambda k: modes_out[k]["ms_per_solve"])}
+    # HBM GB/s per iteration on the paper's byte model: this form against plain FP64
+    s_in = 4 if fp32 else 8
+    m_eff = state["kept"] if mode != esd.PLAIN else 0
+    model_this = 2 * (s_in + 4) * p.nnz + (4 + 12 * s_in) * n + (2 * s_in * m_eff * n + 2 * s_in * n if m_eff else 0)
+    model_f64 = 24 * p.nnz + 100 * n
+    it_this = np.mean([c["this"]["iters"] + c["this"]["adjoint_iters"] for c in cmp_rows])
+    it_f64 = np.mean([c["fp64_plain_forward"]["iters"] + c["fp64_plain_adjoint"]["iters"] for c in cmp_rows])
+    result["iteration_bandwidth"] = {
+        "this": {"model_bytes_per_iter": model_this, "ms_per_iter": this_ms / it_this,
+                 "model_gbs": model_this / (this_ms / it_this / 1e3) / 1e9},
+        "fp64_plain": {"model_bytes_per_iter": model_f64, "ms_per_iter": f64_ms / it_f64,
+                       "model_gbs": model_f64 / (f64_ms / it_f64 / 1e3) / 1e9},
+        "peak_gbs": peaks["hbm_gbs"], "peak_src": peaks["src"]}
+    result["e2e"] = system_e2e(esd, p, args, torch, S, x, lam, src, neg2xt)
+    return result, None
+
+
+def system_e2e(esd, p, args, torch, S, x, lam, src, neg2xt):
+    """The same step through the C ABI with host buffers: the right-hand sides and both
+    solves take pinned host arrays, so every system's inputs go in and its results come
+    back inside the timed region (the library stages the copies)."""
+    pin = lambda t: t.cpu().pin_memory()  # noqa: E731
+    x_h, lam_h, src_h, n2_h = pin(x), pin(lam), pin(src), pin(neg2xt)
+    b_h = torch.zeros(p.n, dtype=torch.float64).pin_memory()
+    g_h = torch.zeros_like(b_h).pin_memory()
+    inv_dt = 1.0 / p.dt
+
+    def step():
+        S.backward_euler_rhs(x_h, src_h, inv_dt, b_h)
+        S.solve(b_h, x_h, args.tol, 20000, 0)
+        S.backward_euler_rhs(x_h, n2_h, 2.0, g_h)
+        S.solve(g_h, lam_h, args.tol, 20000, 0)
+
+    step()
+    torch.cuda.synchronize()
+    k = 3
+    t0 = time.perf_counter()
+    for _ in range(k):
+        step()
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    n = p.n
+    # rhs: x_prev, s in, b out; solve: b, x in, x out; adjoint rhs: x, -2 x_t in, g out;
+    # adjoint solve: g, lambda in, lambda out
+    h2d = 8 * n * 6
+    d2h = 8 * n * 4
+    return {"value": 2 * k / sec, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": sec * 1e3 / k, "steps": k}
+
+
 def c4_arm(args, esd, torch, dev, ws, rank):
     """One optimisation step of the differentiation form: theta moves, A(theta) is assembled
     on the device, refactored, AW/E refreshed for the kept W, then x = A^-1 b and the
@@ -636,16 +920,16 @@ def power_method_report(esd, A, p, args, b, torch, peaks):
     timed_solve()  # graph capture with the power product
     S.power_start(v0)
     t_on, it_on = timed_solve()
-    lmax, steps = S.power_estimate()
+    _, steps = S.power_estimate()
     S.sample_and_build_W()
-    lmin = float(S.ritz_values()[0])
+    lmax, lmin, kappa = S.paper_cond_estimate()
     k_on = dict(S.profile_iterations(b, torch.zeros_like(b), reps=20))
     S.power_start(None)
     n, nnz = p.n, p.nnz
     t_k = k_on["spmv_pq"] / 1e3
     by = 12 * nnz + 20 * n + 16 * n
     fmas = 2 * nnz + 2 * n
-    return {"lambda_max": lmax, "power_steps": steps, "ritz_min": lmin, "kappa": lmax / lmin,
+    return {"lambda_max": lmax, "power_steps": steps, "ritz_min": lmin, "kappa": kappa,
             "iterations": it_on, "us_per_iteration_without": t_off / it_off * 1e6,
             "us_per_iteration_with": t_on / it_on * 1e6, "cost_frac": (t_on / it_on) / (t_off / it_off) - 1.0,
             "spmv_pq_us_without": k_off["spmv_pq"] * 1e3, "spmv_pq_us_with": k_on["spmv_pq"] * 1e3,
@@ -778,8 +1062,9 @@ def e2e(esd, p, args, torch):
 
 # ---------------------------------------------------------------- CPU oracle
 
-def oracle_rates(p, args, iters_plain=20, iters_acc=20):
-    """Seconds per oracle iteration (plain ICCG and the accelerated mode), single thread."""
+def oracle_rates(p, args, iters_plain=20, iters_acc=20, m=None):
+    """Seconds per oracle iteration (plain ICCG and the accelerated mode) with whichever
+    oracle library is current (serial, or the OpenMP build under oracle.using)."""
     import oracle
     ic = oracle.IC0(p)
     rng = np.random.default_rng(0)
@@ -787,9 +1072,11 @@ def oracle_rates(p, args, iters_plain=20, iters_acc=20):
     t0 = time.perf_counter()
     oracle.System(p, ic).solve(p.source, tol=1e-300, maxit=iters_plain, history=False)
     out["plain"] = (time.perf_counter() - t0) / iters_plain
-    if args.mode != "plain":
-        Q, _ = np.linalg.qr(rng.standard_normal((p.n, args.m)))
-        aux = oracle.Aux.from_basis(p, Q)
+    m = m or args.m
+    if args.mode != "plain" and m > 0:
+        # any full-rank W costs the same per iteration: scaled Gaussian columns
+        W = np.asfortranarray(rng.standard_normal((p.n, m)) / math.sqrt(p.n))
+        aux = oracle.Aux.from_basis(p, W)
         md = oracle.DEFLATION if args.mode == "deflation" else oracle.SUBSPACE_CORRECTION
         t0 = time.perf_counter()
         oracle.System(p, ic, md, aux).solve(p.source, tol=1e-300, maxit=iters_acc, history=False)
@@ -799,8 +1086,13 @@ def oracle_rates(p, args, iters_plain=20, iters_acc=20):
     return out
 
 
-def extrapolate(rates, its):
-    sec = rates["plain"] * its[0] + rates["acc"] * sum(its[1:])
+def extrapolate(rates, its, first_plain=True):
+    """Solves per second of a run with these iteration counts per solve at these rates (the
+    first solve plain when the sequence samples W in it)."""
+    if first_plain:
+        sec = rates["plain"] * its[0] + rates["acc"] * sum(its[1:])
+    else:
+        sec = rates["acc"] * sum(its)
     return len(its) / sec
 
 
@@ -818,13 +1110,30 @@ def host_info():
     return {"nproc": os.cpu_count(), "cpu_model": model, "machine": platform.machine()}
 
 
-def cpu_baseline(p, args, its):
+def cpu_baseline(p, args, its, first_plain=True, m=None):
+    """The oracle timed on the host: one thread, and the OpenMP build of the same source on
+    every core (rows of a colour, SpMV rows and vector updates shared among threads; results
+    bit-identical). A bounded sample of iterations, extrapolated to solves per second with
+    this run's iteration counts."""
+    import oracle
     k = 20 if p.nnz < 50_000_000 else 3  # keep the CPU sample to tens of seconds
-    r = oracle_rates(p, args, iters_plain=k, iters_acc=k)
-    return {"value": extrapolate(r, its), "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_info(),
+    entries = []
+    r1 = oracle_rates(p, args, iters_plain=k, iters_acc=k, m=m)
+    entries.append({"cores": 1, "value": extrapolate(r1, its, first_plain), "s_per_iter": r1})
+    try:
+        omp = oracle.openmp_lib()
+        with oracle.using(omp):
+            rn = oracle_rates(p, args, iters_plain=k, iters_acc=k, m=m)
+        entries.append({"cores": int(omp.orc_threads()), "value": extrapolate(rn, its, first_plain),
+                        "s_per_iter": rn})
+    except Exception as e:  # no OpenMP in this compiler: the single-thread timing stands alone
+        entries.append({"cores": None, "value": None, "unavailable": f"OpenMP oracle: {e}"})
+    best = max((e for e in entries if e.get("value")), key=lambda e: e["value"])
+    return {"value": best["value"], "unit": UNIT, "cores": best["cores"], "kind": "oracle", "host": host_info(),
+            "entries": entries,
             "sample": (f"{k} plain and {k} {args.mode} FP64 ICCG iterations of the {args.config} system "
-                       f"(n={p.n}, m={args.m}, orthonormal W) on one host core, extrapolated with this "
-                       f"run's iteration counts per solve"), "s_per_iter": r}
+                       f"(n={p.n}, m={m or args.m} columns of W) per timing, extrapolated with this run's "
+                       f"iteration counts per solve; single thread and OpenMP on all host cores")}
 
 
 def oracle_counts(args):
@@ -837,30 +1146,65 @@ def oracle_counts(args):
         raise SystemExit(f"missing {path}: run python -m oracle.sequence_counts {args.mode}")
 
 
+def c5_oracle_counts(args):
+    """The oracle's own forward and adjoint iteration counts of the 256^3 sequence's systems
+    in this mode (oracle/data, written by oracle/sequence_counts.py --c5 from the oracle
+    alone); system 2 stands for every later system."""
+    mode = "plain" if args.mode == "plain" else args.mode
+    path = os.path.join(ROOT, "oracle", "data", f"fv7_256cube_{mode}_counts.json")
+    try:
+        d = json.load(open(path))
+        k = 1 if len(d["iterations"]) > 1 else 0
+        return d["iterations"][k], d["adjoint_iterations"][k], path
+    except (OSError, KeyError, ValueError, IndexError):
+        raise SystemExit(f"missing {path}: run python -m oracle.sequence_counts --c5 {mode}")
+
+
 def reference_arm(args):
+    """The CPU oracle on this arm's workload, metric and unit: per step a bounded sample of
+    oracle iterations (plain and the configured mode), extrapolated to solves per second with
+    the oracle's own iteration counts. C5 (one system = forward + adjoint solve) runs the
+    OpenMP build of the oracle on every host core; C2 the single-threaded build."""
+    import oracle
     ws, rank, local = dist_env()
     if rank != 0:
         return
-    if args.config != "c2":
-        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm is timed on the headline 128^3 "
-                          "sequence (config c2) only"}), flush=True)
+    if args.config not in ("c2", "c5"):
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm is timed on the 128^3 and 256^3 "
+                          "sequences (configs c2 and c5) only"}), flush=True)
         return
     p = workload(args)
-    its = oracle_counts(args)
     vals = []
-    for s in range(args.warmup + args.steps):
-        r = oracle_rates(p, args, iters_plain=5, iters_acc=5)
-        if s >= args.warmup:
-            vals.append(extrapolate(r, its))
+    if args.config == "c5":
+        fwd, adj, path = c5_oracle_counts(args)
+        omp = oracle.openmp_lib()
+        with oracle.using(omp):
+            for s_ in range(args.warmup + args.steps):
+                r = oracle_rates(p, args, iters_plain=4, iters_acc=4, m=args.m)
+                sec = r["acc"] * (fwd + adj)
+                if s_ >= args.warmup:
+                    vals.append(2.0 / sec)
+        cores = int(omp.orc_threads())
+        sample = (f"4 plain and 4 {args.mode} FP64 oracle iterations per step (OpenMP, {cores} threads), "
+                  f"extrapolated with the oracle's own forward + adjoint counts of system 2 ({fwd} + {adj}, "
+                  f"{os.path.relpath(path, ROOT)}); the oracle has no FP32 form")
+    else:
+        its = oracle_counts(args)
+        for s_ in range(args.warmup + args.steps):
+            r = oracle_rates(p, args, iters_plain=5, iters_acc=5)
+            if s_ >= args.warmup:
+                vals.append(extrapolate(r, its))
+        cores = 1
+        sample = ("5 plain and 5 accelerated oracle iterations per step, extrapolated with the oracle's own "
+                  "iteration counts of this sequence (oracle/data, written by oracle/sequence_counts.py)")
     v = float(np.mean(vals))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(args, p), "grid": args.grid, "n": p.n, "nnz": p.nnz},
-            "cpu_baseline": {"value": v, "unit": UNIT, "kind": "oracle", "cores": 1, "host": host_info(),
-                             "sample": "5 plain and 5 accelerated oracle iterations per step, extrapolated "
-                                       "with the oracle's own iteration counts of this sequence "
-                                       "(oracle/data, written by oracle/sequence_counts.py)"},
+            "config": {"workload": workload_name(args, p), "config": args.config, "grid": args.grid, "n": p.n,
+                       "nnz": p.nnz, "mode": args.mode},
+            "cpu_baseline": {"value": v, "unit": UNIT, "kind": "oracle", "cores": cores, "host": host_info(),
+                             "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -877,12 +1221,18 @@ def main():
             if args.config == "c4":
                 p = workload(args)[0]
                 its = [k for pair in result["iterations_forward_adjoint"] for k in pair]
+            elif args.config == "c5":
+                p = workload(args)
+                its = list(result["iterations"]) + list(result["adjoint_iterations"])
+                result["cpu_baseline"] = cpu_baseline(p, args, its, first_plain=False,
+                                                      m=result["config"]["m_kept"])
             else:
                 p = workload(args)
                 its = list(result["iterations"])
                 if args.adjoint:
                     its += list(result["adjoint_iterations"])
-            result["cpu_baseline"] = cpu_baseline(p, args, its)
+            if "cpu_baseline" not in result:
+                result["cpu_baseline"] = cpu_baseline(p, args, its)
         print(json.dumps(result), flush=True)
     if ws > 1:
         import torch.distributed as dist

@@ -347,6 +347,17 @@ int esd_power_start(esd_solver* S, const double* v0);
  */
 int esd_power_estimate(esd_solver* S, double* lmax, int32_t* steps, double* v);
 
+/*
+ * The paper's condition number estimate (Algorithm "PCG with condition number estimation",
+ * Section 5.4): kappa = lambda_max / lambda_min with lambda_max = (v_k, A v_k) of the power
+ * method (as esd_power_estimate) and lambda_min the smallest Ritz value of the current W
+ * (esd_sample_and_build_W with theta = +inf on the sampled solve, Eq. Rayleigh-Ritz).
+ *   lmax, lmin, kappa  (host, any may be NULL)
+ * Errors: ESD_ERR_STATE without W or without the power method, ESD_ERR_BREAKDOWN as
+ * esd_power_estimate, ESD_ERR_CHOL_E when the smallest Ritz value is not positive.
+ */
+int esd_paper_cond_estimate(esd_solver* S, double* lmax, double* lmin, double* kappa);
+
 /* alpha_j and beta_j of the last solve (host arrays of cap entries). */
 int esd_get_history(esd_solver* S, double* alpha, double* beta, int32_t cap, int32_t* count);
 
@@ -377,6 +388,10 @@ int esd_profile_iterations(esd_solver* S, const double* b, double* x, int32_t re
  *   k      1 .. ESD_NOALLOC_MAX_K; a larger k returns ESD_ERR_INVALID before any launch
  *   out    device array of 3 doubles: lambda_min, lambda_max, kappa
  *   stream cudaStream_t of the launch (0 = legacy default stream); the call does not wait
+ * alpha, beta and out must be device (or managed) memory of the current device, holding at
+ * least k, k-1 and 3 doubles; a pointer that is not (a host array, another GPU's memory)
+ * returns ESD_ERR_INVALID before any launch. The lengths cannot be checked here: the Python
+ * binding checks them.
  * Scratch: a file-scope device array of 2 * ESD_NOALLOC_MAX_K doubles (512 KB), which every
  * GPU that loads the library holds until the process exits. The first call on a device, with
  * that device current, looks up the array's device address; make that first call before any

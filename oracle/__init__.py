@@ -87,6 +87,8 @@ def load(path: str):
     L.orc_solve.restype = i32
     L.orc_solve.argtypes = [C.POINTER(_System), vp, vp, C.POINTER(_SolveIO)]
     L.orc_sampling_a_schedule.argtypes = [i32, i32, i32, vp]
+    L.orc_threads.restype = i32
+    L.orc_threads.argtypes = []
     L.orc_power_method.restype = f64
     L.orc_power_method.argtypes = [i32, vp, vp, vp, vp, i32, vp]
     return L

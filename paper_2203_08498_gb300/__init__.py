@@ -45,6 +45,7 @@ __all__ = [
     "esd_lanczos_extremes_noalloc", "NOALLOC_MAX_K", "esd_matrix_set_values", "esd_fv_assemble",
     "esd_fv_grad_theta", "esd_refresh_W", "EsdFvGrid", "esd_power_start", "esd_power_estimate",
     "esd_matrix_diag_scale", "MATRIX_DIAG_SCALE", "esd_set_precision", "esd_solver_set_precond_matrix",
+    "esd_paper_cond_estimate",
 ]
 MATRIX_DIAG_SCALE = 1
 NOALLOC_MAX_K = 32768
@@ -135,6 +136,7 @@ def lib(build_if_missing: bool = True):
             "esd_set_precision": (i32, [vp, i32, f64]),
             "esd_solver_set_precond_matrix": (i32, [vp, vp]),
             "esd_power_estimate": (i32, [vp, P(f64), P(i32), vp]),
+            "esd_paper_cond_estimate": (i32, [vp, P(f64), P(f64), P(f64)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -362,6 +364,13 @@ def esd_power_estimate(h, v=None):
     return lam.value, k.value
 
 
+def esd_paper_cond_estimate(h):
+    """(lambda_max, lambda_min, kappa) of Algorithm PCG-con, formed by the library."""
+    lmax, lmin, kap = C.c_double(), C.c_double(), C.c_double()
+    _check(lib().esd_paper_cond_estimate(h, C.byref(lmax), C.byref(lmin), C.byref(kap)))
+    return lmax.value, lmin.value, kap.value
+
+
 def esd_get_history(h, cap):
     a, b = np.zeros(cap), np.zeros(cap)
     cnt = C.c_int32()
@@ -396,7 +405,16 @@ def esd_profile_iterations(h, b, x, reps, cap=64):
 
 def esd_lanczos_extremes_noalloc(alpha, beta, k, out, stream=None):
     """Condition estimate from caller-owned device arrays, allocating nothing (for callers
-    that cannot call cudaMalloc). out: device array of 3 doubles (lmin, lmax, kappa)."""
+    that cannot call cudaMalloc). alpha: k doubles, beta: k-1 doubles (may be None when
+    k = 1), out: 3 doubles (lmin, lmax, kappa); all contiguous CUDA float64 tensors."""
+    import torch
+    for name, t, need in (("alpha", alpha, k), ("beta", beta, k - 1), ("out", out, 3)):
+        if t is None and need <= 0:
+            continue
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise TypeError(f"{name} must be a contiguous CUDA float64 tensor")
+        if t.numel() < need:
+            raise ValueError(f"{name} holds {t.numel()} values, {need} needed")
     st = current_stream() if stream is None else stream
     _check(lib().esd_lanczos_extremes_noalloc(_ptr(alpha), _ptr(beta), k, _ptr(out), C.c_void_p(st)))
 
@@ -533,9 +551,7 @@ class Solver:
         """Algorithm PCG-con's kappa = lambda_max / lambda_min: lambda_max from the power
         method, lambda_min the smallest Ritz value of the current W (after
         sample_and_build_W with theta = inf on the sampled solve). Returns (lmax, lmin, kappa)."""
-        lmax, _ = self.power_estimate()
-        lmin = float(self.ritz_values()[0])
-        return lmax, lmin, lmax / lmin
+        return esd_paper_cond_estimate(self._h)
 
     def history(self):
         return esd_get_history(self._h, self.maxit_cap)

@@ -803,6 +803,24 @@ int esd_power_estimate(esd_solver* S, double* lmax, int32_t* steps, double* v) {
   ESD_API_END
 }
 
+int esd_paper_cond_estimate(esd_solver* S, double* lmax, double* lmin, double* kappa) {
+  ESD_API_BEGIN
+  ESD_CHECK(S, ESD_ERR_INVALID, "NULL solver");
+  ESD_CHECK(S->have_W, ESD_ERR_STATE, "no W: the smallest Ritz value needs the sampled basis");
+  double lx = 0.0;
+  const int rc = esd_power_estimate(S, &lx, nullptr, nullptr);
+  if (rc != ESD_OK) return rc;
+  double r0 = 0.0;
+  ESD_CUDA(cudaMemcpyAsync(&r0, S->ritz.get(), sizeof(double), cudaMemcpyDeviceToHost, S->stream));
+  ESD_CUDA(cudaStreamSynchronize(S->stream));
+  ESD_CHECK(r0 > 0.0, ESD_ERR_CHOL_E, "the smallest Ritz value is not positive");
+  if (lmax) *lmax = lx;
+  if (lmin) *lmin = r0;
+  if (kappa) *kappa = lx / r0;
+  return ESD_OK;
+  ESD_API_END
+}
+
 int esd_estimate_cond(esd_solver* S, double* lmin, double* lmax, double* kappa, double* ritz_min) {
   ESD_API_BEGIN
   ESD_CHECK(S, ESD_ERR_INVALID, "NULL solver");

@@ -1,6 +1,6 @@
 """Per-kernel timing of one PCG iteration, outside any CUDA graph (for ncu and for users).
 
-python -m paper_2203_08498_gb300.profile --grid 96 --mode deflation --m 16 --reps 5 [--precision fp32]
+python -m paper_2203_08498_gb300.profile --grid 96 --mode deflation --m 16 --reps 5 [--precision fp32] [--recipe c5]
 
 Builds the heterogeneous-diffusion matrix of the given grid, factors it, installs an
 orthonormal W of m columns (random, seeded: the per-iteration cost does not depend on W's
@@ -35,9 +35,15 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--precond", default="ic0", choices=["ic0", "none"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--recipe", default="c2", choices=["c2", "c5"],
+                    help="c2: 16 balls of 1e5 (radius 4-8 cells at 128^3); c5: 64 balls of 1e6 (8-16 at 256^3)")
     a = ap.parse_args(argv)
-    r = a.grid / 128.0
-    p = wl.config_c2(N=a.grid, rmin=4 * r, rmax=8 * r)
+    if a.recipe == "c5":
+        r = a.grid / 256.0
+        p = wl.config_c5(N=a.grid, rmin=8 * r, rmax=16 * r)
+    else:
+        r = a.grid / 128.0
+        p = wl.config_c2(N=a.grid, rmin=4 * r, rmax=8 * r)
     dev = torch.device("cuda:0")
     A = esd.Matrix.from_problem(p)
     pre = esd.PRECOND_IC0 if a.precond == "ic0" else esd.PRECOND_NONE
@@ -53,7 +59,7 @@ def main(argv=None):
     b = torch.from_numpy(p.source).to(dev)
     x = torch.zeros(p.n, dtype=torch.float64, device=dev)
     prof = S.profile_iterations(b, x, reps=a.reps)
-    print(json.dumps({"grid": a.grid, "n": p.n, "nnz": p.nnz, "mode": a.mode, "m": a.m,
+    print(json.dumps({"grid": a.grid, "recipe": a.recipe, "n": p.n, "nnz": p.nnz, "mode": a.mode, "m": a.m,
                       "precision": a.precision, "kernels_ms": prof}), flush=True)
 
 

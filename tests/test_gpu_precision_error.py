@@ -1,0 +1,96 @@
+"""Final error of the precision form against the FP64 oracle, per configuration (GPU only).
+
+The refinement form (FP32 inner PCG in FP64 iterative refinement) stops when the FP64 true
+residual ||b - A x|| / ||b|| meets the tolerance. Its solution is compared with the oracle's
+FP64 ICCG solution of the same system, taken to a tolerance a hundred times tighter and
+refined once in FP64 by the oracle, and with the FP64 GPU solve of the same system (plain PCG stopped by its recursive residual). The
+bound the residual gives is ||x - x*|| / ||x*|| <= kappa(A) ||b - A x|| / ||b||, with kappa(A)
+up to 1e9 here; the test records the measured errors and requires 1e-5 at most.
+
+Systems: the first system of each sequence (b = s, x_0 = 0) of C2 (128^3), C3 at 64^3
+(the 27-point operator), C4 (128^3, the steady exp(theta) operator) and C5's recipe at
+128^3; with ESD_FULL_C5=1 also C5 itself at 256^3 (several minutes of oracle time).
+The errors are appended to gpurun_out/precision_errors.jsonl when that folder exists.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2203_08498_gb300 as esd  # noqa: E402
+
+DEV = torch.device("cuda:0")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _cases():
+    cases = {
+        "c2_128cube": (lambda: wl.config_c2(), 1e-8),
+        "c3_64cube": (lambda: wl.config_c3(N=64), 1e-10),
+        "c4_128cube": (lambda: wl.config_c4()[0], 1e-8),
+        "c5_recipe_128cube": (lambda: wl.config_c5(N=128, rmin=4.0, rmax=8.0), 1e-8),
+    }
+    if os.environ.get("ESD_FULL_C5") == "1":
+        cases["c5_256cube"] = (lambda: wl.config_c5(), 1e-8)
+    return cases
+
+
+CASES = _cases()
+
+
+def _record(row):
+    out = os.path.join(ROOT, "gpurun_out")
+    if os.path.isdir(out):
+        with open(os.path.join(out, "precision_errors.jsonl"), "a") as f:
+            f.write(json.dumps(row) + "\n")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_precision_form_error_against_oracle(name):
+    make, tol = CASES[name]
+    p = make()
+    b = p.source
+    A = esd.Matrix.from_problem(p)
+    A.factor_ic0()
+    S32 = esd.Solver(A, sample_cap=0, precision=esd.FP32_REFINE)
+    x32 = np.zeros(p.n)
+    st, it32, rr32 = S32.solve(b, x32, tol=tol)
+    assert st == esd.OK and rr32 <= tol
+    S64 = esd.Solver(A, sample_cap=0)
+    x64 = np.zeros(p.n)
+    st, it64, _ = S64.solve(b, x64, tol=tol)
+    true64 = S64.true_relres()
+    lib = oracle.openmp_lib()
+    with oracle.using(lib):
+        # the reference: oracle ICCG to tol / 100, then one FP64 refinement step by the oracle
+        # (its recursive residual drifts from the true one at kappa ~ 1e9)
+        sysm = oracle.System(p, oracle.IC0(p))
+        ref = sysm.solve(b, tol=tol / 100, history=False)
+        assert ref["status"] == oracle.OK
+        r = b - oracle.spmv(p, ref["x"])
+        d = sysm.solve(r, tol=1e-6, history=False)
+        x_ref = ref["x"] + d["x"]
+        ref_true = float(np.linalg.norm(b - oracle.spmv(p, x_ref)) / np.linalg.norm(b))
+    e32, e64 = rel(x32, x_ref), rel(x64, x_ref)
+    row = {"config": name, "n": p.n, "tol": tol, "precision_form": {"iters": it32, "true_relres": rr32, "rel_error": e32},
+           "fp64_pcg": {"iters": it64, "true_relres": true64, "rel_error": e64},
+           "oracle": {"tol": tol / 100, "iters": ref["iters"] + d["iters"], "true_relres": ref_true,
+                      "threads": int(lib.orc_threads())}}
+    _record(row)
+    print(json.dumps(row))
+    assert e32 <= 1e-5
