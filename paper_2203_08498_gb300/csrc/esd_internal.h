@@ -45,6 +45,7 @@ struct Sell {
   DevBuf val32;  // float per entry (FP32 inner solves)
   DevBuf ent32;  // uint2 per entry: (float bits, column), so an FP32 entry is one 8-byte load
   long long entries = 0;
+  int wmax = 0;  // widest slice (entries per row)
   template <typename T> SellView<T> view() const;
 };
 
@@ -84,6 +85,7 @@ struct esd_matrix {
   std::vector<esd::SliceSet> fwd_all_sets; // all forward levels incl. level 0 (factor, apply)
   std::vector<esd::SliceSet> bwd_all_sets; // all backward levels incl. level 0 (apply)
   std::vector<esd::SliceSet> bwd0_sets;    // colours without later neighbours
+  std::vector<int> fwd_wmax, bwd_wmax;     // widest L (U) row of each fwd_sets (bwd_sets) launch
   esd::DevBuf fwd_grid64, fwd_grid32;      // int per forward launch: its grid (FP64 / FP32 kernel)
   esd::Sell A, L, U;  // L and U hold the strict factor entries negated (-l_ij)
   esd::DevBuf slice_flags;   // uint8 per slice: bit0 fwd level 0, bit1 bwd level 0

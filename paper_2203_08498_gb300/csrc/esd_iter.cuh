@@ -1378,6 +1378,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_true_res(IterCtx<T> c, SliceSet s
     default: throw Error(ESD_ERR_INVALID, "unsupported padded column count");         \
   }
 
+}  // namespace esd
+
+#include "esd_stream.cuh"
+
+namespace esd {
+
 #define ESD_DISPATCH_MPOS(Mrt, ...)                                                   \
   switch (Mrt) {                                                                      \
     case 8: { constexpr int MM = 8; __VA_ARGS__; } break;                             \
@@ -1429,12 +1435,38 @@ static void launch_update(const IterCtx<T>& c, int do_update, int finalize, cuda
   if (marks) marks->mark(s, "update");
 }
 
+// The FP32 substitutions of P stream their factor entries through staged shared memory
+// (k_fwd_stream, k_bwd_stream) when every factor row fits a stage.
+template <typename T>
+static bool stream_sweeps(const esd_matrix* P) {
+  return sizeof(T) == 4 && stream_enabled() && P->L.wmax <= kStreamWmax && P->U.wmax <= kStreamWmax;
+}
+
+// Plan and grid of forward launch l (the last forward launch reads the rho block totals of
+// the earlier ones, so every launch of a sweep uses exactly this grid).
+template <typename T>
+static int fwd_grid(const esd_matrix* P, size_t l, StreamPlan* plan = nullptr, int* K_out = nullptr) {
+  const SliceSet& set = P->fwd_sets[l];
+  if constexpr (sizeof(T) == 4) {
+    if (stream_sweeps<T>(P)) {
+      int K = 1;
+      const StreamPlan pl = stream_plan(set, SliceSet{}, P->fwd_wmax[l], 2, 4, &K);
+      if (plan) *plan = pl;
+      if (K_out) *K_out = K;
+      int G = 0;
+      ESD_DISPATCH_K(K, { G = stream_blocks(k_fwd_stream<T, KK>, pl); });
+      return G;
+    }
+  }
+  auto kf = k_fwd<T>;
+  return grid_for(kf, set.total());
+}
+
 // forward levels >= 1 then backward levels (with the direction update)
 template <typename T>
 std::vector<int> fwd_grids(const esd_matrix* P) {
   std::vector<int> g;
-  auto kf = k_fwd<T>;
-  for (const SliceSet& set : P->fwd_sets) g.push_back(grid_for(kf, set.total()));
+  for (size_t l = 0; l < P->fwd_sets.size(); ++l) g.push_back(fwd_grid<T>(P, l));
   return g;
 }
 
@@ -1449,12 +1481,21 @@ static void launch_precond(const IterCtx<T>& c, cudaStream_t s, KernelMarks* mar
   }
   const size_t nf = A->fwd_sets.size();
   const int* dG = sizeof(T) == 8 ? A->fwd_grid64.as<int>() : A->fwd_grid32.as<int>();
+  const bool staged = stream_sweeps<T>(A);
+  if (staged)
+    ESD_CHECK(c.Lv.ent && c.Uv.ent, ESD_ERR_INTERNAL, "the staged sweeps need the FP32 (value, column) factor entries");
   auto kf = k_fwd<T>;
   for (size_t l = 0; l < nf; ++l) {
     const SliceSet& set = A->fwd_sets[l];
-    const int G = grid_for(kf, set.total());
+    StreamPlan pl{};
+    int K = 1;
+    const int G = fwd_grid<T>(A, l, &pl, &K);
     const bool last = l + 1 == nf;
-    launch_pdl(kf, G, s, c, set, last ? -1 : (int)l, last ? (int)l : 0, dG);
+    if constexpr (sizeof(T) == 4) {
+      if (staged)
+        ESD_DISPATCH_K(K, launch_stream(k_fwd_stream<T, KK>, G, pl, s, c, pl, last ? -1 : (int)l, last ? (int)l : 0, dG));
+    }
+    if (!staged) launch_pdl(kf, G, s, c, set, last ? -1 : (int)l, last ? (int)l : 0, dG);
     if (marks) marks->mark(s, ("fwd_" + std::to_string(l + 1)).c_str());
   }
   SliceSet none{};
@@ -1462,7 +1503,19 @@ static void launch_precond(const IterCtx<T>& c, cudaStream_t s, KernelMarks* mar
   for (size_t l = 0; l < nb; ++l) {
     const SliceSet& sw = l < A->bwd_sets.size() ? A->bwd_sets[l] : none;
     const SliceSet& el = l < A->bwd0_sets.size() ? A->bwd0_sets[l] : none;
-    ESD_DISPATCH_M(SCM, { auto k = k_bwd<T, MM>; ESD_LAUNCH(k, sw.total() + el.total(), s, c, sw, el); });
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+      if (staged && SCM == 0) {
+        int K = 1;
+        const StreamPlan pl = stream_plan(sw, el, l < A->bwd_wmax.size() ? A->bwd_wmax[l] : 0, 3, 4, &K);
+        ESD_DISPATCH_K(K, {
+          auto k = k_bwd_stream<T, KK>;
+          launch_stream(k, stream_blocks(k, pl), pl, s, c, pl);
+        });
+        done = true;
+      }
+    }
+    if (!done) ESD_DISPATCH_M(SCM, { auto k = k_bwd<T, MM>; ESD_LAUNCH(k, sw.total() + el.total(), s, c, sw, el); });
     if (marks) marks->mark(s, ("bwd_" + std::to_string(l + 1)).c_str());
   }
 }
@@ -1508,6 +1561,17 @@ void launch_iteration(const IterCtx<T>& c, cudaStream_t s, KernelMarks* marks) {
       auto k = k_spmv_pq<T, MM>;
       launch_pdl_smem(k, all.total(), df_stage_bytes<MM>(), s, c, all);
     });
+  } else if (sizeof(T) == 4 && Mm == 0 && c.rowsum && c.Av.ent && c.A->A.wmax <= kStreamWmax &&
+             stream_enabled()) {
+    // FP32 plain product: the matrix stream staged by bulk copies
+    if constexpr (sizeof(T) == 4) {
+      int K = 1;
+      const StreamPlan pl = stream_plan(all, SliceSet{}, c.A->A.wmax, 2, 4, &K);
+      ESD_DISPATCH_K(K, {
+        auto k = k_spmv_pq_stream<T, KK>;
+        launch_stream(k, stream_blocks(k, pl), pl, s, c, pl);
+      });
+    }
   } else {
     ESD_DISPATCH_M(Mm, { auto k = k_spmv_pq<T, MM>; ESD_LAUNCH(k, all.total(), s, c, all); });
   }

@@ -633,6 +633,7 @@ int esd_create_matrix(int32_t n, int64_t nnz, const int32_t* rowptr, const int32
         ESD_CHECK(off < (long long)INT32_MAX, ESD_ERR_INVALID, "matrix too large for 32-bit slice offsets");
       }
       part.entries = off;
+      part.wmax = NS > 0 ? *std::max_element(w.begin(), w.end()) : 0;
       part.meta.alloc(sizeof(int4) * NS);
       ESD_CUDA(cudaMemcpyAsync(part.meta.get(), meta.data(), part.meta.bytes(), cudaMemcpyHostToDevice, s));
       part.col.alloc(sizeof(int) * std::max(off, 1LL));
@@ -652,6 +653,17 @@ int esd_create_matrix(int32_t n, int64_t nnz, const int32_t* rowptr, const int32
 
     // slice flags and launch sets
     build_level_sets(M.get(), hadj);
+    // widest factor row of every sweep launch (the staged FP32 sweeps size their stages by it)
+    auto set_wmax = [](const SliceSet& set, const std::vector<int>& w) {
+      int m = 0;
+      for (int r = 0; r < set.nr; ++r)
+        for (int g = set.cum[r]; g < set.cum[r + 1]; ++g) m = std::max(m, w[set.begin[r] + (g - set.cum[r])]);
+      return m;
+    };
+    M->fwd_wmax.clear();
+    for (const SliceSet& set : M->fwd_sets) M->fwd_wmax.push_back(set_wmax(set, hwL));
+    M->bwd_wmax.clear();
+    for (const SliceSet& set : M->bwd_sets) M->bwd_wmax.push_back(set_wmax(set, hwU));
     // grid of every forward launch (one table per kernel precision): the last forward launch
     // of an iteration adds the block totals the earlier ones left
     for (int prec = 0; prec < 2; ++prec) {

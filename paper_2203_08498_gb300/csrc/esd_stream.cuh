@@ -1,0 +1,607 @@
+// Bulk-staged matrix streaming for the FP32 kernels of the refinement form's inner PCG: the
+// sliced-ELL entries and the row vectors of a launch reach shared memory by cp.async.bulk
+// (the TMA engine's 1-D copies), chunk by chunk through a ring of stages, while consumer warps
+// form the row products from shared memory.
+//
+// Why: in the one-warp-per-slice kernels every slice waits on three dependent memory round
+// trips (its meta, then its entries and vector elements, then the gathers), so the SpMV and
+// the sweeps were latency-bound at 55-72 % of the copy bandwidth. Here one producer warp per
+// block issues large contiguous copies (kilobytes per request) up to three chunks ahead, so
+// the matrix stream never waits on the gathers, and a slice costs its consumer warp one
+// round trip (the gathers of the vector, mostly L2 hits). Short rows (the first levels of a
+// sweep hold 2 factor entries per row) give a warp K slices per chunk, so that enough
+// gathers are in flight.
+//
+// Layout of one stage: the chunk's slice metas (16 bytes each), the row vectors (the chunk's
+// rows, widened to 16-byte boundaries), then its entries exactly as they lie in global memory
+// (slice after slice, 32 x width 8-byte entries each). The slices of a chunk are consecutive,
+// and so are their rows, so every copy is one contiguous range: 16-byte aligned, a multiple of
+// 16 bytes, as cp.async.bulk requires.
+//
+// Synchronisation: stage k has a "full" mbarrier (one producer arrival + the copies' byte
+// count) and an "empty" one (one arrival per consumer warp). Use u of a stage completes phase
+// u of both. Every wait is bounded (about a second of the global timer); a wait that runs out
+// sets ESD_ERR_INTERNAL, stops the solve's loop, and leaves its loop; the producer then waits
+// (bounded again) for the copies it issued before the block exits.
+#pragma once
+
+#include <cstdlib>
+
+namespace esd {
+
+constexpr int kStreamWarps = 16;                             // consumer warps per block
+constexpr int kStreamThreads = (kStreamWarps + 1) * 32;      // + one producer warp
+constexpr int kStreamMaxStages = 3;                          // chunks in flight per block, at most
+constexpr int kStreamWmax = 8;                               // widest slice the staged kernels take
+constexpr int kStreamMaxK = 4;                               // slices per consumer warp per chunk, at most
+constexpr int kStreamStageCap = 50 * 1024;                   // bytes of one stage, at most
+constexpr int kStreamRingCap = 100 * 1024;                   // bytes of the stage ring (2 blocks per SM)
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // bound of every mbarrier wait
+
+// Chunks of one slice set: range r of the set holds chunks [ccum[r], ccum[r+1]) of cs slices
+// each (the last one of a range may be shorter); no chunk spans two ranges, so its slices,
+// and their rows, are consecutive in memory.
+struct ChunkMap {
+  int nr;
+  int ccum[kMaxRanges + 1];
+  __host__ __device__ int total() const { return ccum[nr]; }
+};
+
+inline ChunkMap chunk_map(const SliceSet& set, int cs) {
+  ChunkMap m{};
+  m.nr = set.nr;
+  m.ccum[0] = 0;
+  for (int r = 0; r < set.nr; ++r) {
+    const int len = set.cum[r + 1] - set.cum[r];
+    m.ccum[r + 1] = m.ccum[r] + (len + cs - 1) / cs;
+  }
+  return m;
+}
+
+// Row-vector elements a stage holds per vector: the chunk's rows, widened at both ends to
+// 16-byte boundaries.
+__host__ __device__ constexpr int stream_vcap(int cs, int vec_bytes) { return cs * kSlice + 2 * (16 / vec_bytes); }
+
+// Bytes of one stage: metas, nvec row vectors of vec_bytes elements, then the entries of cs
+// slices of at most wmax entries per row.
+__host__ __device__ constexpr int stream_stage_bytes(int cs, int wmax, int entry_bytes, int nvec, int vec_bytes) {
+  return cs * 16 + nvec * stream_vcap(cs, vec_bytes) * vec_bytes + cs * wmax * kSlice * entry_bytes;
+}
+
+// The chunks of one staged launch: those of set 0 (matrix entries and row vectors staged),
+// then those of set 1 (row vectors only; empty unless a kernel has such rows). cs = slices
+// per chunk (kStreamWarps x K), ns = stages in the ring, stage = bytes of one stage.
+struct StreamPlan {
+  SliceSet set[2];
+  ChunkMap cm[2];
+  int cs, ns, stage;
+  __host__ __device__ int total() const { return cm[0].total() + cm[1].total(); }
+};
+
+// Shape of a launch whose set-0 rows hold at most wmax entries: K, the slices a consumer warp
+// takes per chunk (K x wmax <= kStreamWmax, stage <= kStreamStageCap), and the stages that fit
+// kStreamRingCap (3, else 2).
+inline StreamPlan stream_plan(const SliceSet& with_entries, const SliceSet& vectors_only, int wmax, int nvec,
+                              int vec_bytes, int* K_out) {
+  int K = 1;
+  for (int k = kStreamMaxK; k > 1; k /= 2)
+    if (k * std::max(wmax, 1) <= kStreamWmax &&
+        stream_stage_bytes(kStreamWarps * k, wmax, 8, nvec, vec_bytes) <= kStreamStageCap) {
+      K = k;
+      break;
+    }
+  StreamPlan pl{};
+  pl.cs = kStreamWarps * K;
+  pl.stage = stream_stage_bytes(pl.cs, wmax, 8, nvec, vec_bytes);
+  pl.ns = 3 * pl.stage <= kStreamRingCap ? 3 : 2;
+  pl.set[0] = with_entries;
+  pl.set[1] = vectors_only;
+  pl.cm[0] = chunk_map(with_entries, pl.cs);
+  pl.cm[1] = chunk_map(vectors_only, pl.cs);
+  *K_out = K;
+  return pl;
+}
+
+// Part (0 or 1), range of the part's set, and slices [s0, s1) of chunk ch.
+struct ChunkPos {
+  int part, range, s0, s1;
+};
+
+__device__ __forceinline__ ChunkPos chunk_pos(const StreamPlan& pl, int ch) {
+  ChunkPos cp;
+  const int n0 = pl.cm[0].total();
+  cp.part = ch < n0 ? 0 : 1;
+  const SliceSet& set = pl.set[cp.part];
+  const ChunkMap& cm = pl.cm[cp.part];
+  const int c = ch - (cp.part ? n0 : 0);
+  int r = 0;
+#pragma unroll 1
+  while (r + 1 < cm.nr && c >= cm.ccum[r + 1]) ++r;
+  const int g0 = set.cum[r] + (c - cm.ccum[r]) * pl.cs;
+  const int g1 = min(g0 + pl.cs, set.cum[r + 1]);
+  cp.range = r;
+  cp.s0 = set.begin[r] + (g0 - set.cum[r]);
+  cp.s1 = cp.s0 + (g1 - g0);
+  return cp;
+}
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the completion of the phase of parity `parity`; false after kWaitLimitNs.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  if (mbar_test(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_test(bar, parity))
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  return true;
+}
+
+// L2 policy for data read once per pass: evict first, so the gathered vectors stay in L2.
+__device__ __forceinline__ unsigned long long l2_evict_first() {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+// L2 policy for data that other rows will gather soon: keep it.
+__device__ __forceinline__ unsigned long long l2_evict_last() {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+// bytes (a multiple of 16) from global src to shared dst (both 16-byte aligned), completing
+// on bar's transaction count
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar,
+                                          unsigned long long pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
+      : "memory");
+}
+
+// The solve's loop stops with ESD_ERR_INTERNAL (a staged wait ran out, or a slice did not fit
+// the stage shape the launch was planned for).
+__device__ __forceinline__ void stream_fail(State* st, unsigned long long cond) {
+  st->status = ESD_ERR_INTERNAL;
+  st->conv = 1;
+  end_loop(cond);
+}
+
+// First element of the widened row range of a chunk whose first row is z0 (16-byte aligned).
+template <int VB>
+__device__ __forceinline__ int stream_row0(int z0) {
+  return z0 & ~(16 / VB - 1);
+}
+
+// Producer loop of one block: chunks blockIdx.x, blockIdx.x + G, ... into the stage ring.
+// A stage receives the chunk's metas, row vectors (vec[v][a0 .. a1): the chunk's rows
+// widened to 16-byte boundaries; every vector holds a multiple of 32 elements, so the
+// widened end stays inside it) and, for chunks of part 0, the entries. Part-1 chunks copy
+// only the vectors of part1_vmask. Vectors in keep_mask are copied with an evict-last L2
+// policy (other rows gather them), the rest evict-first. Returns false if a wait ran out;
+// on return every copy it issued has landed (or a drain wait ran out, reported as well).
+template <int NV, int VB>
+__device__ __forceinline__ bool stream_produce(const StreamPlan& pl, const int4* meta, const void* ent,
+                                               int entry_bytes, const void* const* vec, unsigned keep_mask,
+                                               unsigned part1_vmask, unsigned long long* full,
+                                               unsigned long long* empty) {
+  const unsigned long long pol_first = l2_evict_first(), pol_last = l2_evict_last();
+  const int vcap = stream_vcap(pl.cs, VB);
+  const int G = gridDim.x, nch = pl.total(), ns = pl.ns;
+  bool ok = true;
+  int j = 0;
+  for (int ch = blockIdx.x; ch < nch; ch += G, ++j) {
+    const int k = j % ns, u = j / ns;
+    if (u > 0 && !mbar_wait(&empty[k], (unsigned)(u - 1) & 1u)) {
+      ok = false;
+      break;
+    }
+    const ChunkPos cp = chunk_pos(pl, ch);
+    const int4 m0 = meta[cp.s0], m1 = meta[cp.s1 - 1];
+    const unsigned mbytes = (unsigned)(cp.s1 - cp.s0) * 16u;
+    const unsigned ebytes = cp.part ? 0u : (unsigned)(m1.x + m1.y * kSlice - m0.x) * (unsigned)entry_bytes;
+    const unsigned vmask = cp.part ? part1_vmask : ~0u;
+    const int a0 = stream_row0<VB>(m0.z);
+    const int a1 = (m1.z + m1.w + (16 / VB - 1)) & ~(16 / VB - 1);
+    const unsigned vbytes = (unsigned)(a1 - a0) * VB;
+    unsigned tx = mbytes + ebytes;
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      if ((vmask >> v) & 1u) tx += vbytes;
+    unsigned char* st = esd_dyn_smem + (size_t)k * pl.stage;
+    mbar_arrive_expect_tx(&full[k], tx);
+    bulk_load(st, meta + cp.s0, mbytes, &full[k], pol_first);
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      if ((vmask >> v) & 1u)
+        bulk_load(st + pl.cs * 16 + v * vcap * VB, (const unsigned char*)vec[v] + (size_t)a0 * VB, vbytes, &full[k],
+                  ((keep_mask >> v) & 1u) ? pol_last : pol_first);
+    if (ebytes)
+      bulk_load(st + pl.cs * 16 + NV * vcap * VB, (const unsigned char*)ent + (size_t)m0.x * entry_bytes, ebytes,
+                &full[k], pol_first);
+  }
+  // drain: the last use of every stage this block issued
+  for (int k = 0; k < ns && k < j; ++k) {
+    const int ulast = (j - 1 - k) / ns;
+    if (!mbar_wait(&full[k], (unsigned)ulast & 1u)) ok = false;
+  }
+  return ok;
+}
+
+// One stage as a consumer warp sees it.
+template <int NV, int VB>
+struct StageView {
+  const unsigned char* base;
+  int cs;
+  int a0;  // first row of the staged vectors
+  int x0;  // entry offset of the chunk's first slice
+  __device__ __forceinline__ const int4* meta() const { return reinterpret_cast<const int4*>(base); }
+  __device__ __forceinline__ const float* vecf(int v) const {
+    return reinterpret_cast<const float*>(base + cs * 16 + v * stream_vcap(cs, VB) * VB);
+  }
+  __device__ __forceinline__ const uint2* ent() const {
+    return reinterpret_cast<const uint2*>(base + cs * 16 + NV * stream_vcap(cs, VB) * VB);
+  }
+};
+
+// mbarriers of a staged block, set up by thread 0 (visible after the next block barrier)
+__device__ __forceinline__ void stream_init_barriers(unsigned long long* full, unsigned long long* empty) {
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < kStreamMaxStages; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], kStreamWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+}
+
+// Consumer loop of one warp: for each chunk of this block, wait for its stage, call
+// f(chunk position, stage view), then release the stage. Every consumer warp takes part in
+// every chunk (the empty barrier counts kStreamWarps arrivals). False if a wait ran out.
+template <int NV, int VB, typename F>
+__device__ __forceinline__ bool stream_consume(const StreamPlan& pl, unsigned long long* full,
+                                               unsigned long long* empty, F&& f) {
+  const int G = gridDim.x, nch = pl.total(), ns = pl.ns;
+  int j = 0;
+  for (int ch = blockIdx.x; ch < nch; ch += G, ++j) {
+    const int k = j % ns, u = j / ns;
+    if (!mbar_wait(&full[k], (unsigned)u & 1u)) return false;
+    StageView<NV, VB> sv;
+    sv.base = esd_dyn_smem + (size_t)k * pl.stage;
+    sv.cs = pl.cs;
+    const int4 m0 = sv.meta()[0];
+    sv.a0 = stream_row0<VB>(m0.z);
+    sv.x0 = m0.x;
+    f(chunk_pos(pl, ch), sv);
+    __syncwarp();
+    if (lane_id() == 0) mbar_arrive(&empty[k]);
+  }
+  return true;
+}
+
+// The K slices of one consumer warp in a chunk (warp, warp + kStreamWarps, ...): their metas
+// (zero for slices past the chunk's end: no rows, no entries).
+template <int K, int NV, int VB>
+__device__ __forceinline__ void stream_slices(const StageView<NV, VB>& sv, const ChunkPos& cp, int warp,
+                                              int4 (&md)[K]) {
+#pragma unroll
+  for (int t = 0; t < K; ++t) {
+    const int ls = warp + t * kStreamWarps;
+    md[t] = ls < cp.s1 - cp.s0 ? sv.meta()[ls] : make_int4(0, 0, 0, 0);
+  }
+}
+
+// Row products of K slices of one lane from staged entries: acc[t] += sum_e val_e * (v[col_e]
+// - vi[t]) (vi = 0 in the plain form), the entries of a row in stored order, as row_fma and
+// row_fma_diff take them. Every gather of the K rows is issued before the first FMA. A row
+// wider than kStreamWmax / K (which the launch plan excludes) is reported through `bad`.
+template <int K, bool DIFF, int NV, int VB>
+__device__ __forceinline__ void staged_rows(const StageView<NV, VB>& sv, const int4 (&md)[K], int lane,
+                                            const float* __restrict__ v, const float (&vi)[K], float (&acc)[K],
+                                            bool& bad) {
+  constexpr int W = kStreamWmax / K;
+  uint2 ev[K][W];
+  float vj[K][W];
+  const uint2* ent = sv.ent();
+#pragma unroll
+  for (int t = 0; t < K; ++t) {
+    bad |= md[t].y > W;
+    const uint2* ep = ent + (md[t].x - sv.x0) + lane;
+#pragma unroll
+    for (int e = 0; e < W; ++e) {
+      ev[t][e] = e < md[t].y ? ep[e * kSlice] : make_uint2(0u, 0u);
+      vj[t][e] = e < md[t].y ? v[ev[t][e].y] : 0.f;
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < K; ++t)
+#pragma unroll
+    for (int e = 0; e < W; ++e)
+      if (e < md[t].y) acc[t] = fmaf(__uint_as_float(ev[t][e].x), DIFF ? vj[t][e] - vi[t] : vj[t][e], acc[t]);
+}
+
+// Common entry of the staged kernels: barriers, the dependency wait, and the stop flag of the
+// solve (false: the block leaves at once, before any copy is issued).
+__device__ __forceinline__ bool stream_enter(State* st, unsigned long long* full, unsigned long long* empty,
+                                             int* s_stop, bool loop_start, unsigned long long cond) {
+  stream_init_barriers(full, empty);
+  pdl_enter();
+  if (threadIdx.x == 0) {
+    // the loop-body bound of k_spmv_pq (the staged product starts the body in its place)
+    if (loop_start && blockIdx.x == 0 && cond && atomicAdd(&st->guard, 1) >= st->maxit + 2) stream_fail(st, cond);
+    *s_stop = st->conv;
+  }
+  __syncthreads();
+  return *s_stop == 0;
+}
+
+// q = A p (difference form, FP32 inner solves) and (p, q); the last block sets alpha.
+// Entries are (value bits, column) pairs; the products are formed in the order of
+// row_fma_diff, so q is bit-identical to k_spmv_pq<float, 0>'s. Staged vectors: s = A 1, p.
+template <typename T, int K>
+__global__ void __launch_bounds__(kStreamThreads, 2) k_spmv_pq_stream(IterCtx<T> c, StreamPlan pl) {
+  static_assert(sizeof(T) == 4, "the staged product reads the FP32 (value, column) entries");
+  __shared__ unsigned long long full[kStreamMaxStages], empty[kStreamMaxStages];
+  __shared__ float red[kStreamThreads / 32 + 1];
+  __shared__ int s_stop;
+  State* st = c.st;
+  if (!stream_enter(st, full, empty, &s_stop, true, c.cond)) return;
+  const int warp = threadIdx.x >> 5, lane = lane_id();
+  float acc[1] = {0.f};
+  if (warp == kStreamWarps) {
+    const void* vec[2] = {c.rowsum, c.p};
+    if (lane == 0 && !stream_produce<2, 4>(pl, c.Av.meta, c.Av.ent, 8, vec, 2u, 0u, full, empty))
+      stream_fail(st, c.cond);
+  } else {
+    const float* __restrict__ p = c.p;
+    bool bad = false;
+    const bool ok = stream_consume<2, 4>(pl, full, empty, [&](const ChunkPos& cp, const StageView<2, 4>& sv) {
+      int4 md[K];
+      stream_slices<K>(sv, cp, warp, md);
+      float pv[K], q[K];
+#pragma unroll
+      for (int t = 0; t < K; ++t) {
+        const bool valid = lane < md[t].w;
+        const int li = md[t].z + lane - sv.a0;
+        pv[t] = valid ? sv.vecf(1)[li] : 0.f;
+        q[t] = fmaf(valid ? sv.vecf(0)[li] : 0.f, pv[t], 0.f);
+      }
+      staged_rows<K, true>(sv, md, lane, p, pv, q, bad);
+#pragma unroll
+      for (int t = 0; t < K; ++t)
+        if (lane < md[t].w) {
+          c.q[md[t].z + lane] = q[t];
+          acc[0] = fmaf(pv[t], q[t], acc[0]);
+        }
+    });
+    if (!ok || bad) stream_fail(st, c.cond);
+  }
+  if (grid_sum_multi<1>(acc, red, (float*)c.partials, &st->ticket[kTkSpmv]) && threadIdx.x == 0) {
+    const double pq = (double)red[0];
+    st->pq = pq;
+    st->pap = pq;
+    if (!(pq > 0.0) || !(st->rho > 0.0)) {
+      st->status = ESD_ERR_BREAKDOWN;
+      st->conv = 1;
+      st->alpha = 0.0;
+      end_loop(c.cond);
+    } else if (st->status != ESD_ERR_INTERNAL) {
+      const double a = st->rho / pq;
+      st->alpha = a;
+      c.ahist[st->iter] = a;
+    }
+  }
+}
+
+// One forward colour level (as k_fwd<float>): y_i = (r_i - sum_k l_ik y_k) / l_ii and
+// sum y_i^2; the same slot / last-launch protocol for rho. Staged vectors: r, 1/l_ii.
+template <typename T, int K>
+__global__ void __launch_bounds__(kStreamThreads, 2)
+    k_fwd_stream(IterCtx<T> c, StreamPlan pl, int slot, int nprev, const int* __restrict__ prevG) {
+  static_assert(sizeof(T) == 4, "the staged sweep reads the FP32 (value, column) entries");
+  __shared__ unsigned long long full[kStreamMaxStages], empty[kStreamMaxStages];
+  __shared__ float red[kStreamThreads / 32 + 1];
+  __shared__ double own_s;
+  __shared__ int s_stop;
+  State* st = c.st;
+  if (!stream_enter(st, full, empty, &s_stop, false, c.cond)) return;
+  const int warp = threadIdx.x >> 5, lane = lane_id();
+  float acc[1] = {0.f};
+  if (warp == kStreamWarps) {
+    const void* vec[2] = {c.r, c.inv_d};
+    if (lane == 0 && !stream_produce<2, 4>(pl, c.Lv.meta, c.Lv.ent, 8, vec, 0u, 0u, full, empty))
+      stream_fail(st, c.cond);
+  } else {
+    float* Y = c.Y;
+    const unsigned bwd0 = pl.set[0].bwd0;
+    bool bad = false;
+    const bool ok = stream_consume<2, 4>(pl, full, empty, [&](const ChunkPos& cp, const StageView<2, 4>& sv) {
+      int4 md[K];
+      stream_slices<K>(sv, cp, warp, md);
+      float d[K], y[K];
+      const float zero[K] = {};
+#pragma unroll
+      for (int t = 0; t < K; ++t) {
+        const bool valid = lane < md[t].w;
+        const int li = md[t].z + lane - sv.a0;
+        d[t] = valid ? sv.vecf(1)[li] : 0.f;
+        y[t] = valid ? sv.vecf(0)[li] : 0.f;
+      }
+      staged_rows<K, false>(sv, md, lane, Y, zero, y, bad);
+      const bool to_z = (bwd0 >> cp.range) & 1u;
+#pragma unroll
+      for (int t = 0; t < K; ++t)
+        if (lane < md[t].w) {
+          const float yv = y[t] * d[t];
+          acc[0] = fmaf(yv, yv, acc[0]);
+          Y[md[t].z + lane] = to_z ? yv * d[t] : yv;
+        }
+    });
+    if (!ok || bad) stream_fail(st, c.cond);
+  }
+  float* slots = (float*)c.rho_part;
+  if (slot >= 0) {
+    block_sum_multi<1>(acc, red);
+    if (threadIdx.x == 0) slots[(size_t)slot * c.rho_stride + blockIdx.x] = red[0];
+    return;
+  }
+  if (grid_sum_multi<1>(acc, red, (float*)c.partials, &st->ticket[kTkSweep])) {
+    if (threadIdx.x == 0) own_s = (double)red[0];
+    float acc2[1] = {0.f};
+    for (int k = 0; k < nprev; ++k) {
+      const int gk = prevG[k];
+      for (int b = threadIdx.x; b < gk; b += blockDim.x) acc2[0] += __ldcg(&slots[(size_t)k * c.rho_stride + b]);
+    }
+    block_sum_multi<1>(acc2, red);
+    if (threadIdx.x == 0 && st->status != ESD_ERR_INTERNAL)
+      finalize_rho(st, own_s + (double)red[0] + st->rho_acc + st->fu, c.bhist, c.cond);
+  }
+}
+
+// One backward colour level without subspace-correction terms (as k_bwd<float, 0>):
+// z_i = (y_i - sum_j l_ji z_j) / l_ii, p_i = z_i + beta p_i. Part-1 chunks hold the rows
+// whose z_i the forward sweep stored: direction update only. Staged vectors: y, 1/l_ii, p
+// (part 1: y, p).
+template <typename T, int K>
+__global__ void __launch_bounds__(kStreamThreads, 2) k_bwd_stream(IterCtx<T> c, StreamPlan pl) {
+  static_assert(sizeof(T) == 4, "the staged sweep reads the FP32 (value, column) entries");
+  __shared__ unsigned long long full[kStreamMaxStages], empty[kStreamMaxStages];
+  __shared__ int s_stop;
+  State* st = c.st;
+  if (!stream_enter(st, full, empty, &s_stop, false, c.cond)) return;
+  const int warp = threadIdx.x >> 5, lane = lane_id();
+  const float beta = (float)st->beta;
+  const bool first = st->iter == 0 || st->fresh_dir;
+  if (warp == kStreamWarps) {
+    const void* vec[3] = {c.Y, c.inv_d, c.p};
+    if (lane == 0 && !stream_produce<3, 4>(pl, c.Uv.meta, c.Uv.ent, 8, vec, 0u, 5u, full, empty))
+      stream_fail(st, c.cond);
+  } else {
+    float* Y = c.Y;
+    bool bad = false;
+    const bool ok = stream_consume<3, 4>(pl, full, empty, [&](const ChunkPos& cp, const StageView<3, 4>& sv) {
+      const bool sweep = cp.part == 0;
+      int4 md[K];
+      stream_slices<K>(sv, cp, warp, md);
+      float d[K], z[K], pold[K];
+      const float zero[K] = {};
+#pragma unroll
+      for (int t = 0; t < K; ++t) {
+        if (!sweep) md[t].y = 0;  // rows whose z_i the forward sweep stored
+        const bool valid = lane < md[t].w;
+        const int li = md[t].z + lane - sv.a0;
+        z[t] = valid ? sv.vecf(0)[li] : 0.f;
+        d[t] = (valid && sweep) ? sv.vecf(1)[li] : 1.f;
+        pold[t] = (valid && !first) ? sv.vecf(2)[li] : 0.f;
+      }
+      if (sweep) staged_rows<K, false>(sv, md, lane, Y, zero, z, bad);
+#pragma unroll
+      for (int t = 0; t < K; ++t)
+        if (lane < md[t].w) {
+          const int i = md[t].z + lane;
+          const float zi = sweep ? z[t] * d[t] : z[t];
+          if (sweep) Y[i] = zi;
+          c.p[i] = first ? zi : fmaf(beta, pold[t], zi);
+        }
+    });
+    if (!ok || bad) stream_fail(st, c.cond);
+  }
+}
+
+// Whether the staged kernels are used (ESD_STREAM=0 in the environment turns them off, for
+// comparisons); read once per process.
+inline bool stream_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("ESD_STREAM");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+// Blocks of a staged launch: one wave (as many as fit with the plan's stage ring), never
+// more blocks than chunks.
+template <typename... KArgs>
+inline int stream_blocks(void (*kernel)(KArgs...), const StreamPlan& pl) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, std::unordered_map<int, int>> cache;  // kernel -> smem -> blocks per SM
+  const int smem = pl.ns * pl.stage;
+  int per_sm = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto& per = cache[(const void*)kernel];
+    if (per.empty())  // the largest stage ring a plan may have, set once per kernel
+      ESD_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kStreamRingCap));
+    auto it = per.find(smem);
+    if (it != per.end()) {
+      per_sm = it->second;
+    } else {
+      ESD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kStreamThreads, smem));
+      per_sm = std::max(1, per_sm);
+      per[smem] = per_sm;
+    }
+  }
+  return std::max(1, std::min(pl.total(), per_sm * (max_grid_blocks() / 4)));
+}
+
+// Launch a staged kernel on `blocks` blocks with programmatic stream serialisation on.
+template <typename... KArgs, typename... Args>
+inline void launch_stream(void (*kernel)(KArgs...), int blocks, const StreamPlan& pl, cudaStream_t s,
+                          Args&&... args) {
+  ESD_CHECK(pl.ns >= 2 && pl.ns <= kStreamMaxStages && pl.ns * pl.stage <= kStreamRingCap, ESD_ERR_INTERNAL,
+            "staged launch: stage ring out of range");
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(kStreamThreads);
+  cfg.dynamicSmemBytes = pl.ns * pl.stage;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  ESD_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+}
+
+// Dispatch on the slices per consumer warp of a plan.
+#define ESD_DISPATCH_K(Krt, ...)                                         \
+  switch (Krt) {                                                         \
+    case 1: { constexpr int KK = 1; __VA_ARGS__; } break;                \
+    case 2: { constexpr int KK = 2; __VA_ARGS__; } break;                \
+    case 4: { constexpr int KK = 4; __VA_ARGS__; } break;                \
+    default: throw Error(ESD_ERR_INTERNAL, "unsupported staged shape");  \
+  }
+
+}  // namespace esd
