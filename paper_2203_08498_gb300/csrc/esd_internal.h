@@ -86,6 +86,8 @@ struct esd_matrix {
   std::vector<esd::SliceSet> bwd_all_sets; // all backward levels incl. level 0 (apply)
   std::vector<esd::SliceSet> bwd0_sets;    // colours without later neighbours
   std::vector<int> fwd_wmax, bwd_wmax;     // widest L (U) row of each fwd_sets (bwd_sets) launch
+  esd::SliceSet upd_sets[2];               // forward level-0 slices, the other slices
+  bool upd_ok = false;                     // both fit kMaxRanges ranges
   esd::DevBuf fwd_grid64, fwd_grid32;      // int per forward launch: its grid (FP64 / FP32 kernel)
   esd::Sell A, L, U;  // L and U hold the strict factor entries negated (-l_ij)
   esd::DevBuf slice_flags;   // uint8 per slice: bit0 fwd level 0, bit1 bwd level 0

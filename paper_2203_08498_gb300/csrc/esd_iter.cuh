@@ -913,6 +913,44 @@ __host__ __device__ constexpr int update_pipe_minb() {
   return sizeof(T) == 4 ? ESD_UPDATE_PIPE_MINB_F32 : ESD_UPDATE_PIPE_MINB;
 }
 
+// The plain update's decision, taken by the last block with the grid totals rr = ||r||^2
+// and ry = sum y_i^2 over forward level 0: the convergence test, the sampling step, and
+// (finalize: no later forward launch) beta.
+template <int PRE>
+__device__ __forceinline__ void update_decide(State* st, double rr_new, double ry, int do_update, int finalize,
+                                              double* bhist, unsigned long long cond) {
+  if (do_update) {
+    st->rr = rr_new;
+    st->iter += 1;
+    st->pend_slot = -1;
+    st->fresh_dir = 0;
+  }
+  const double rr = st->rr;
+  bool stop = false;
+  if (!(rr == rr)) {
+    st->status = ESD_ERR_BREAKDOWN;
+    stop = true;
+  } else if (st->zero_rhs || rr <= st->tol2bb) {
+    stop = true;
+  } else if (st->iter >= st->maxit) {
+    st->status = ESD_ERR_MAXIT;
+    stop = true;
+  }
+  if ((!stop || st->defer_sample) && do_update && st->samp_m > 0) {
+    if (st->samp_method == 1) sampling_b(st, st->bb > 0.0 ? rr / st->bb : 0.0);
+    else sampling_a(st);
+  }
+  st->fu = 0.0;
+  if (PRE == ESD_PRECOND_IC0) st->rho_acc = ry;
+  if (stop) {
+    st->conv = 1;
+    end_loop(cond);
+  } else if (finalize) {
+    const double rho_ic = (PRE == ESD_PRECOND_IC0) ? st->rho_acc : rr;
+    finalize_rho(st, rho_ic, bhist, cond);
+  }
+}
+
 template <typename T>
 struct UpdStage {
   int4 md;
@@ -1003,40 +1041,8 @@ __global__ void __launch_bounds__(kBlock, update_pipe_minb<T>()) k_update_pipe(I
     cur = nxt;
     nxt = far;
   }
-  if (grid_sum_multi<2>(acc, red, (T*)c.partials, &st->ticket[kTkUpdate])) {
-    if (threadIdx.x == 0) {
-      if (do_update) {
-        st->rr = (double)red[0];
-        st->iter += 1;
-        st->pend_slot = -1;
-        st->fresh_dir = 0;
-      }
-      const double rr = st->rr;
-      bool stop = false;
-      if (!(rr == rr)) {
-        st->status = ESD_ERR_BREAKDOWN;
-        stop = true;
-      } else if (st->zero_rhs || rr <= st->tol2bb) {
-        stop = true;
-      } else if (st->iter >= st->maxit) {
-        st->status = ESD_ERR_MAXIT;
-        stop = true;
-      }
-      if ((!stop || st->defer_sample) && do_update && st->samp_m > 0) {
-        if (st->samp_method == 1) sampling_b(st, st->bb > 0.0 ? rr / st->bb : 0.0);
-        else sampling_a(st);
-      }
-      st->fu = 0.0;
-      if (PRE == ESD_PRECOND_IC0) st->rho_acc = (double)red[1];
-      if (stop) {
-        st->conv = 1;
-        end_loop(c.cond);
-      } else if (finalize) {
-        const double rho_ic = (PRE == ESD_PRECOND_IC0) ? st->rho_acc : rr;
-        finalize_rho(st, rho_ic, c.bhist, c.cond);
-      }
-    }
-  }
+  if (grid_sum_multi<2>(acc, red, (T*)c.partials, &st->ticket[kTkUpdate]) && threadIdx.x == 0)
+    update_decide<PRE>(st, (double)red[0], (double)red[1], do_update, finalize, c.bhist, c.cond);
 }
 
 // One forward colour level: y_i = (r_i - sum_k l_ik y_k) / l_ii and sum y_i^2. A launch that
@@ -1407,7 +1413,23 @@ template <typename T>
 static void launch_update(const IterCtx<T>& c, int do_update, int finalize, cudaStream_t s,
                           KernelMarks* marks = nullptr) {
   const int Mm = (c.mode == ESD_PLAIN) ? 0 : c.M;
-  if (c.mode == ESD_PLAIN && ESD_UPDATE_PIPE) {
+  const esd_matrix* P = c.P ? c.P : c.A;  // its forward level 0 rides on the update
+  if (sizeof(T) == 4 && c.mode == ESD_PLAIN && c.x64 && P->upd_ok && stream_enabled()) {
+    // FP32 plain update of the refinement form, vectors staged by bulk copies
+    if constexpr (sizeof(T) == 4) {
+      int K = 1;
+      const bool ic = c.pre == ESD_PRECOND_IC0;
+      const StreamPlan pl = ic ? stream_plan(P->upd_sets[0], P->upd_sets[1], 0, 0, 4, 1, &K)
+                               : stream_plan(SliceSet{}, c.A->all, 0, 0, 4, 1, &K);
+      if (ic) {
+        auto k = k_update_stream<T, ESD_PRECOND_IC0>;
+        launch_stream(k, stream_blocks(k, pl), pl, s, c, pl, do_update, finalize);
+      } else {
+        auto k = k_update_stream<T, ESD_PRECOND_NONE>;
+        launch_stream(k, stream_blocks(k, pl), pl, s, c, pl, do_update, finalize);
+      }
+    }
+  } else if (c.mode == ESD_PLAIN && ESD_UPDATE_PIPE) {
     if (c.pre == ESD_PRECOND_IC0) {
       auto k = k_update_pipe<T, ESD_PRECOND_IC0>;
       ESD_LAUNCH(k, c.A->all.total(), s, c, c.A->all, do_update, finalize);
@@ -1450,7 +1472,7 @@ static int fwd_grid(const esd_matrix* P, size_t l, StreamPlan* plan = nullptr, i
   if constexpr (sizeof(T) == 4) {
     if (stream_sweeps<T>(P)) {
       int K = 1;
-      const StreamPlan pl = stream_plan(set, SliceSet{}, P->fwd_wmax[l], 2, 4, &K);
+      const StreamPlan pl = stream_plan(set, SliceSet{}, P->fwd_wmax[l], 8, 2, 0, &K);
       if (plan) *plan = pl;
       if (K_out) *K_out = K;
       int G = 0;
@@ -1507,7 +1529,7 @@ static void launch_precond(const IterCtx<T>& c, cudaStream_t s, KernelMarks* mar
     if constexpr (sizeof(T) == 4) {
       if (staged && SCM == 0) {
         int K = 1;
-        const StreamPlan pl = stream_plan(sw, el, l < A->bwd_wmax.size() ? A->bwd_wmax[l] : 0, 3, 4, &K);
+        const StreamPlan pl = stream_plan(sw, el, l < A->bwd_wmax.size() ? A->bwd_wmax[l] : 0, 8, 3, 0, &K);
         ESD_DISPATCH_K(K, {
           auto k = k_bwd_stream<T, KK>;
           launch_stream(k, stream_blocks(k, pl), pl, s, c, pl);
@@ -1566,7 +1588,7 @@ void launch_iteration(const IterCtx<T>& c, cudaStream_t s, KernelMarks* marks) {
     // FP32 plain product: the matrix stream staged by bulk copies
     if constexpr (sizeof(T) == 4) {
       int K = 1;
-      const StreamPlan pl = stream_plan(all, SliceSet{}, c.A->A.wmax, 2, 4, &K);
+      const StreamPlan pl = stream_plan(all, SliceSet{}, c.A->A.wmax, 8, 2, 0, &K);
       ESD_DISPATCH_K(K, {
         auto k = k_spmv_pq_stream<T, KK>;
         launch_stream(k, stream_blocks(k, pl), pl, s, c, pl);

@@ -517,6 +517,34 @@ static void build_level_sets(esd_matrix* M, const std::vector<unsigned>& adj) {
       if (lv >= 1) M->bwd_sets.push_back(s); else M->bwd0_sets.push_back(s);
     }
   }
+  // the update's two classes of slices: forward level 0 (ranges split by the bwd0 flag) and
+  // the rest; the staged FP32 update needs each within kMaxRanges ranges
+  M->upd_sets[0] = SliceSet{};
+  M->upd_sets[1] = SliceSet{};
+  M->upd_ok = true;
+  {
+    int prev_key = -1;
+    for (int c = 0; c < C; ++c) {
+      if (nsl(c) == 0) continue;
+      const int cls = M->fwd_level[c] == 0 ? 0 : 1;
+      const unsigned b0 = (cls == 0 && M->bwd_level[c] == 0) ? 1u : 0u;
+      const int key = cls * 2 + (int)b0;
+      SliceSet& set = M->upd_sets[cls];
+      const bool extend = key == prev_key && set.nr > 0 &&
+                          set.begin[set.nr - 1] + (set.cum[set.nr] - set.cum[set.nr - 1]) == M->colour_first_slice[c];
+      if (extend) {
+        set.cum[set.nr] += nsl(c);
+      } else if (set.nr == kMaxRanges) {
+        M->upd_ok = false;
+      } else {
+        set.begin[set.nr] = M->colour_first_slice[c];
+        set.cum[set.nr + 1] = set.cum[set.nr] + nsl(c);
+        if (b0) set.bwd0 |= 1u << set.nr;
+        ++set.nr;
+      }
+      prev_key = key;
+    }
+  }
   // the "all slices" set
   SliceSet all{};
   all.nr = 1;

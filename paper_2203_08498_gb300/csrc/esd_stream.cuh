@@ -62,38 +62,59 @@ inline ChunkMap chunk_map(const SliceSet& set, int cs) {
 // 16-byte boundaries.
 __host__ __device__ constexpr int stream_vcap(int cs, int vec_bytes) { return cs * kSlice + 2 * (16 / vec_bytes); }
 
-// Bytes of one stage: metas, nvec row vectors of vec_bytes elements, then the entries of cs
-// slices of at most wmax entries per row.
-__host__ __device__ constexpr int stream_stage_bytes(int cs, int wmax, int entry_bytes, int nvec, int vec_bytes) {
-  return cs * 16 + nvec * stream_vcap(cs, vec_bytes) * vec_bytes + cs * wmax * kSlice * entry_bytes;
+// The row vectors a staged kernel copies with every chunk, in stage order: element bytes (4
+// or 8), the vectors copied with an evict-last L2 policy (other rows gather them; the rest
+// evict-first), and those copied for part-1 chunks (part-0 chunks copy all).
+template <int NV>
+struct VecSet {
+  const void* ptr[NV];
+  int vb[NV];
+  unsigned keep;
+  unsigned part1;
+};
+
+// Matrix entries of a staged kernel: one or two arrays per entry (FP32: (value, column)
+// pairs; FP64: columns, then values), eb[a] bytes per entry; none for vector-only kernels.
+struct EntSet {
+  const void* ptr[2];
+  int eb[2];
+  int n;
+};
+
+// Bytes of one stage: metas, row vectors (vbytes: the sum of their element bytes), then the
+// entries of cs slices of at most wmax entries per row (ebytes per entry over all arrays).
+__host__ __device__ constexpr int stream_stage_bytes(int cs, int wmax, int ebytes, int nv4, int nv8) {
+  return cs * 16 + nv4 * stream_vcap(cs, 4) * 4 + nv8 * stream_vcap(cs, 8) * 8 + cs * wmax * kSlice * ebytes;
 }
 
 // The chunks of one staged launch: those of set 0 (matrix entries and row vectors staged),
-// then those of set 1 (row vectors only; empty unless a kernel has such rows). cs = slices
-// per chunk (kStreamWarps x K), ns = stages in the ring, stage = bytes of one stage.
+// then those of set 1 (row vectors only). cs = slices per chunk (kStreamWarps x K), ns =
+// stages in the ring, stage = bytes of one stage, ecap = entries per entry array in a stage.
 struct StreamPlan {
   SliceSet set[2];
   ChunkMap cm[2];
-  int cs, ns, stage;
+  int cs, ns, stage, ecap;
   __host__ __device__ int total() const { return cm[0].total() + cm[1].total(); }
 };
 
-// Shape of a launch whose set-0 rows hold at most wmax entries: K, the slices a consumer warp
-// takes per chunk (K x wmax <= kStreamWmax, stage <= kStreamStageCap), and the stages that fit
-// kStreamRingCap (3, else 2).
-inline StreamPlan stream_plan(const SliceSet& with_entries, const SliceSet& vectors_only, int wmax, int nvec,
-                              int vec_bytes, int* K_out) {
+// Plan of a launch whose set-0 rows hold at most wmax entries (ebytes per entry; 0 for a
+// vector-only kernel) and that stages nv4 4-byte and nv8 8-byte row vectors: K, the slices a
+// consumer warp takes per chunk (the largest of 4, 2, 1 with K x wmax <= kmax_w and a stage
+// of at most kStreamStageCap bytes), and the stages that fit kStreamRingCap (3, else 2).
+inline StreamPlan stream_plan(const SliceSet& with_entries, const SliceSet& vectors_only, int wmax, int ebytes,
+                              int nv4, int nv8, int* K_out, int kmax_w = kStreamWmax) {
   int K = 1;
   for (int k = kStreamMaxK; k > 1; k /= 2)
-    if (k * std::max(wmax, 1) <= kStreamWmax &&
-        stream_stage_bytes(kStreamWarps * k, wmax, 8, nvec, vec_bytes) <= kStreamStageCap) {
+    if (k * std::max(wmax, 1) <= kmax_w &&
+        stream_stage_bytes(kStreamWarps * k, wmax, ebytes, nv4, nv8) <= kStreamStageCap) {
       K = k;
       break;
     }
   StreamPlan pl{};
   pl.cs = kStreamWarps * K;
-  pl.stage = stream_stage_bytes(pl.cs, wmax, 8, nvec, vec_bytes);
+  pl.stage = stream_stage_bytes(pl.cs, wmax, ebytes, nv4, nv8);
   pl.ns = 3 * pl.stage <= kStreamRingCap ? 3 : 2;
+  pl.ecap = pl.cs * wmax * kSlice;
   pl.set[0] = with_entries;
   pl.set[1] = vectors_only;
   pl.cm[0] = chunk_map(with_entries, pl.cs);
@@ -200,26 +221,20 @@ __device__ __forceinline__ void stream_fail(State* st, unsigned long long cond) 
   end_loop(cond);
 }
 
-// First element of the widened row range of a chunk whose first row is z0 (16-byte aligned).
-template <int VB>
-__device__ __forceinline__ int stream_row0(int z0) {
-  return z0 & ~(16 / VB - 1);
-}
+// First element of the widened row range of a chunk whose first row is z0, for elements of
+// vb bytes (16-byte aligned).
+__host__ __device__ __forceinline__ int stream_row0(int z0, int vb) { return z0 & ~(16 / vb - 1); }
 
 // Producer loop of one block: chunks blockIdx.x, blockIdx.x + G, ... into the stage ring.
-// A stage receives the chunk's metas, row vectors (vec[v][a0 .. a1): the chunk's rows
-// widened to 16-byte boundaries; every vector holds a multiple of 32 elements, so the
-// widened end stays inside it) and, for chunks of part 0, the entries. Part-1 chunks copy
-// only the vectors of part1_vmask. Vectors in keep_mask are copied with an evict-last L2
-// policy (other rows gather them), the rest evict-first. Returns false if a wait ran out;
+// A stage receives the chunk's metas, its row vectors (vec[v][a0 .. a1): the chunk's rows
+// widened to 16-byte boundaries; every vector holds a multiple of 32 elements, so the widened
+// end stays inside it) and, for part-0 chunks, its entries. Returns false if a wait ran out;
 // on return every copy it issued has landed (or a drain wait ran out, reported as well).
-template <int NV, int VB>
-__device__ __forceinline__ bool stream_produce(const StreamPlan& pl, const int4* meta, const void* ent,
-                                               int entry_bytes, const void* const* vec, unsigned keep_mask,
-                                               unsigned part1_vmask, unsigned long long* full,
+template <int NV>
+__device__ __forceinline__ bool stream_produce(const StreamPlan& pl, const int4* meta, const EntSet& es,
+                                               const VecSet<NV>& vs, unsigned long long* full,
                                                unsigned long long* empty) {
   const unsigned long long pol_first = l2_evict_first(), pol_last = l2_evict_last();
-  const int vcap = stream_vcap(pl.cs, VB);
   const int G = gridDim.x, nch = pl.total(), ns = pl.ns;
   bool ok = true;
   int j = 0;
@@ -232,26 +247,37 @@ __device__ __forceinline__ bool stream_produce(const StreamPlan& pl, const int4*
     const ChunkPos cp = chunk_pos(pl, ch);
     const int4 m0 = meta[cp.s0], m1 = meta[cp.s1 - 1];
     const unsigned mbytes = (unsigned)(cp.s1 - cp.s0) * 16u;
-    const unsigned ebytes = cp.part ? 0u : (unsigned)(m1.x + m1.y * kSlice - m0.x) * (unsigned)entry_bytes;
-    const unsigned vmask = cp.part ? part1_vmask : ~0u;
-    const int a0 = stream_row0<VB>(m0.z);
-    const int a1 = (m1.z + m1.w + (16 / VB - 1)) & ~(16 / VB - 1);
-    const unsigned vbytes = (unsigned)(a1 - a0) * VB;
-    unsigned tx = mbytes + ebytes;
+    const unsigned nent = cp.part ? 0u : (unsigned)(m1.x + m1.y * kSlice - m0.x);
+    const unsigned vmask = cp.part ? vs.part1 : ~0u;
+    const int z1 = m1.z + m1.w;
+    unsigned tx = mbytes;
 #pragma unroll
     for (int v = 0; v < NV; ++v)
-      if ((vmask >> v) & 1u) tx += vbytes;
+      if ((vmask >> v) & 1u) {
+        const int q = 16 / vs.vb[v];
+        tx += (unsigned)(((z1 + q - 1) & ~(q - 1)) - stream_row0(m0.z, vs.vb[v])) * vs.vb[v];
+      }
+    for (int a = 0; a < es.n; ++a) tx += nent * es.eb[a];
     unsigned char* st = esd_dyn_smem + (size_t)k * pl.stage;
     mbar_arrive_expect_tx(&full[k], tx);
     bulk_load(st, meta + cp.s0, mbytes, &full[k], pol_first);
+    unsigned char* dst = st + pl.cs * 16;
 #pragma unroll
-    for (int v = 0; v < NV; ++v)
-      if ((vmask >> v) & 1u)
-        bulk_load(st + pl.cs * 16 + v * vcap * VB, (const unsigned char*)vec[v] + (size_t)a0 * VB, vbytes, &full[k],
-                  ((keep_mask >> v) & 1u) ? pol_last : pol_first);
-    if (ebytes)
-      bulk_load(st + pl.cs * 16 + NV * vcap * VB, (const unsigned char*)ent + (size_t)m0.x * entry_bytes, ebytes,
-                &full[k], pol_first);
+    for (int v = 0; v < NV; ++v) {
+      const int vb = vs.vb[v], q = 16 / vb;
+      if ((vmask >> v) & 1u) {
+        const int a0 = stream_row0(m0.z, vb), a1 = (z1 + q - 1) & ~(q - 1);
+        bulk_load(dst, (const unsigned char*)vs.ptr[v] + (size_t)a0 * vb, (unsigned)(a1 - a0) * vb, &full[k],
+                  ((vs.keep >> v) & 1u) ? pol_last : pol_first);
+      }
+      dst += stream_vcap(pl.cs, vb) * vb;
+    }
+    if (nent)
+      for (int a = 0; a < es.n; ++a) {
+        bulk_load(dst, (const unsigned char*)es.ptr[a] + (size_t)m0.x * es.eb[a], nent * es.eb[a], &full[k],
+                  pol_first);
+        dst += (size_t)pl.ecap * es.eb[a];
+      }
   }
   // drain: the last use of every stage this block issued
   for (int k = 0; k < ns && k < j; ++k) {
@@ -261,19 +287,24 @@ __device__ __forceinline__ bool stream_produce(const StreamPlan& pl, const int4*
   return ok;
 }
 
-// One stage as a consumer warp sees it.
-template <int NV, int VB>
+// One stage as a consumer warp sees it: the chunk's metas, the row vectors (element i of
+// the chunk's rows is vec<V>(v, i)) and the entry arrays (entry x of the chunk at
+// ent<E>(a)[x - x0]).
+template <int NV>
 struct StageView {
   const unsigned char* base;
-  int cs;
-  int a0;  // first row of the staged vectors
-  int x0;  // entry offset of the chunk's first slice
+  const unsigned char* vptr[NV];
+  const unsigned char* eptr[2];
+  int a0[NV];
+  int x0;
   __device__ __forceinline__ const int4* meta() const { return reinterpret_cast<const int4*>(base); }
-  __device__ __forceinline__ const float* vecf(int v) const {
-    return reinterpret_cast<const float*>(base + cs * 16 + v * stream_vcap(cs, VB) * VB);
+  template <typename V>
+  __device__ __forceinline__ V vec(int v, int i) const {
+    return reinterpret_cast<const V*>(vptr[v])[i - a0[v]];
   }
-  __device__ __forceinline__ const uint2* ent() const {
-    return reinterpret_cast<const uint2*>(base + cs * 16 + NV * stream_vcap(cs, VB) * VB);
+  template <typename E>
+  __device__ __forceinline__ const E* ent(int a) const {
+    return reinterpret_cast<const E*>(eptr[a]);
   }
 };
 
@@ -291,19 +322,26 @@ __device__ __forceinline__ void stream_init_barriers(unsigned long long* full, u
 // Consumer loop of one warp: for each chunk of this block, wait for its stage, call
 // f(chunk position, stage view), then release the stage. Every consumer warp takes part in
 // every chunk (the empty barrier counts kStreamWarps arrivals). False if a wait ran out.
-template <int NV, int VB, typename F>
-__device__ __forceinline__ bool stream_consume(const StreamPlan& pl, unsigned long long* full,
-                                               unsigned long long* empty, F&& f) {
+template <int NV, typename F>
+__device__ __forceinline__ bool stream_consume(const StreamPlan& pl, const EntSet& es, const VecSet<NV>& vs,
+                                               unsigned long long* full, unsigned long long* empty, F&& f) {
   const int G = gridDim.x, nch = pl.total(), ns = pl.ns;
   int j = 0;
   for (int ch = blockIdx.x; ch < nch; ch += G, ++j) {
     const int k = j % ns, u = j / ns;
     if (!mbar_wait(&full[k], (unsigned)u & 1u)) return false;
-    StageView<NV, VB> sv;
+    StageView<NV> sv;
     sv.base = esd_dyn_smem + (size_t)k * pl.stage;
-    sv.cs = pl.cs;
     const int4 m0 = sv.meta()[0];
-    sv.a0 = stream_row0<VB>(m0.z);
+    const unsigned char* q = sv.base + pl.cs * 16;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      sv.vptr[v] = q;
+      sv.a0[v] = stream_row0(m0.z, vs.vb[v]);
+      q += stream_vcap(pl.cs, vs.vb[v]) * vs.vb[v];
+    }
+    sv.eptr[0] = q;
+    sv.eptr[1] = q + (size_t)pl.ecap * es.eb[0];
     sv.x0 = m0.x;
     f(chunk_pos(pl, ch), sv);
     __syncwarp();
@@ -314,9 +352,8 @@ __device__ __forceinline__ bool stream_consume(const StreamPlan& pl, unsigned lo
 
 // The K slices of one consumer warp in a chunk (warp, warp + kStreamWarps, ...): their metas
 // (zero for slices past the chunk's end: no rows, no entries).
-template <int K, int NV, int VB>
-__device__ __forceinline__ void stream_slices(const StageView<NV, VB>& sv, const ChunkPos& cp, int warp,
-                                              int4 (&md)[K]) {
+template <int K, int NV>
+__device__ __forceinline__ void stream_slices(const StageView<NV>& sv, const ChunkPos& cp, int warp, int4 (&md)[K]) {
 #pragma unroll
   for (int t = 0; t < K; ++t) {
     const int ls = warp + t * kStreamWarps;
@@ -324,18 +361,19 @@ __device__ __forceinline__ void stream_slices(const StageView<NV, VB>& sv, const
   }
 }
 
-// Row products of K slices of one lane from staged entries: acc[t] += sum_e val_e * (v[col_e]
-// - vi[t]) (vi = 0 in the plain form), the entries of a row in stored order, as row_fma and
-// row_fma_diff take them. Every gather of the K rows is issued before the first FMA. A row
-// wider than kStreamWmax / K (which the launch plan excludes) is reported through `bad`.
-template <int K, bool DIFF, int NV, int VB>
-__device__ __forceinline__ void staged_rows(const StageView<NV, VB>& sv, const int4 (&md)[K], int lane,
+// Row products of K slices of one lane from staged FP32 (value, column) entries: acc[t] +=
+// sum_e val_e * (v[col_e] - vi[t]) (vi = 0 in the plain form), the entries of a row in stored
+// order, as row_fma and row_fma_diff take them. Every gather of the K rows is issued before
+// the first FMA. A row wider than kStreamWmax / K (which the launch plan excludes) is
+// reported through `bad`.
+template <int K, bool DIFF, int NV>
+__device__ __forceinline__ void staged_rows(const StageView<NV>& sv, const int4 (&md)[K], int lane,
                                             const float* __restrict__ v, const float (&vi)[K], float (&acc)[K],
                                             bool& bad) {
   constexpr int W = kStreamWmax / K;
   uint2 ev[K][W];
   float vj[K][W];
-  const uint2* ent = sv.ent();
+  const uint2* ent = sv.template ent<uint2>(0);
 #pragma unroll
   for (int t = 0; t < K; ++t) {
     bad |= md[t].y > W;
@@ -380,24 +418,24 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_spmv_pq_stream(IterCtx<T>
   State* st = c.st;
   if (!stream_enter(st, full, empty, &s_stop, true, c.cond)) return;
   const int warp = threadIdx.x >> 5, lane = lane_id();
+  const EntSet es{{c.Av.ent, nullptr}, {8, 0}, 1};
+  const VecSet<2> vs{{c.rowsum, c.p}, {4, 4}, 2u, 0u};
   float acc[1] = {0.f};
   if (warp == kStreamWarps) {
-    const void* vec[2] = {c.rowsum, c.p};
-    if (lane == 0 && !stream_produce<2, 4>(pl, c.Av.meta, c.Av.ent, 8, vec, 2u, 0u, full, empty))
-      stream_fail(st, c.cond);
+    if (lane == 0 && !stream_produce(pl, c.Av.meta, es, vs, full, empty)) stream_fail(st, c.cond);
   } else {
     const float* __restrict__ p = c.p;
     bool bad = false;
-    const bool ok = stream_consume<2, 4>(pl, full, empty, [&](const ChunkPos& cp, const StageView<2, 4>& sv) {
+    const bool ok = stream_consume(pl, es, vs, full, empty, [&](const ChunkPos& cp, const StageView<2>& sv) {
       int4 md[K];
       stream_slices<K>(sv, cp, warp, md);
       float pv[K], q[K];
 #pragma unroll
       for (int t = 0; t < K; ++t) {
         const bool valid = lane < md[t].w;
-        const int li = md[t].z + lane - sv.a0;
-        pv[t] = valid ? sv.vecf(1)[li] : 0.f;
-        q[t] = fmaf(valid ? sv.vecf(0)[li] : 0.f, pv[t], 0.f);
+        const int i = md[t].z + lane;
+        pv[t] = valid ? sv.template vec<float>(1, i) : 0.f;
+        q[t] = fmaf(valid ? sv.template vec<float>(0, i) : 0.f, pv[t], 0.f);
       }
       staged_rows<K, true>(sv, md, lane, p, pv, q, bad);
 #pragma unroll
@@ -426,6 +464,61 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_spmv_pq_stream(IterCtx<T>
   }
 }
 
+// x += alpha p (the FP64 iterate of the refinement form), r -= alpha q, ||r||^2, the pending
+// sample, and forward level 0 (y = r / l_ii, sum y^2): the plain FP32 update of k_update_pipe
+// with its vectors staged. Part 0 holds the forward-level-0 rows (x, p, q, r, 1/l_ii staged),
+// part 1 the others (x, p, q, r). do_update = 0 runs the level-0 epilogue on r alone.
+template <typename T, int PRE>
+__global__ void __launch_bounds__(kStreamThreads, 2)
+    k_update_stream(IterCtx<T> c, StreamPlan pl, int do_update, int finalize) {
+  static_assert(sizeof(T) == 4, "the staged update is the FP32 inner solver's");
+  __shared__ unsigned long long full[kStreamMaxStages], empty[kStreamMaxStages];
+  __shared__ float red[2 * (kStreamThreads / 32 + 1)];
+  __shared__ int s_stop;
+  State* st = c.st;
+  if (!stream_enter(st, full, empty, &s_stop, false, c.cond)) return;
+  const int warp = threadIdx.x >> 5, lane = lane_id();
+  const float alpha = (float)st->alpha;
+  const double alpha_d = st->alpha;
+  const int pend = do_update ? st->pend_slot : -1;
+  const EntSet es{{nullptr, nullptr}, {0, 0}, 0};
+  const VecSet<5> vs{{c.x64, c.p, c.q, c.r, c.inv_d}, {8, 4, 4, 4, 4}, 0u, 15u};
+  float acc[2] = {0.f, 0.f};
+  if (warp == kStreamWarps) {
+    if (lane == 0 && !stream_produce(pl, c.Av.meta, es, vs, full, empty)) stream_fail(st, c.cond);
+  } else {
+    const unsigned bwd0 = pl.set[0].bwd0;
+    const bool ok = stream_consume(pl, es, vs, full, empty, [&](const ChunkPos& cp, const StageView<5>& sv) {
+      const bool lev0 = PRE == ESD_PRECOND_IC0 && cp.part == 0;
+      const bool to_z = lev0 && ((bwd0 >> cp.range) & 1u);
+      for (int ls = warp; ls < cp.s1 - cp.s0; ls += kStreamWarps) {
+        const int4 md = sv.meta()[ls];
+        if (lane >= md.w) continue;
+        const int i = md.z + lane;
+        float ri = sv.template vec<float>(3, i);
+        if (do_update) {
+          const double xi = sv.template vec<double>(0, i);
+          if (pend >= 0 && c.samples64) c.samples64[(size_t)pend * c.ld + i] = xi;
+          c.x64[i] = fma(alpha_d, (double)sv.template vec<float>(1, i), xi);
+          ri = fmaf(-alpha, sv.template vec<float>(2, i), ri);
+          c.r[i] = ri;
+          acc[0] = fmaf(ri, ri, acc[0]);
+        }
+        if (lev0) {
+          const float d = sv.template vec<float>(4, i);
+          const float yv = ri * d;
+          acc[1] = fmaf(yv, yv, acc[1]);
+          c.Y[i] = to_z ? yv * d : yv;
+        }
+      }
+    });
+    if (!ok) stream_fail(st, c.cond);
+  }
+  if (grid_sum_multi<2>(acc, red, (float*)c.partials, &st->ticket[kTkUpdate]) && threadIdx.x == 0 &&
+      st->status != ESD_ERR_INTERNAL)
+    update_decide<PRE>(st, (double)red[0], (double)red[1], do_update, finalize, c.bhist, c.cond);
+}
+
 // One forward colour level (as k_fwd<float>): y_i = (r_i - sum_k l_ik y_k) / l_ii and
 // sum y_i^2; the same slot / last-launch protocol for rho. Staged vectors: r, 1/l_ii.
 template <typename T, int K>
@@ -439,16 +532,16 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
   State* st = c.st;
   if (!stream_enter(st, full, empty, &s_stop, false, c.cond)) return;
   const int warp = threadIdx.x >> 5, lane = lane_id();
+  const EntSet es{{c.Lv.ent, nullptr}, {8, 0}, 1};
+  const VecSet<2> vs{{c.r, c.inv_d}, {4, 4}, 0u, 0u};
   float acc[1] = {0.f};
   if (warp == kStreamWarps) {
-    const void* vec[2] = {c.r, c.inv_d};
-    if (lane == 0 && !stream_produce<2, 4>(pl, c.Lv.meta, c.Lv.ent, 8, vec, 0u, 0u, full, empty))
-      stream_fail(st, c.cond);
+    if (lane == 0 && !stream_produce(pl, c.Lv.meta, es, vs, full, empty)) stream_fail(st, c.cond);
   } else {
     float* Y = c.Y;
     const unsigned bwd0 = pl.set[0].bwd0;
     bool bad = false;
-    const bool ok = stream_consume<2, 4>(pl, full, empty, [&](const ChunkPos& cp, const StageView<2, 4>& sv) {
+    const bool ok = stream_consume(pl, es, vs, full, empty, [&](const ChunkPos& cp, const StageView<2>& sv) {
       int4 md[K];
       stream_slices<K>(sv, cp, warp, md);
       float d[K], y[K];
@@ -456,9 +549,9 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
 #pragma unroll
       for (int t = 0; t < K; ++t) {
         const bool valid = lane < md[t].w;
-        const int li = md[t].z + lane - sv.a0;
-        d[t] = valid ? sv.vecf(1)[li] : 0.f;
-        y[t] = valid ? sv.vecf(0)[li] : 0.f;
+        const int i = md[t].z + lane;
+        d[t] = valid ? sv.template vec<float>(1, i) : 0.f;
+        y[t] = valid ? sv.template vec<float>(0, i) : 0.f;
       }
       staged_rows<K, false>(sv, md, lane, Y, zero, y, bad);
       const bool to_z = (bwd0 >> cp.range) & 1u;
@@ -505,14 +598,14 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_bwd_stream(IterCtx<T> c, 
   const int warp = threadIdx.x >> 5, lane = lane_id();
   const float beta = (float)st->beta;
   const bool first = st->iter == 0 || st->fresh_dir;
+  const EntSet es{{c.Uv.ent, nullptr}, {8, 0}, 1};
+  const VecSet<3> vs{{c.Y, c.inv_d, c.p}, {4, 4, 4}, 0u, 5u};
   if (warp == kStreamWarps) {
-    const void* vec[3] = {c.Y, c.inv_d, c.p};
-    if (lane == 0 && !stream_produce<3, 4>(pl, c.Uv.meta, c.Uv.ent, 8, vec, 0u, 5u, full, empty))
-      stream_fail(st, c.cond);
+    if (lane == 0 && !stream_produce(pl, c.Uv.meta, es, vs, full, empty)) stream_fail(st, c.cond);
   } else {
     float* Y = c.Y;
     bool bad = false;
-    const bool ok = stream_consume<3, 4>(pl, full, empty, [&](const ChunkPos& cp, const StageView<3, 4>& sv) {
+    const bool ok = stream_consume(pl, es, vs, full, empty, [&](const ChunkPos& cp, const StageView<3>& sv) {
       const bool sweep = cp.part == 0;
       int4 md[K];
       stream_slices<K>(sv, cp, warp, md);
@@ -522,10 +615,10 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_bwd_stream(IterCtx<T> c, 
       for (int t = 0; t < K; ++t) {
         if (!sweep) md[t].y = 0;  // rows whose z_i the forward sweep stored
         const bool valid = lane < md[t].w;
-        const int li = md[t].z + lane - sv.a0;
-        z[t] = valid ? sv.vecf(0)[li] : 0.f;
-        d[t] = (valid && sweep) ? sv.vecf(1)[li] : 1.f;
-        pold[t] = (valid && !first) ? sv.vecf(2)[li] : 0.f;
+        const int i = md[t].z + lane;
+        z[t] = valid ? sv.template vec<float>(0, i) : 0.f;
+        d[t] = (valid && sweep) ? sv.template vec<float>(1, i) : 1.f;
+        pold[t] = (valid && !first) ? sv.template vec<float>(2, i) : 0.f;
       }
       if (sweep) staged_rows<K, false>(sv, md, lane, Y, zero, z, bad);
 #pragma unroll
