@@ -868,7 +868,8 @@ def roofline(prof, p, args, mode, esd, peaks):
     f_hbm = gbs / peaks["hbm_gbs"]
     alu_peak = FP32_NOMINAL_TFLOPS if args.precision == "fp32" else FP64_NOMINAL_TFLOPS
     f_alu = tflops / alu_peak
-    traffic = read_traffic(name) if args.config == "c2" and args.precision == "fp64" else None
+    full_size = args.grid == CONFIGS[args.config]["grid"]
+    traffic = read_traffic(TRAFFIC.get((args.config, args.precision, name))) if full_size else None
     if f_alu > f_hbm:
         roof = {"bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": f_alu, "traffic": traffic, "kernel": name,
@@ -883,9 +884,19 @@ def roofline(prof, p, args, mode, esd, peaks):
     return roof, times
 
 
-def read_traffic(kernel):
+# ncu summaries that hold the DRAM traffic of a configuration's dominant kernel per launch at
+# the configuration's full size: (config, precision, kernel) -> file under profiles/
+TRAFFIC = {
+    ("c2", "fp64", "spmv_pq"): "spmv_pq_128cube_traffic.txt",
+    ("c5", "fp32", "spmv_pq"): "spmv_pq_stream_fp32_256cube_traffic.txt",
+}
+
+
+def read_traffic(fname):
     """DRAM bytes per launch from the committed ncu summary of this kernel, if any."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_128cube_traffic.txt")
+    if fname is None:
+        return None
+    path = os.path.join(ROOT, "profiles", fname)
     try:
         for ln in open(path):
             if ln.startswith("traffic_bytes_per_launch:"):

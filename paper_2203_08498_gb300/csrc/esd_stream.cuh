@@ -391,6 +391,17 @@ __device__ __forceinline__ void staged_rows(const StageView<NV>& sv, const int4 
       if (e < md[t].y) acc[t] = fmaf(__uint_as_float(ev[t][e].x), DIFF ? vj[t][e] - vi[t] : vj[t][e], acc[t]);
 }
 
+// Compensated (Kahan) accumulation of one thread's partial sum: sum += v, with the rounding
+// error of each addition carried in c. A thread of a staged kernel adds up to a few hundred
+// terms of a dot product; with compensation its partial sum is exact to about the last bit
+// whatever their number.
+__device__ __forceinline__ void kahan_add(float& sum, float& c, float v) {
+  const float y = __fsub_rn(v, c);
+  const float t = __fadd_rn(sum, y);
+  c = __fsub_rn(__fsub_rn(t, sum), y);
+  sum = t;
+}
+
 // Common entry of the staged kernels: barriers, the dependency wait, and the stop flag of the
 // solve (false: the block leaves at once, before any copy is issued).
 __device__ __forceinline__ bool stream_enter(State* st, unsigned long long* full, unsigned long long* empty,
@@ -420,7 +431,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_spmv_pq_stream(IterCtx<T>
   const int warp = threadIdx.x >> 5, lane = lane_id();
   const EntSet es{{c.Av.ent, nullptr}, {8, 0}, 1};
   const VecSet<2> vs{{c.rowsum, c.p}, {4, 4}, 2u, 0u};
-  float acc[1] = {0.f};
+  float acc[1] = {0.f}, cmp[1] = {0.f};
   if (warp == kStreamWarps) {
     if (lane == 0 && !stream_produce(pl, c.Av.meta, es, vs, full, empty)) stream_fail(st, c.cond);
   } else {
@@ -442,11 +453,12 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_spmv_pq_stream(IterCtx<T>
       for (int t = 0; t < K; ++t)
         if (lane < md[t].w) {
           c.q[md[t].z + lane] = q[t];
-          acc[0] = fmaf(pv[t], q[t], acc[0]);
+          kahan_add(acc[0], cmp[0], __fmul_rn(pv[t], q[t]));
         }
     });
     if (!ok || bad) stream_fail(st, c.cond);
   }
+  acc[0] = __fsub_rn(acc[0], cmp[0]);
   if (grid_sum_multi<1>(acc, red, (float*)c.partials, &st->ticket[kTkSpmv]) && threadIdx.x == 0) {
     const double pq = (double)red[0];
     st->pq = pq;
@@ -483,7 +495,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
   const int pend = do_update ? st->pend_slot : -1;
   const EntSet es{{nullptr, nullptr}, {0, 0}, 0};
   const VecSet<5> vs{{c.x64, c.p, c.q, c.r, c.inv_d}, {8, 4, 4, 4, 4}, 0u, 15u};
-  float acc[2] = {0.f, 0.f};
+  float acc[2] = {0.f, 0.f}, cmp[2] = {0.f, 0.f};
   if (warp == kStreamWarps) {
     if (lane == 0 && !stream_produce(pl, c.Av.meta, es, vs, full, empty)) stream_fail(st, c.cond);
   } else {
@@ -502,18 +514,20 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
           c.x64[i] = fma(alpha_d, (double)sv.template vec<float>(1, i), xi);
           ri = fmaf(-alpha, sv.template vec<float>(2, i), ri);
           c.r[i] = ri;
-          acc[0] = fmaf(ri, ri, acc[0]);
+          kahan_add(acc[0], cmp[0], __fmul_rn(ri, ri));
         }
         if (lev0) {
           const float d = sv.template vec<float>(4, i);
           const float yv = ri * d;
-          acc[1] = fmaf(yv, yv, acc[1]);
+          kahan_add(acc[1], cmp[1], __fmul_rn(yv, yv));
           c.Y[i] = to_z ? yv * d : yv;
         }
       }
     });
     if (!ok) stream_fail(st, c.cond);
   }
+  acc[0] = __fsub_rn(acc[0], cmp[0]);
+  acc[1] = __fsub_rn(acc[1], cmp[1]);
   if (grid_sum_multi<2>(acc, red, (float*)c.partials, &st->ticket[kTkUpdate]) && threadIdx.x == 0 &&
       st->status != ESD_ERR_INTERNAL)
     update_decide<PRE>(st, (double)red[0], (double)red[1], do_update, finalize, c.bhist, c.cond);
@@ -534,7 +548,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
   const int warp = threadIdx.x >> 5, lane = lane_id();
   const EntSet es{{c.Lv.ent, nullptr}, {8, 0}, 1};
   const VecSet<2> vs{{c.r, c.inv_d}, {4, 4}, 0u, 0u};
-  float acc[1] = {0.f};
+  float acc[1] = {0.f}, cmp[1] = {0.f};
   if (warp == kStreamWarps) {
     if (lane == 0 && !stream_produce(pl, c.Lv.meta, es, vs, full, empty)) stream_fail(st, c.cond);
   } else {
@@ -559,12 +573,13 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
       for (int t = 0; t < K; ++t)
         if (lane < md[t].w) {
           const float yv = y[t] * d[t];
-          acc[0] = fmaf(yv, yv, acc[0]);
+          kahan_add(acc[0], cmp[0], __fmul_rn(yv, yv));
           Y[md[t].z + lane] = to_z ? yv * d[t] : yv;
         }
     });
     if (!ok || bad) stream_fail(st, c.cond);
   }
+  acc[0] = __fsub_rn(acc[0], cmp[0]);
   float* slots = (float*)c.rho_part;
   if (slot >= 0) {
     block_sum_multi<1>(acc, red);
