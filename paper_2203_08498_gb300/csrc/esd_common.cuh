@@ -50,6 +50,10 @@ struct SellView {
   const int* col;
   const T* val;
   const uint2* ent = nullptr;  // FP32 copy: (value bits, column) per entry, one 8-byte load
+  // FP32 column-free copy (null when the part has none): metas, slot bases, values
+  const int4* ameta = nullptr;
+  const int* abase = nullptr;
+  const float* aval = nullptr;
 };
 
 // Device-resident scalar state of one solve. All Krylov scalars stay here; the host reads

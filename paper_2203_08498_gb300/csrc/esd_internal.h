@@ -46,6 +46,16 @@ struct Sell {
   DevBuf ent32;  // uint2 per entry: (float bits, column), so an FP32 entry is one 8-byte load
   long long entries = 0;
   int wmax = 0;  // widest slice (entries per row)
+  // Column-free FP32 copy for the staged kernels, built when every slice fits: slot k of
+  // slice s holds, in lane l, the entry of column abase[8 s + k] + l of row (first row + l),
+  // value 0 where that row has no such entry. The slot bases of a slice increase, so a row's
+  // entries keep their order. Pattern at creation, values with the other FP32 copies.
+  DevBuf ameta;  // int4 per slice: {value offset, slots, first row, rows}
+  DevBuf abase;  // int[kAffineSlots] per slice: the slot bases
+  DevBuf aval;   // float per slot entry (slots x 32 per slice)
+  bool affine = false;
+  int awmax = 0;              // most slots of a slice
+  std::vector<int> aslots;    // slots per slice (host)
   template <typename T> SellView<T> view() const;
 };
 
@@ -53,7 +63,13 @@ template <> inline SellView<double> Sell::view<double>() const {
   return {meta.as<int4>(), col.as<int>(), val.as<double>()};
 }
 template <> inline SellView<float> Sell::view<float>() const {
-  return {meta.as<int4>(), col.as<int>(), val32.as<float>(), ent32.as<uint2>()};
+  SellView<float> v{meta.as<int4>(), col.as<int>(), val32.as<float>(), ent32.as<uint2>()};
+  if (affine) {
+    v.ameta = ameta.as<int4>();
+    v.abase = abase.as<int>();
+    v.aval = aval.as<float>();
+  }
+  return v;
 }
 
 // Scratch for the grid-wide reductions of one stream of launches.
@@ -63,6 +79,7 @@ struct Scratch {
 };
 
 constexpr int kMaxRed = 2 * kMaxM + 8;
+constexpr int kAffineSlots = 8;  // slots of a slice in the column-free copy, at most
 
 int grid_blocks(int work_slices);  // blocks for a launch over this many slices
 int max_grid_blocks();
@@ -86,6 +103,7 @@ struct esd_matrix {
   std::vector<esd::SliceSet> bwd_all_sets; // all backward levels incl. level 0 (apply)
   std::vector<esd::SliceSet> bwd0_sets;    // colours without later neighbours
   std::vector<int> fwd_wmax, bwd_wmax;     // widest L (U) row of each fwd_sets (bwd_sets) launch
+  std::vector<int> fwd_awmax, bwd_awmax;   // most slots of a slice of the column-free L (U) copy, per launch
   esd::SliceSet upd_sets[2];               // forward level-0 slices, the other slices
   bool upd_ok = false;                     // both fit kMaxRanges ranges
   esd::DevBuf fwd_grid64, fwd_grid32;      // int per forward launch: its grid (FP64 / FP32 kernel)

@@ -1464,6 +1464,17 @@ static bool stream_sweeps(const esd_matrix* P) {
   return sizeof(T) == 4 && stream_enabled() && P->L.wmax <= kStreamWmax && P->U.wmax <= kStreamWmax;
 }
 
+// The staged sweeps read the column-free copies of L and U when both parts have one.
+static bool affine_sweeps(const esd_matrix* P) { return P->L.affine && P->U.affine; }
+
+// Plan of a staged launch over `with_entries` (+ `vectors_only`) of a part whose widest slice
+// has wmax entries, or awmax slots in its column-free copy (aff), with nv4 staged FP32 vectors.
+inline StreamPlan staged_plan(const SliceSet& with_entries, const SliceSet& vectors_only, bool aff, int wmax,
+                              int awmax, int nv4, int* K) {
+  return aff ? stream_plan(with_entries, vectors_only, awmax, 4, nv4, 0, K, kStreamWmax, kHdrAffine)
+             : stream_plan(with_entries, vectors_only, wmax, 8, nv4, 0, K);
+}
+
 // Plan and grid of forward launch l (the last forward launch reads the rho block totals of
 // the earlier ones, so every launch of a sweep uses exactly this grid).
 template <typename T>
@@ -1472,11 +1483,14 @@ static int fwd_grid(const esd_matrix* P, size_t l, StreamPlan* plan = nullptr, i
   if constexpr (sizeof(T) == 4) {
     if (stream_sweeps<T>(P)) {
       int K = 1;
-      const StreamPlan pl = stream_plan(set, SliceSet{}, P->fwd_wmax[l], 8, 2, 0, &K);
+      const bool aff = affine_sweeps(P);
+      const StreamPlan pl = staged_plan(set, SliceSet{}, aff, P->fwd_wmax[l], aff ? P->fwd_awmax[l] : 0, 2, &K);
       if (plan) *plan = pl;
       if (K_out) *K_out = K;
       int G = 0;
-      ESD_DISPATCH_K(K, { G = stream_blocks(k_fwd_stream<T, KK>, pl); });
+      ESD_DISPATCH_K(K, {
+        G = aff ? stream_blocks(k_fwd_stream<T, KK, true>, pl) : stream_blocks(k_fwd_stream<T, KK, false>, pl);
+      });
       return G;
     }
   }
@@ -1514,8 +1528,13 @@ static void launch_precond(const IterCtx<T>& c, cudaStream_t s, KernelMarks* mar
     const int G = fwd_grid<T>(A, l, &pl, &K);
     const bool last = l + 1 == nf;
     if constexpr (sizeof(T) == 4) {
-      if (staged)
-        ESD_DISPATCH_K(K, launch_stream(k_fwd_stream<T, KK>, G, pl, s, c, pl, last ? -1 : (int)l, last ? (int)l : 0, dG));
+      if (staged) {
+        const int slot = last ? -1 : (int)l, nprev = last ? (int)l : 0;
+        ESD_DISPATCH_K(K, {
+          if (affine_sweeps(A)) launch_stream(k_fwd_stream<T, KK, true>, G, pl, s, c, pl, slot, nprev, dG);
+          else launch_stream(k_fwd_stream<T, KK, false>, G, pl, s, c, pl, slot, nprev, dG);
+        });
+      }
     }
     if (!staged) launch_pdl(kf, G, s, c, set, last ? -1 : (int)l, last ? (int)l : 0, dG);
     if (marks) marks->mark(s, ("fwd_" + std::to_string(l + 1)).c_str());
@@ -1529,10 +1548,17 @@ static void launch_precond(const IterCtx<T>& c, cudaStream_t s, KernelMarks* mar
     if constexpr (sizeof(T) == 4) {
       if (staged && SCM == 0) {
         int K = 1;
-        const StreamPlan pl = stream_plan(sw, el, l < A->bwd_wmax.size() ? A->bwd_wmax[l] : 0, 8, 3, 0, &K);
+        const bool aff = affine_sweeps(A);
+        const bool has = l < A->bwd_sets.size();
+        const StreamPlan pl = staged_plan(sw, el, aff, has ? A->bwd_wmax[l] : 0, has && aff ? A->bwd_awmax[l] : 0, 3, &K);
         ESD_DISPATCH_K(K, {
-          auto k = k_bwd_stream<T, KK>;
-          launch_stream(k, stream_blocks(k, pl), pl, s, c, pl);
+          if (aff) {
+            auto k = k_bwd_stream<T, KK, true>;
+            launch_stream(k, stream_blocks(k, pl), pl, s, c, pl);
+          } else {
+            auto k = k_bwd_stream<T, KK, false>;
+            launch_stream(k, stream_blocks(k, pl), pl, s, c, pl);
+          }
         });
         done = true;
       }
@@ -1588,10 +1614,16 @@ void launch_iteration(const IterCtx<T>& c, cudaStream_t s, KernelMarks* marks) {
     // FP32 plain product: the matrix stream staged by bulk copies
     if constexpr (sizeof(T) == 4) {
       int K = 1;
-      const StreamPlan pl = stream_plan(all, SliceSet{}, c.A->A.wmax, 8, 2, 0, &K);
+      const bool aff = c.A->A.affine;
+      const StreamPlan pl = staged_plan(all, SliceSet{}, aff, c.A->A.wmax, c.A->A.awmax, 2, &K);
       ESD_DISPATCH_K(K, {
-        auto k = k_spmv_pq_stream<T, KK>;
-        launch_stream(k, stream_blocks(k, pl), pl, s, c, pl);
+        if (aff) {
+          auto k = k_spmv_pq_stream<T, KK, true>;
+          launch_stream(k, stream_blocks(k, pl), pl, s, c, pl);
+        } else {
+          auto k = k_spmv_pq_stream<T, KK, false>;
+          launch_stream(k, stream_blocks(k, pl), pl, s, c, pl);
+        }
       });
     }
   } else {

@@ -1,6 +1,7 @@
 // Matrix set-up: CSR validation, colour levels, the sliced-ELL copies of A, L and U, and
 // the IC(0) factorisation computed colour level by colour level on the device.
 #include <algorithm>
+#include <climits>
 #include <cstring>
 #include <numeric>
 
@@ -222,6 +223,54 @@ __global__ void k_fill(int nslices, int n, const int4* mA, const int4* mL, const
   }
 }
 
+// Column-free copy, pattern: one warp per slice. The slot bases of a slice are the distinct
+// values of (column - lane) over its present entries (column < n), in increasing order; every
+// lane's columns increase, so its entries fall into increasing slots. slots[s] = their number,
+// or -1 when a slice needs more than kAffineSlots.
+__global__ void k_affine_slots(int nslices, int n, const int4* meta, const int* col, int* slots, int* abase) {
+  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (s >= nslices) return;
+  const int4 md = meta[s];
+  int e = 0, cnt = 0;
+  auto base_at = [&](int k) {
+    const int c = k < md.y ? col[md.x + k * kSlice + lane] : n;
+    return c < n ? c - lane : INT_MAX;
+  };
+  int cand = base_at(0);
+  while (true) {
+    const int m = __reduce_min_sync(0xffffffffu, cand);
+    if (m == INT_MAX) break;
+    if (cnt == kAffineSlots) {
+      cnt = -1;
+      break;
+    }
+    if (lane == 0) abase[(size_t)s * kAffineSlots + cnt] = m;
+    if (cand == m) cand = base_at(++e);
+    ++cnt;
+  }
+  if (lane == 0) {
+    slots[s] = cnt;
+    for (int k = cnt < 0 ? 0 : cnt; k < kAffineSlots; ++k) abase[(size_t)s * kAffineSlots + k] = 0;
+  }
+}
+
+// Column-free copy, values: every present entry to its slot (the slots of absent entries keep
+// the zero they were allocated with).
+__global__ void k_affine_values(int nslices, int n, const int4* meta, const int* col, const double* val,
+                                const int4* ameta, const int* abase, float* aval) {
+  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (s >= nslices) return;
+  const int4 md = meta[s], am = ameta[s];
+  const int* b = abase + (size_t)s * kAffineSlots;
+  int k = 0;
+  for (int e = 0; e < md.y; ++e) {
+    const int c = col[md.x + e * kSlice + lane];
+    if (c >= n) continue;
+    while (k < am.y && b[k] + lane != c) ++k;
+    if (k < am.y) aval[am.x + k * kSlice + lane] = (float)val[md.x + e * kSlice + lane];
+  }
+}
+
 // One colour level of IC(0): every row i of the level computes, in column order,
 //   l_ik = (a_ik - sum_{j<k} l_ij l_kj) / l_kk       (sum over the common pattern)
 //   l_ii = sqrt(a_ii (1 + shift) - sum_k l_ik^2),
@@ -349,6 +398,47 @@ static void interleave(Sell& M, cudaStream_t s) {
   ESD_CUDA(cudaGetLastError());
 }
 
+// Column-free FP32 copy of one part (pattern only; values come with the other FP32 copies):
+// built when every slice fits kAffineSlots slots.
+static void build_affine(Sell& part, int NS, int n, const std::vector<int2>& rows, cudaStream_t s) {
+  part.affine = false;
+  part.awmax = 0;
+  part.aslots.clear();
+  if (NS == 0) return;
+  DevBuf dslots(sizeof(int) * NS), dbase(sizeof(int) * (size_t)NS * kAffineSlots);
+  k_affine_slots<<<(NS * 32 + 255) / 256, 256, 0, s>>>(NS, n, part.meta.as<int4>(), part.col.as<int>(),
+                                                      dslots.as<int>(), dbase.as<int>());
+  ESD_CUDA(cudaGetLastError());
+  std::vector<int> slots(NS);
+  ESD_CUDA(cudaMemcpyAsync(slots.data(), dslots.get(), dslots.bytes(), cudaMemcpyDeviceToHost, s));
+  ESD_CUDA(cudaStreamSynchronize(s));
+  if (*std::min_element(slots.begin(), slots.end()) < 0) return;
+  std::vector<int4> am(NS);
+  long long off = 0;
+  for (int i = 0; i < NS; ++i) {
+    am[i] = make_int4((int)off, slots[i], rows[i].x, rows[i].y);
+    off += (long long)slots[i] * kSlice;
+    if (off >= (long long)INT32_MAX) return;
+  }
+  part.ameta.alloc(sizeof(int4) * NS);
+  ESD_CUDA(cudaMemcpyAsync(part.ameta.get(), am.data(), part.ameta.bytes(), cudaMemcpyHostToDevice, s));
+  part.aval.alloc(sizeof(float) * std::max(off, 1LL));
+  ESD_CUDA(cudaMemsetAsync(part.aval.get(), 0, part.aval.bytes(), s));
+  part.abase = std::move(dbase);
+  ESD_CUDA(cudaStreamSynchronize(s));  // am is a stack vector
+  part.awmax = *std::max_element(slots.begin(), slots.end());
+  part.aslots = std::move(slots);
+  part.affine = true;
+}
+
+static void affine_values(const Sell& part, int NS, int n, cudaStream_t s) {
+  if (!part.affine || NS == 0) return;
+  k_affine_values<<<(NS * 32 + 255) / 256, 256, 0, s>>>(NS, n, part.meta.as<int4>(), part.col.as<int>(),
+                                                       part.val.as<double>(), part.ameta.as<int4>(),
+                                                       part.abase.as<int>(), part.aval.as<float>());
+  ESD_CUDA(cudaGetLastError());
+}
+
 static void to_float(const DevBuf& src, DevBuf& dst, long long cnt, cudaStream_t s) {
   if (dst.bytes() < (size_t)cnt * sizeof(float)) dst.alloc((size_t)cnt * sizeof(float));
   if (cnt == 0) return;
@@ -416,6 +506,7 @@ void esd_matrix::ensure_fp32() {
   if (a32_version != values_version || !A.val32.get()) {
     to_float(A.val, A.val32, A.entries, stream);
     interleave(A, stream);
+    affine_values(A, nslices, n, stream);
     if (!rowsum32.get()) {
       rowsum32.alloc(sizeof(float) * vec_stride());
       rowsum64.alloc(sizeof(double) * vec_stride());
@@ -433,6 +524,8 @@ void esd_matrix::ensure_fp32() {
     to_float(U.val, U.val32, U.entries, stream);
     interleave(L, stream);
     interleave(U, stream);
+    affine_values(L, nslices, n, stream);
+    affine_values(U, nslices, n, stream);
     to_float(inv_d, inv_d32, (long long)vec_stride(), stream);
   }
   fp32_version = factor_version;
@@ -678,6 +771,7 @@ int esd_create_matrix(int32_t n, int64_t nnz, const int32_t* rowptr, const int32
         M->A.col.as<int>(), M->A.val.as<double>(), M->L.col.as<int>(), M->L.val.as<double>(),
         M->U.col.as<int>(), M->umap.as<int>());
     ESD_CUDA(cudaGetLastError());
+    for (Sell* part : {&M->A, &M->L, &M->U}) build_affine(*part, NS, n, rows, s);
 
     // slice flags and launch sets
     build_level_sets(M.get(), hadj);
@@ -692,6 +786,12 @@ int esd_create_matrix(int32_t n, int64_t nnz, const int32_t* rowptr, const int32
     for (const SliceSet& set : M->fwd_sets) M->fwd_wmax.push_back(set_wmax(set, hwL));
     M->bwd_wmax.clear();
     for (const SliceSet& set : M->bwd_sets) M->bwd_wmax.push_back(set_wmax(set, hwU));
+    M->fwd_awmax.clear();
+    M->bwd_awmax.clear();
+    if (M->L.affine && M->U.affine) {
+      for (const SliceSet& set : M->fwd_sets) M->fwd_awmax.push_back(set_wmax(set, M->L.aslots));
+      for (const SliceSet& set : M->bwd_sets) M->bwd_awmax.push_back(set_wmax(set, M->U.aslots));
+    }
     // grid of every forward launch (one table per kernel precision): the last forward launch
     // of an iteration adds the block totals the earlier ones left
     for (int prec = 0; prec < 2; ++prec) {

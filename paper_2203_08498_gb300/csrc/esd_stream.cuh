@@ -74,18 +74,25 @@ struct VecSet {
 };
 
 // Matrix entries of a staged kernel: one or two arrays per entry (FP32: (value, column)
-// pairs; FP64: columns, then values), eb[a] bytes per entry; none for vector-only kernels.
+// pairs; the column-free copy: values, with kAffineSlots slot bases per slice in sbase),
+// eb[a] bytes per entry; none for vector-only kernels.
 struct EntSet {
   const void* ptr[2];
   int eb[2];
   int n;
+  const int* sbase = nullptr;
 };
 
-// Bytes of one stage: metas, row vectors (vbytes: the sum of their element bytes), then the
-// entries of cs slices of at most wmax entries per row (ebytes per entry over all arrays).
-__host__ __device__ constexpr int stream_stage_bytes(int cs, int wmax, int ebytes, int nv4, int nv8) {
-  return cs * 16 + nv4 * stream_vcap(cs, 4) * 4 + nv8 * stream_vcap(cs, 8) * 8 + cs * wmax * kSlice * ebytes;
+// Bytes of one stage: the slice headers (hdr bytes each: the meta, and the slot bases of the
+// column-free copy), row vectors (nv4 of 4-byte and nv8 of 8-byte elements), then the entries
+// of cs slices of at most wmax entries per row (ebytes per entry over all arrays).
+__host__ __device__ constexpr int stream_stage_bytes(int cs, int wmax, int ebytes, int nv4, int nv8, int hdr = 16) {
+  return cs * hdr + nv4 * stream_vcap(cs, 4) * 4 + nv8 * stream_vcap(cs, 8) * 8 + cs * wmax * kSlice * ebytes;
 }
+
+// Slice header bytes of a stage: the meta, plus the slot bases of the column-free copy.
+constexpr int kHdrPlain = 16;
+constexpr int kHdrAffine = 16 + kAffineSlots * 4;
 
 // The chunks of one staged launch: those of set 0 (matrix entries and row vectors staged),
 // then those of set 1 (row vectors only). cs = slices per chunk (kStreamWarps x K), ns =
@@ -93,7 +100,7 @@ __host__ __device__ constexpr int stream_stage_bytes(int cs, int wmax, int ebyte
 struct StreamPlan {
   SliceSet set[2];
   ChunkMap cm[2];
-  int cs, ns, stage, ecap;
+  int cs, ns, stage, ecap, hdr;
   __host__ __device__ int total() const { return cm[0].total() + cm[1].total(); }
 };
 
@@ -102,17 +109,18 @@ struct StreamPlan {
 // consumer warp takes per chunk (the largest of 4, 2, 1 with K x wmax <= kmax_w and a stage
 // of at most kStreamStageCap bytes), and the stages that fit kStreamRingCap (3, else 2).
 inline StreamPlan stream_plan(const SliceSet& with_entries, const SliceSet& vectors_only, int wmax, int ebytes,
-                              int nv4, int nv8, int* K_out, int kmax_w = kStreamWmax) {
+                              int nv4, int nv8, int* K_out, int kmax_w = kStreamWmax, int hdr = kHdrPlain) {
   int K = 1;
   for (int k = kStreamMaxK; k > 1; k /= 2)
     if (k * std::max(wmax, 1) <= kmax_w &&
-        stream_stage_bytes(kStreamWarps * k, wmax, ebytes, nv4, nv8) <= kStreamStageCap) {
+        stream_stage_bytes(kStreamWarps * k, wmax, ebytes, nv4, nv8, hdr) <= kStreamStageCap) {
       K = k;
       break;
     }
   StreamPlan pl{};
   pl.cs = kStreamWarps * K;
-  pl.stage = stream_stage_bytes(pl.cs, wmax, ebytes, nv4, nv8);
+  pl.hdr = hdr;
+  pl.stage = stream_stage_bytes(pl.cs, wmax, ebytes, nv4, nv8, hdr);
   pl.ns = 3 * pl.stage <= kStreamRingCap ? 3 : 2;
   pl.ecap = pl.cs * wmax * kSlice;
   pl.set[0] = with_entries;
@@ -250,7 +258,8 @@ __device__ __forceinline__ bool stream_produce(const StreamPlan& pl, const int4*
     const unsigned nent = cp.part ? 0u : (unsigned)(m1.x + m1.y * kSlice - m0.x);
     const unsigned vmask = cp.part ? vs.part1 : ~0u;
     const int z1 = m1.z + m1.w;
-    unsigned tx = mbytes;
+    const unsigned bbytes = es.sbase ? (unsigned)(cp.s1 - cp.s0) * (kAffineSlots * 4u) : 0u;
+    unsigned tx = mbytes + bbytes;
 #pragma unroll
     for (int v = 0; v < NV; ++v)
       if ((vmask >> v) & 1u) {
@@ -261,7 +270,8 @@ __device__ __forceinline__ bool stream_produce(const StreamPlan& pl, const int4*
     unsigned char* st = esd_dyn_smem + (size_t)k * pl.stage;
     mbar_arrive_expect_tx(&full[k], tx);
     bulk_load(st, meta + cp.s0, mbytes, &full[k], pol_first);
-    unsigned char* dst = st + pl.cs * 16;
+    if (bbytes) bulk_load(st + pl.cs * 16, es.sbase + (size_t)cp.s0 * kAffineSlots, bbytes, &full[k], pol_first);
+    unsigned char* dst = st + pl.cs * pl.hdr;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const int vb = vs.vb[v], q = 16 / vb;
@@ -295,6 +305,7 @@ struct StageView {
   const unsigned char* base;
   const unsigned char* vptr[NV];
   const unsigned char* eptr[2];
+  const int* sbase;  // slot bases of the column-free copy (kAffineSlots per slice)
   int a0[NV];
   int x0;
   __device__ __forceinline__ const int4* meta() const { return reinterpret_cast<const int4*>(base); }
@@ -333,7 +344,8 @@ __device__ __forceinline__ bool stream_consume(const StreamPlan& pl, const EntSe
     StageView<NV> sv;
     sv.base = esd_dyn_smem + (size_t)k * pl.stage;
     const int4 m0 = sv.meta()[0];
-    const unsigned char* q = sv.base + pl.cs * 16;
+    sv.sbase = reinterpret_cast<const int*>(sv.base + pl.cs * 16);
+    const unsigned char* q = sv.base + pl.cs * pl.hdr;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       sv.vptr[v] = q;
@@ -361,34 +373,58 @@ __device__ __forceinline__ void stream_slices(const StageView<NV>& sv, const Chu
   }
 }
 
-// Row products of K slices of one lane from staged FP32 (value, column) entries: acc[t] +=
-// sum_e val_e * (v[col_e] - vi[t]) (vi = 0 in the plain form), the entries of a row in stored
-// order, as row_fma and row_fma_diff take them. Every gather of the K rows is issued before
-// the first FMA. A row wider than kStreamWmax / K (which the launch plan excludes) is
-// reported through `bad`.
-template <int K, bool DIFF, int NV>
-__device__ __forceinline__ void staged_rows(const StageView<NV>& sv, const int4 (&md)[K], int lane,
+// Row products of K slices of one lane from staged FP32 entries: acc[t] += sum_e val_e *
+// (v[col_e] - vi[t]) (vi = 0 in the plain form), the entries of a row in stored order, as
+// row_fma and row_fma_diff take them. AFF = false: (value, column) pairs; AFF = true: the
+// column-free copy, column = slot base + lane (clamped to [0, cmax]: a slot where the row has
+// no entry holds 0 and may point anywhere). The K slices are the warp's, at local indices
+// warp + t kStreamWarps. Every gather of the K rows is issued before the first FMA. A row
+// wider than kStreamWmax / K (which the launch plan excludes) is reported through `bad`.
+template <int K, bool DIFF, bool AFF, int NV>
+__device__ __forceinline__ void staged_rows(const StageView<NV>& sv, const int4 (&md)[K], int warp, int lane, int cmax,
                                             const float* __restrict__ v, const float (&vi)[K], float (&acc)[K],
                                             bool& bad) {
   constexpr int W = kStreamWmax / K;
-  uint2 ev[K][W];
-  float vj[K][W];
-  const uint2* ent = sv.template ent<uint2>(0);
+  float val[K][W], vj[K][W];
 #pragma unroll
   for (int t = 0; t < K; ++t) {
     bad |= md[t].y > W;
-    const uint2* ep = ent + (md[t].x - sv.x0) + lane;
+    const int off = (md[t].x - sv.x0) + lane;
+    const int* sb = sv.sbase + (warp + t * kStreamWarps) * kAffineSlots;
 #pragma unroll
     for (int e = 0; e < W; ++e) {
-      ev[t][e] = e < md[t].y ? ep[e * kSlice] : make_uint2(0u, 0u);
-      vj[t][e] = e < md[t].y ? v[ev[t][e].y] : 0.f;
+      int col = 0;
+      val[t][e] = 0.f;
+      if (e < md[t].y) {
+        if constexpr (AFF) {
+          val[t][e] = sv.template ent<float>(0)[off + e * kSlice];
+          col = min(max(sb[e] + lane, 0), cmax);
+        } else {
+          const uint2 pr = sv.template ent<uint2>(0)[off + e * kSlice];
+          val[t][e] = __uint_as_float(pr.x);
+          col = (int)pr.y;
+        }
+      }
+      vj[t][e] = e < md[t].y ? v[col] : 0.f;
     }
   }
 #pragma unroll
   for (int t = 0; t < K; ++t)
 #pragma unroll
     for (int e = 0; e < W; ++e)
-      if (e < md[t].y) acc[t] = fmaf(__uint_as_float(ev[t][e].x), DIFF ? vj[t][e] - vi[t] : vj[t][e], acc[t]);
+      if (e < md[t].y) acc[t] = fmaf(val[t][e], DIFF ? vj[t][e] - vi[t] : vj[t][e], acc[t]);
+}
+
+// The staged entries of a sliced-ELL part: the column-free copy (AFF) or the (value, column)
+// pairs, and the metas that go with them.
+template <bool AFF>
+__device__ __forceinline__ EntSet stream_entries(const SellView<float>& M) {
+  if constexpr (AFF) return EntSet{{M.aval, nullptr}, {4, 0}, 1, M.abase};
+  else return EntSet{{M.ent, nullptr}, {8, 0}, 1, nullptr};
+}
+template <bool AFF>
+__device__ __forceinline__ const int4* stream_metas(const SellView<float>& M) {
+  return AFF ? M.ameta : M.meta;
 }
 
 // Compensated (Kahan) accumulation of one thread's partial sum: sum += v, with the rounding
@@ -420,7 +456,7 @@ __device__ __forceinline__ bool stream_enter(State* st, unsigned long long* full
 // q = A p (difference form, FP32 inner solves) and (p, q); the last block sets alpha.
 // Entries are (value bits, column) pairs; the products are formed in the order of
 // row_fma_diff, so q is bit-identical to k_spmv_pq<float, 0>'s. Staged vectors: s = A 1, p.
-template <typename T, int K>
+template <typename T, int K, bool AFF>
 __global__ void __launch_bounds__(kStreamThreads, 2) k_spmv_pq_stream(IterCtx<T> c, StreamPlan pl) {
   static_assert(sizeof(T) == 4, "the staged product reads the FP32 (value, column) entries");
   __shared__ unsigned long long full[kStreamMaxStages], empty[kStreamMaxStages];
@@ -429,11 +465,12 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_spmv_pq_stream(IterCtx<T>
   State* st = c.st;
   if (!stream_enter(st, full, empty, &s_stop, true, c.cond)) return;
   const int warp = threadIdx.x >> 5, lane = lane_id();
-  const EntSet es{{c.Av.ent, nullptr}, {8, 0}, 1};
+  const EntSet es = stream_entries<AFF>(c.Av);
   const VecSet<2> vs{{c.rowsum, c.p}, {4, 4}, 2u, 0u};
+  const int cmax = (int)c.ld - 1;
   float acc[1] = {0.f}, cmp[1] = {0.f};
   if (warp == kStreamWarps) {
-    if (lane == 0 && !stream_produce(pl, c.Av.meta, es, vs, full, empty)) stream_fail(st, c.cond);
+    if (lane == 0 && !stream_produce(pl, stream_metas<AFF>(c.Av), es, vs, full, empty)) stream_fail(st, c.cond);
   } else {
     const float* __restrict__ p = c.p;
     bool bad = false;
@@ -448,7 +485,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_spmv_pq_stream(IterCtx<T>
         pv[t] = valid ? sv.template vec<float>(1, i) : 0.f;
         q[t] = fmaf(valid ? sv.template vec<float>(0, i) : 0.f, pv[t], 0.f);
       }
-      staged_rows<K, true>(sv, md, lane, p, pv, q, bad);
+      staged_rows<K, true, AFF>(sv, md, warp, lane, cmax, p, pv, q, bad);
 #pragma unroll
       for (int t = 0; t < K; ++t)
         if (lane < md[t].w) {
@@ -535,7 +572,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
 
 // One forward colour level (as k_fwd<float>): y_i = (r_i - sum_k l_ik y_k) / l_ii and
 // sum y_i^2; the same slot / last-launch protocol for rho. Staged vectors: r, 1/l_ii.
-template <typename T, int K>
+template <typename T, int K, bool AFF>
 __global__ void __launch_bounds__(kStreamThreads, 2)
     k_fwd_stream(IterCtx<T> c, StreamPlan pl, int slot, int nprev, const int* __restrict__ prevG) {
   static_assert(sizeof(T) == 4, "the staged sweep reads the FP32 (value, column) entries");
@@ -546,11 +583,12 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
   State* st = c.st;
   if (!stream_enter(st, full, empty, &s_stop, false, c.cond)) return;
   const int warp = threadIdx.x >> 5, lane = lane_id();
-  const EntSet es{{c.Lv.ent, nullptr}, {8, 0}, 1};
+  const EntSet es = stream_entries<AFF>(c.Lv);
   const VecSet<2> vs{{c.r, c.inv_d}, {4, 4}, 0u, 0u};
+  const int cmax = (int)c.ld - 1;
   float acc[1] = {0.f}, cmp[1] = {0.f};
   if (warp == kStreamWarps) {
-    if (lane == 0 && !stream_produce(pl, c.Lv.meta, es, vs, full, empty)) stream_fail(st, c.cond);
+    if (lane == 0 && !stream_produce(pl, stream_metas<AFF>(c.Lv), es, vs, full, empty)) stream_fail(st, c.cond);
   } else {
     float* Y = c.Y;
     const unsigned bwd0 = pl.set[0].bwd0;
@@ -567,7 +605,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
         d[t] = valid ? sv.template vec<float>(1, i) : 0.f;
         y[t] = valid ? sv.template vec<float>(0, i) : 0.f;
       }
-      staged_rows<K, false>(sv, md, lane, Y, zero, y, bad);
+      staged_rows<K, false, AFF>(sv, md, warp, lane, cmax, Y, zero, y, bad);
       const bool to_z = (bwd0 >> cp.range) & 1u;
 #pragma unroll
       for (int t = 0; t < K; ++t)
@@ -603,7 +641,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
 // z_i = (y_i - sum_j l_ji z_j) / l_ii, p_i = z_i + beta p_i. Part-1 chunks hold the rows
 // whose z_i the forward sweep stored: direction update only. Staged vectors: y, 1/l_ii, p
 // (part 1: y, p).
-template <typename T, int K>
+template <typename T, int K, bool AFF>
 __global__ void __launch_bounds__(kStreamThreads, 2) k_bwd_stream(IterCtx<T> c, StreamPlan pl) {
   static_assert(sizeof(T) == 4, "the staged sweep reads the FP32 (value, column) entries");
   __shared__ unsigned long long full[kStreamMaxStages], empty[kStreamMaxStages];
@@ -613,10 +651,11 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_bwd_stream(IterCtx<T> c, 
   const int warp = threadIdx.x >> 5, lane = lane_id();
   const float beta = (float)st->beta;
   const bool first = st->iter == 0 || st->fresh_dir;
-  const EntSet es{{c.Uv.ent, nullptr}, {8, 0}, 1};
+  const EntSet es = stream_entries<AFF>(c.Uv);
   const VecSet<3> vs{{c.Y, c.inv_d, c.p}, {4, 4, 4}, 0u, 5u};
+  const int cmax = (int)c.ld - 1;
   if (warp == kStreamWarps) {
-    if (lane == 0 && !stream_produce(pl, c.Uv.meta, es, vs, full, empty)) stream_fail(st, c.cond);
+    if (lane == 0 && !stream_produce(pl, stream_metas<AFF>(c.Uv), es, vs, full, empty)) stream_fail(st, c.cond);
   } else {
     float* Y = c.Y;
     bool bad = false;
@@ -635,7 +674,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_bwd_stream(IterCtx<T> c, 
         d[t] = (valid && sweep) ? sv.template vec<float>(1, i) : 1.f;
         pold[t] = (valid && !first) ? sv.template vec<float>(2, i) : 0.f;
       }
-      if (sweep) staged_rows<K, false>(sv, md, lane, Y, zero, z, bad);
+      if (sweep) staged_rows<K, false, AFF>(sv, md, warp, lane, cmax, Y, zero, z, bad);
 #pragma unroll
       for (int t = 0; t < K; ++t)
         if (lane < md[t].w) {
