@@ -377,7 +377,7 @@ def gpu_arm(args):
     xs = x.clone()
     prof = S.profile_iterations(b, xs, reps=20)
     peaks = read_peaks()
-    result["roofline"], result["kernel_times_ms"] = roofline(prof, p, args, mode, esd, peaks)
+    result["roofline"], result["kernel_times_ms"] = roofline(prof, p, args, mode, esd, peaks, A.layout())
 
     modes = None
     if args.config == "c2" and not fp32:
@@ -617,7 +617,7 @@ def system_arm(args, esd, torch, dev, ws, rank):
     S.set_mode(mode)
     prof = S.profile_iterations(b, x.clone(), reps=10)
     peaks = read_peaks()
-    result["roofline"], result["kernel_times_ms"] = roofline(prof, p, args, mode, esd, peaks)
+    result["roofline"], result["kernel_times_ms"] = roofline(prof, p, args, mode, esd, peaks, A.layout())
 
     # the next two systems: this mode (advancing the sequence), then from the same b_t and
     # x_{t-1} (and g_t, lambda_{t-1}) the other modes of this precision form with the same W,
@@ -702,7 +702,10 @@ def system_arm(args, esd, torch, dev, ws, rank):
     # HBM GB/s per iteration on the paper's byte model: this form against plain FP64
     s_in = 4 if fp32 else 8
     m_eff = state["kept"] if mode != esd.PLAIN else 0
-    model_this = 2 * (s_in + 4) * p.nnz + (4 + 12 * s_in) * n + (2 * s_in * m_eff * n + 2 * s_in * n if m_eff else 0)
+    lay = A.layout() if mode == esd.PLAIN else None
+    mat = matrix_bytes(p, s_in, lay, 0) + (matrix_bytes(p, s_in, lay, 1) + matrix_bytes(p, s_in, lay, 2)
+                                           if lay is not None and lay["column_free"][1] else (s_in + 4) * p.nnz)
+    model_this = mat + (4 + 12 * s_in) * n + (2 * s_in * m_eff * n + 2 * s_in * n if m_eff else 0)
     model_f64 = 24 * p.nnz + 100 * n
     it_this = np.mean([c["this"]["iters"] + c["this"]["adjoint_iters"] for c in cmp_rows])
     it_f64 = np.mean([c["fp64_plain_forward"]["iters"] + c["fp64_plain_adjoint"]["iters"] for c in cmp_rows])
@@ -825,7 +828,18 @@ FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (CUDA cores and tensor), nominal
 FP32_NOMINAL_TFLOPS = 80.5  # 152 SMs x 128 FP32 FMA/clk x 2 x 2.07 GHz
 
 
-def kernel_model(name, p, args, mode, esd, lv):
+def matrix_bytes(p, s, layout, part):
+    """Bytes of one pass over a matrix part (0: A, 1: L, 2: U; L + U together for one sweep
+    pair) in the format the kernels of value size s read: (value, column) entries, s + 4
+    bytes each; or, for the FP32 kernels of a part with the column-free copy, its 4-byte slot
+    values and 32 bytes of slot bases per 32-row slice."""
+    entries = p.nnz if part == 0 else (p.nnz - p.n) // 2
+    if s == 4 and layout is not None and layout["column_free"][part]:
+        return 4 * layout["slot_entries"][part] + 32 * layout["slices"]
+    return (s + 4) * entries
+
+
+def kernel_model(name, p, args, mode, esd, lv, layout=None):
     """Algorithmic bytes and FMAs of one launch, each array element counted once; value
     size s = 8 (FP64) or 4 (FP32 inner kernels, whose SpMV also reads s = A 1)."""
     n, nnz = p.n, p.nnz
@@ -838,7 +852,10 @@ def kernel_model(name, p, args, mode, esd, lv):
         # FP64 deflation with up to 32 (padded) columns forms (AW)^T p in double-float on the
         # FP32 pipe: only the matrix product and (p, q) are FP64 FMAs
         df = s == 8 and 0 < mb and pad_m(mb) <= 32
-        return (s + 4) * nnz + (2 * s + 4) * n + extra + s * mb * n, nnz + n + (0 if df else mb * n)
+        # the deflated FP32 product keeps the (value, column) pairs
+        lay = layout if mb == 0 else None
+        return (matrix_bytes(p, s, lay, 0) + (2 * s + 4) * n + extra + s * mb * n,
+                nnz + n + (0 if df else mb * n))
     if name == "update":
         dm = m if mode == esd.DEFLATION else 0
         sm = m if mode == esd.SUBSPACE_CORRECTION else 0
@@ -856,12 +873,12 @@ def pad_m(m):
     return 0 if m <= 0 else next(c for c in (8, 16, 24, 32, 64) if m <= c)
 
 
-def roofline(prof, p, args, mode, esd, peaks):
+def roofline(prof, p, args, mode, esd, peaks, layout=None):
     lv = level_stats(p)
     times = {nm: t for nm, t in prof}
     cand = [(t, nm) for nm, t in prof if nm in ("spmv_pq", "update")]
     t_ms, name = max(cand)
-    by, fmas = kernel_model(name, p, args, mode, esd, lv)
+    by, fmas = kernel_model(name, p, args, mode, esd, lv, layout)
     sec = t_ms / 1e3
     gbs = by / sec / 1e9
     tflops = 2 * fmas / sec / 1e12
@@ -888,7 +905,7 @@ def roofline(prof, p, args, mode, esd, peaks):
 # the configuration's full size: (config, precision, kernel) -> file under profiles/
 TRAFFIC = {
     ("c2", "fp64", "spmv_pq"): "spmv_pq_128cube_traffic.txt",
-    ("c5", "fp32", "spmv_pq"): "spmv_pq_stream_fp32_256cube_traffic.txt",
+    ("c5", "fp32", "spmv_pq"): "spmv_pq_stream_colfree_fp32_256cube_traffic.txt",
 }
 
 

@@ -112,6 +112,16 @@ int esd_matrix_diag_scale(const esd_matrix* A, double* d);
 int esd_matrix_info(const esd_matrix* A, int32_t* n, int64_t* nnz, int32_t* ncolours,
                     int32_t* fwd_levels, int32_t* bwd_levels);
 
+/* Storage the FP32 kernels of the refinement form read (a layout of this library, not in the
+ * paper). column_free (host, 3 int32, may be NULL): 1 where A, L, U (in that order) have the
+ * column-free copy, built at creation when every 32-row slice has at most 8 distinct
+ * (column - lane) values: per slice 8 slot bases (32 bytes) and one 4-byte value per slot
+ * and row, 0 where the row lacks that neighbour; 0 where the part keeps its (value, column)
+ * pairs of 8 bytes. slot_entries (host, 3 int64, may be NULL): the values each copy holds
+ * (slots x 32 summed over the slices; 0 without a copy). slices (host, may be NULL): the
+ * number of 32-row slices. */
+int esd_matrix_layout(const esd_matrix* A, int32_t* column_free, int64_t* slot_entries, int32_t* slices);
+
 /*
  * IC(0) factor M = L L^T on the pattern of tril(A), computed colour by colour in the
  * given order (the paper's incomplete Cholesky preconditioner, Sections 4.4 and 5.3; the

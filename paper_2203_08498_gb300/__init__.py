@@ -36,7 +36,8 @@ from . import _build
 __all__ = [
     "lib", "EsdError", "Matrix", "Solver", "PLAIN", "DEFLATION", "SUBSPACE_CORRECTION",
     "PRECOND_NONE", "PRECOND_IC0", "FP64", "FP32_REFINE", "SAMPLING_A", "SAMPLING_B", "EsdParams", "HEADER_SYMBOLS",
-    "esd_create_matrix", "esd_matrix_destroy", "esd_matrix_info", "esd_factor_ic0", "esd_matrix_spmv",
+    "esd_create_matrix", "esd_matrix_destroy", "esd_matrix_info", "esd_matrix_layout", "esd_factor_ic0",
+    "esd_matrix_spmv",
     "esd_matrix_apply_ic", "esd_pattern_grad", "esd_params_default", "esd_solver_create",
     "esd_solver_destroy", "esd_set_mode", "esd_solve", "esd_true_relres", "esd_last_solve_info",
     "esd_sample_and_build_W",
@@ -106,6 +107,7 @@ def lib(build_if_missing: bool = True):
             "esd_create_matrix": (i32, [i32, i64, vp, vp, vp, vp, i32, u32, vp, P(vp)]),
             "esd_matrix_destroy": (i32, [vp]),
             "esd_matrix_info": (i32, [vp, P(i32), P(i64), P(i32), P(i32), P(i32)]),
+            "esd_matrix_layout": (i32, [vp, P(i32), P(i64), P(i32)]),
             "esd_factor_ic0": (i32, [vp, i32, P(f64)]),
             "esd_matrix_spmv": (i32, [vp, vp, vp]),
             "esd_matrix_apply_ic": (i32, [vp, vp, vp]),
@@ -222,6 +224,16 @@ def esd_matrix_info(h):
     nnz = C.c_int64()
     _check(lib().esd_matrix_info(h, C.byref(n), C.byref(nnz), C.byref(ncol), C.byref(fl), C.byref(bl)))
     return dict(n=n.value, nnz=nnz.value, ncolours=ncol.value, fwd_levels=fl.value, bwd_levels=bl.value)
+
+
+def esd_matrix_layout(h):
+    """Which parts (A, L, U) have the column-free FP32 copy, the values each holds, and the
+    number of 32-row slices."""
+    cf = (C.c_int32 * 3)()
+    ent = (C.c_int64 * 3)()
+    ns = C.c_int32()
+    _check(lib().esd_matrix_layout(h, cf, ent, C.byref(ns)))
+    return dict(column_free=[bool(v) for v in cf], slot_entries=list(ent), slices=ns.value)
 
 
 def esd_factor_ic0(h, max_tries=30):
@@ -450,6 +462,9 @@ class Matrix:
 
     def info(self):
         return esd_matrix_info(self._h)
+
+    def layout(self):
+        return esd_matrix_layout(self._h)
 
     def factor_ic0(self, max_tries=30):
         self.shift = esd_factor_ic0(self._h, max_tries)

@@ -1471,7 +1471,7 @@ static bool affine_sweeps(const esd_matrix* P) { return P->L.affine && P->U.affi
 // has wmax entries, or awmax slots in its column-free copy (aff), with nv4 staged FP32 vectors.
 inline StreamPlan staged_plan(const SliceSet& with_entries, const SliceSet& vectors_only, bool aff, int wmax,
                               int awmax, int nv4, int* K) {
-  return aff ? stream_plan(with_entries, vectors_only, awmax, 4, nv4, 0, K, kStreamWmax, kHdrAffine)
+  return aff ? stream_plan(with_entries, vectors_only, awmax, 4, nv4, 0, K, true, kHdrAffine)
              : stream_plan(with_entries, vectors_only, wmax, 8, nv4, 0, K);
 }
 
@@ -1489,7 +1489,7 @@ static int fwd_grid(const esd_matrix* P, size_t l, StreamPlan* plan = nullptr, i
       if (K_out) *K_out = K;
       int G = 0;
       ESD_DISPATCH_K(K, {
-        G = aff ? stream_blocks(k_fwd_stream<T, KK, true>, pl) : stream_blocks(k_fwd_stream<T, KK, false>, pl);
+        G = aff ? stream_blocks(k_fwd_stream<T, KK, WW, true>, pl) : stream_blocks(k_fwd_stream<T, KK, WW, false>, pl);
       });
       return G;
     }
@@ -1531,8 +1531,8 @@ static void launch_precond(const IterCtx<T>& c, cudaStream_t s, KernelMarks* mar
       if (staged) {
         const int slot = last ? -1 : (int)l, nprev = last ? (int)l : 0;
         ESD_DISPATCH_K(K, {
-          if (affine_sweeps(A)) launch_stream(k_fwd_stream<T, KK, true>, G, pl, s, c, pl, slot, nprev, dG);
-          else launch_stream(k_fwd_stream<T, KK, false>, G, pl, s, c, pl, slot, nprev, dG);
+          if (affine_sweeps(A)) launch_stream(k_fwd_stream<T, KK, WW, true>, G, pl, s, c, pl, slot, nprev, dG);
+          else launch_stream(k_fwd_stream<T, KK, WW, false>, G, pl, s, c, pl, slot, nprev, dG);
         });
       }
     }
@@ -1553,10 +1553,10 @@ static void launch_precond(const IterCtx<T>& c, cudaStream_t s, KernelMarks* mar
         const StreamPlan pl = staged_plan(sw, el, aff, has ? A->bwd_wmax[l] : 0, has && aff ? A->bwd_awmax[l] : 0, 3, &K);
         ESD_DISPATCH_K(K, {
           if (aff) {
-            auto k = k_bwd_stream<T, KK, true>;
+            auto k = k_bwd_stream<T, KK, WW, true>;
             launch_stream(k, stream_blocks(k, pl), pl, s, c, pl);
           } else {
-            auto k = k_bwd_stream<T, KK, false>;
+            auto k = k_bwd_stream<T, KK, WW, false>;
             launch_stream(k, stream_blocks(k, pl), pl, s, c, pl);
           }
         });
@@ -1618,10 +1618,10 @@ void launch_iteration(const IterCtx<T>& c, cudaStream_t s, KernelMarks* marks) {
       const StreamPlan pl = staged_plan(all, SliceSet{}, aff, c.A->A.wmax, c.A->A.awmax, 2, &K);
       ESD_DISPATCH_K(K, {
         if (aff) {
-          auto k = k_spmv_pq_stream<T, KK, true>;
+          auto k = k_spmv_pq_stream<T, KK, WW, true>;
           launch_stream(k, stream_blocks(k, pl), pl, s, c, pl);
         } else {
-          auto k = k_spmv_pq_stream<T, KK, false>;
+          auto k = k_spmv_pq_stream<T, KK, WW, false>;
           launch_stream(k, stream_blocks(k, pl), pl, s, c, pl);
         }
       });

@@ -859,6 +859,22 @@ int esd_matrix_info(const esd_matrix* A, int32_t* n, int64_t* nnz, int32_t* ncol
   return ESD_OK;
 }
 
+int esd_matrix_layout(const esd_matrix* A, int32_t* column_free, int64_t* slot_entries, int32_t* slices) {
+  if (!A) { set_last_error("NULL matrix"); return ESD_ERR_INVALID; }
+  const Sell* parts[3] = {&A->A, &A->L, &A->U};
+  for (int k = 0; k < 3; ++k) {
+    if (column_free) column_free[k] = parts[k]->affine ? 1 : 0;
+    if (slot_entries) {
+      long long e = 0;
+      if (parts[k]->affine)
+        for (int w : parts[k]->aslots) e += (long long)w * kSlice;
+      slot_entries[k] = e;
+    }
+  }
+  if (slices) *slices = A->nslices;
+  return ESD_OK;
+}
+
 int esd_matrix_set_values(esd_matrix* A, const double* val) {
   try {
     ESD_CHECK(A && val, ESD_ERR_INVALID, "NULL argument");

@@ -33,6 +33,10 @@ constexpr int kStreamWarps = 16;                             // consumer warps p
 constexpr int kStreamThreads = (kStreamWarps + 1) * 32;      // + one producer warp
 constexpr int kStreamMaxStages = 3;                          // chunks in flight per block, at most
 constexpr int kStreamWmax = 8;                               // widest slice the staged kernels take
+// Shapes of a staged launch: K slices per consumer warp per chunk, rows of at most W entries
+// (the register arrays of a lane hold K W entries). Code 10 K + W. The column-free copy's
+// 4-byte values leave registers for K = 2 with W = 8, which the (value, column) pairs do not.
+constexpr int kShapes[4] = {42, 24, 28, 18};
 constexpr int kStreamMaxK = 4;                               // slices per consumer warp per chunk, at most
 constexpr int kStreamStageCap = 50 * 1024;                   // bytes of one stage, at most
 constexpr int kStreamRingCap = 100 * 1024;                   // bytes of the stage ring (2 blocks per SM)
@@ -105,18 +109,22 @@ struct StreamPlan {
 };
 
 // Plan of a launch whose set-0 rows hold at most wmax entries (ebytes per entry; 0 for a
-// vector-only kernel) and that stages nv4 4-byte and nv8 8-byte row vectors: K, the slices a
-// consumer warp takes per chunk (the largest of 4, 2, 1 with K x wmax <= kmax_w and a stage
-// of at most kStreamStageCap bytes), and the stages that fit kStreamRingCap (3, else 2).
+// vector-only kernel) and that stages nv4 4-byte and nv8 8-byte row vectors: its shape (the
+// first of kShapes whose W holds wmax and whose stage fits kStreamStageCap bytes; K = 2, W = 8
+// only for the column-free copy), and the stages that fit kStreamRingCap (3, else 2). aff: the
+// entries are the column-free copy's (hdr = kHdrAffine). *shape_out = the shape's code.
 inline StreamPlan stream_plan(const SliceSet& with_entries, const SliceSet& vectors_only, int wmax, int ebytes,
-                              int nv4, int nv8, int* K_out, int kmax_w = kStreamWmax, int hdr = kHdrPlain) {
-  int K = 1;
-  for (int k = kStreamMaxK; k > 1; k /= 2)
-    if (k * std::max(wmax, 1) <= kmax_w &&
-        stream_stage_bytes(kStreamWarps * k, wmax, ebytes, nv4, nv8, hdr) <= kStreamStageCap) {
+                              int nv4, int nv8, int* shape_out, bool aff = false, int hdr = kHdrPlain) {
+  int K = 1, shape = 18;
+  for (int sh : kShapes) {
+    const int k = sh / 10, w = sh % 10;
+    if (sh == 28 && !aff) continue;
+    if (std::max(wmax, 1) <= w && stream_stage_bytes(kStreamWarps * k, wmax, ebytes, nv4, nv8, hdr) <= kStreamStageCap) {
       K = k;
+      shape = sh;
       break;
     }
+  }
   StreamPlan pl{};
   pl.cs = kStreamWarps * K;
   pl.hdr = hdr;
@@ -127,7 +135,7 @@ inline StreamPlan stream_plan(const SliceSet& with_entries, const SliceSet& vect
   pl.set[1] = vectors_only;
   pl.cm[0] = chunk_map(with_entries, pl.cs);
   pl.cm[1] = chunk_map(vectors_only, pl.cs);
-  *K_out = K;
+  *shape_out = shape;
   return pl;
 }
 
@@ -379,12 +387,11 @@ __device__ __forceinline__ void stream_slices(const StageView<NV>& sv, const Chu
 // column-free copy, column = slot base + lane (clamped to [0, cmax]: a slot where the row has
 // no entry holds 0 and may point anywhere). The K slices are the warp's, at local indices
 // warp + t kStreamWarps. Every gather of the K rows is issued before the first FMA. A row
-// wider than kStreamWmax / K (which the launch plan excludes) is reported through `bad`.
-template <int K, bool DIFF, bool AFF, int NV>
+// wider than W (which the launch plan excludes) is reported through `bad`.
+template <int K, int W, bool DIFF, bool AFF, int NV>
 __device__ __forceinline__ void staged_rows(const StageView<NV>& sv, const int4 (&md)[K], int warp, int lane, int cmax,
                                             const float* __restrict__ v, const float (&vi)[K], float (&acc)[K],
                                             bool& bad) {
-  constexpr int W = kStreamWmax / K;
   float val[K][W], vj[K][W];
 #pragma unroll
   for (int t = 0; t < K; ++t) {
@@ -456,7 +463,7 @@ __device__ __forceinline__ bool stream_enter(State* st, unsigned long long* full
 // q = A p (difference form, FP32 inner solves) and (p, q); the last block sets alpha.
 // Entries are (value bits, column) pairs; the products are formed in the order of
 // row_fma_diff, so q is bit-identical to k_spmv_pq<float, 0>'s. Staged vectors: s = A 1, p.
-template <typename T, int K, bool AFF>
+template <typename T, int K, int W, bool AFF>
 __global__ void __launch_bounds__(kStreamThreads, 2) k_spmv_pq_stream(IterCtx<T> c, StreamPlan pl) {
   static_assert(sizeof(T) == 4, "the staged product reads the FP32 (value, column) entries");
   __shared__ unsigned long long full[kStreamMaxStages], empty[kStreamMaxStages];
@@ -485,7 +492,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_spmv_pq_stream(IterCtx<T>
         pv[t] = valid ? sv.template vec<float>(1, i) : 0.f;
         q[t] = fmaf(valid ? sv.template vec<float>(0, i) : 0.f, pv[t], 0.f);
       }
-      staged_rows<K, true, AFF>(sv, md, warp, lane, cmax, p, pv, q, bad);
+      staged_rows<K, W, true, AFF>(sv, md, warp, lane, cmax, p, pv, q, bad);
 #pragma unroll
       for (int t = 0; t < K; ++t)
         if (lane < md[t].w) {
@@ -572,7 +579,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
 
 // One forward colour level (as k_fwd<float>): y_i = (r_i - sum_k l_ik y_k) / l_ii and
 // sum y_i^2; the same slot / last-launch protocol for rho. Staged vectors: r, 1/l_ii.
-template <typename T, int K, bool AFF>
+template <typename T, int K, int W, bool AFF>
 __global__ void __launch_bounds__(kStreamThreads, 2)
     k_fwd_stream(IterCtx<T> c, StreamPlan pl, int slot, int nprev, const int* __restrict__ prevG) {
   static_assert(sizeof(T) == 4, "the staged sweep reads the FP32 (value, column) entries");
@@ -605,7 +612,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
         d[t] = valid ? sv.template vec<float>(1, i) : 0.f;
         y[t] = valid ? sv.template vec<float>(0, i) : 0.f;
       }
-      staged_rows<K, false, AFF>(sv, md, warp, lane, cmax, Y, zero, y, bad);
+      staged_rows<K, W, false, AFF>(sv, md, warp, lane, cmax, Y, zero, y, bad);
       const bool to_z = (bwd0 >> cp.range) & 1u;
 #pragma unroll
       for (int t = 0; t < K; ++t)
@@ -641,7 +648,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
 // z_i = (y_i - sum_j l_ji z_j) / l_ii, p_i = z_i + beta p_i. Part-1 chunks hold the rows
 // whose z_i the forward sweep stored: direction update only. Staged vectors: y, 1/l_ii, p
 // (part 1: y, p).
-template <typename T, int K, bool AFF>
+template <typename T, int K, int W, bool AFF>
 __global__ void __launch_bounds__(kStreamThreads, 2) k_bwd_stream(IterCtx<T> c, StreamPlan pl) {
   static_assert(sizeof(T) == 4, "the staged sweep reads the FP32 (value, column) entries");
   __shared__ unsigned long long full[kStreamMaxStages], empty[kStreamMaxStages];
@@ -674,7 +681,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_bwd_stream(IterCtx<T> c, 
         d[t] = (valid && sweep) ? sv.template vec<float>(1, i) : 1.f;
         pold[t] = (valid && !first) ? sv.template vec<float>(2, i) : 0.f;
       }
-      if (sweep) staged_rows<K, false, AFF>(sv, md, warp, lane, cmax, Y, zero, z, bad);
+      if (sweep) staged_rows<K, W, false, AFF>(sv, md, warp, lane, cmax, Y, zero, z, bad);
 #pragma unroll
       for (int t = 0; t < K; ++t)
         if (lane < md[t].w) {
@@ -742,13 +749,14 @@ inline void launch_stream(void (*kernel)(KArgs...), int blocks, const StreamPlan
   ESD_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
 }
 
-// Dispatch on the slices per consumer warp of a plan.
-#define ESD_DISPATCH_K(Krt, ...)                                         \
-  switch (Krt) {                                                         \
-    case 1: { constexpr int KK = 1; __VA_ARGS__; } break;                \
-    case 2: { constexpr int KK = 2; __VA_ARGS__; } break;                \
-    case 4: { constexpr int KK = 4; __VA_ARGS__; } break;                \
-    default: throw Error(ESD_ERR_INTERNAL, "unsupported staged shape");  \
+// Dispatch on the shape of a plan (KK slices per consumer warp, rows of at most WW entries).
+#define ESD_DISPATCH_K(Srt, ...)                                                   \
+  switch (Srt) {                                                                   \
+    case 42: { constexpr int KK = 4, WW = 2; __VA_ARGS__; } break;                 \
+    case 24: { constexpr int KK = 2, WW = 4; __VA_ARGS__; } break;                 \
+    case 28: { constexpr int KK = 2, WW = 8; __VA_ARGS__; } break;                 \
+    case 18: { constexpr int KK = 1, WW = 8; __VA_ARGS__; } break;                 \
+    default: throw Error(ESD_ERR_INTERNAL, "unsupported staged shape");            \
   }
 
 }  // namespace esd

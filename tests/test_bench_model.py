@@ -36,6 +36,27 @@ def test_spmv_model_fp64_and_fp32():
     assert fm == nnz + n + m * n
 
 
+def test_spmv_model_column_free_copy():
+    n, nnz = 2_097_152, 14_581_760
+    p = _problem(n, nnz)
+    lv = (np.array([n // 8]), None, None)
+    a32 = types.SimpleNamespace(precision="fp32", m=16)
+    slices, slots_a = n // 32, 7 * n
+    lay = {"column_free": [True, True, True], "slot_entries": [slots_a, 3 * n, 3 * n], "slices": slices}
+    by, fm = bench.kernel_model("spmv_pq", p, a32, ESD.PLAIN, ESD, lv, lay)
+    # 4-byte slot values and 32 bytes of slot bases per slice instead of 8-byte pairs
+    assert by == 4 * slots_a + 32 * slices + 12 * n + 4 * n
+    assert fm == nnz + n
+    # the deflated FP32 product keeps the pairs whatever the layout
+    by, _ = bench.kernel_model("spmv_pq", p, a32, ESD.DEFLATION, ESD, lv, lay)
+    assert by == 8 * nnz + 12 * n + 4 * n + 4 * 16 * n
+    # without the copy, or in FP64, the pairs
+    no = {"column_free": [False] * 3, "slot_entries": [0] * 3, "slices": slices}
+    assert bench.matrix_bytes(p, 4, no, 0) == 8 * nnz
+    assert bench.matrix_bytes(p, 8, lay, 0) == 12 * nnz
+    assert bench.matrix_bytes(p, 4, lay, 1) == 4 * 3 * n + 32 * slices
+
+
 def test_update_model():
     n, m = 1000, 16
     p = _problem(n, 7 * n)
