@@ -80,6 +80,9 @@ struct Scratch {
 
 constexpr int kMaxRed = 2 * kMaxM + 8;
 constexpr int kAffineSlots = 8;  // slots of a slice in the column-free copy, at most
+// zero elements before and after the FP32 vectors the column-free products gather: a slot's
+// column base + lane lies in [-31, n + 30] for every lane, also where the row has no entry
+constexpr int kGuard = 32;
 
 int grid_blocks(int work_slices);  // blocks for a launch over this many slices
 int max_grid_blocks();

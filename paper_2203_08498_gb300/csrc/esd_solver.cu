@@ -111,9 +111,9 @@ struct esd_solver {
     c.b = b32.as<float>();
     c.x = x32.as<float>();
     c.r = r32.as<float>();
-    c.p = p32.as<float>();
+    c.p = p32.as<float>() + kGuard;
     c.q = q32.as<float>();
-    c.Y = Y32.as<float>();
+    c.Y = Y32.as<float>() + kGuard;
     c.ld = ld;
     c.mode = md;
     c.pre = prm.precond;
@@ -292,8 +292,10 @@ struct esd_solver {
     if (!b32.get()) {
       const size_t fbytes = sizeof(float) * ld, vbytes = sizeof(double) * ld;
       for (DevBuf* b : {&b32, &x32, &r32, &p32, &q32, &Y32}) {
-        b->alloc(fbytes);
-        ESD_CUDA(cudaMemsetAsync(b->get(), 0, fbytes, stream));
+        // p and Y, which the row products gather, carry kGuard zeros before and after
+        const size_t bytes = (b == &p32 || b == &Y32) ? fbytes + 2 * kGuard * sizeof(float) : fbytes;
+        b->alloc(bytes);
+        ESD_CUDA(cudaMemsetAsync(b->get(), 0, bytes, stream));
       }
       r64.alloc(vbytes);
       ESD_CUDA(cudaMemsetAsync(r64.get(), 0, vbytes, stream));

@@ -35,8 +35,10 @@ constexpr int kStreamMaxStages = 3;                          // chunks in flight
 constexpr int kStreamWmax = 8;                               // widest slice the staged kernels take
 // Shapes of a staged launch: K slices per consumer warp per chunk, rows of at most W entries
 // (the register arrays of a lane hold K W entries). Code 10 K + W. The column-free copy's
-// 4-byte values leave registers for K = 2 with W = 8, which the (value, column) pairs do not.
-constexpr int kShapes[4] = {42, 24, 28, 18};
+// 4-byte values leave registers for K = 2 with W up to 8, which the (value, column) pairs do
+// not; its widths 6, 7 and 8 are exact, since a slot past a row's width still costs the
+// issue slots of its predicated instructions.
+constexpr int kShapes[6] = {42, 24, 26, 27, 28, 18};
 constexpr int kStreamMaxK = 4;                               // slices per consumer warp per chunk, at most
 constexpr int kStreamStageCap = 50 * 1024;                   // bytes of one stage, at most
 constexpr int kStreamRingCap = 100 * 1024;                   // bytes of the stage ring (2 blocks per SM)
@@ -118,7 +120,7 @@ inline StreamPlan stream_plan(const SliceSet& with_entries, const SliceSet& vect
   int K = 1, shape = 18;
   for (int sh : kShapes) {
     const int k = sh / 10, w = sh % 10;
-    if (sh == 28 && !aff) continue;
+    if (sh >= 26 && sh <= 28 && !aff) continue;
     if (std::max(wmax, 1) <= w && stream_stage_bytes(kStreamWarps * k, wmax, ebytes, nv4, nv8, hdr) <= kStreamStageCap) {
       K = k;
       shape = sh;
@@ -384,12 +386,12 @@ __device__ __forceinline__ void stream_slices(const StageView<NV>& sv, const Chu
 // Row products of K slices of one lane from staged FP32 entries: acc[t] += sum_e val_e *
 // (v[col_e] - vi[t]) (vi = 0 in the plain form), the entries of a row in stored order, as
 // row_fma and row_fma_diff take them. AFF = false: (value, column) pairs; AFF = true: the
-// column-free copy, column = slot base + lane (clamped to [0, cmax]: a slot where the row has
-// no entry holds 0 and may point anywhere). The K slices are the warp's, at local indices
+// column-free copy, column = slot base + lane (a slot where the row has no entry holds 0 and
+// points into the vector or into the kGuard zeros around it). The K slices are the warp's, at local indices
 // warp + t kStreamWarps. Every gather of the K rows is issued before the first FMA. A row
 // wider than W (which the launch plan excludes) is reported through `bad`.
 template <int K, int W, bool DIFF, bool AFF, int NV>
-__device__ __forceinline__ void staged_rows(const StageView<NV>& sv, const int4 (&md)[K], int warp, int lane, int cmax,
+__device__ __forceinline__ void staged_rows(const StageView<NV>& sv, const int4 (&md)[K], int warp, int lane,
                                             const float* __restrict__ v, const float (&vi)[K], float (&acc)[K],
                                             bool& bad) {
   float val[K][W], vj[K][W];
@@ -405,7 +407,7 @@ __device__ __forceinline__ void staged_rows(const StageView<NV>& sv, const int4 
       if (e < md[t].y) {
         if constexpr (AFF) {
           val[t][e] = sv.template ent<float>(0)[off + e * kSlice];
-          col = min(max(sb[e] + lane, 0), cmax);
+          col = sb[e] + lane;
         } else {
           const uint2 pr = sv.template ent<uint2>(0)[off + e * kSlice];
           val[t][e] = __uint_as_float(pr.x);
@@ -474,7 +476,6 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_spmv_pq_stream(IterCtx<T>
   const int warp = threadIdx.x >> 5, lane = lane_id();
   const EntSet es = stream_entries<AFF>(c.Av);
   const VecSet<2> vs{{c.rowsum, c.p}, {4, 4}, 2u, 0u};
-  const int cmax = (int)c.ld - 1;
   float acc[1] = {0.f}, cmp[1] = {0.f};
   if (warp == kStreamWarps) {
     if (lane == 0 && !stream_produce(pl, stream_metas<AFF>(c.Av), es, vs, full, empty)) stream_fail(st, c.cond);
@@ -492,7 +493,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_spmv_pq_stream(IterCtx<T>
         pv[t] = valid ? sv.template vec<float>(1, i) : 0.f;
         q[t] = fmaf(valid ? sv.template vec<float>(0, i) : 0.f, pv[t], 0.f);
       }
-      staged_rows<K, W, true, AFF>(sv, md, warp, lane, cmax, p, pv, q, bad);
+      staged_rows<K, W, true, AFF>(sv, md, warp, lane, p, pv, q, bad);
 #pragma unroll
       for (int t = 0; t < K; ++t)
         if (lane < md[t].w) {
@@ -592,7 +593,6 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
   const int warp = threadIdx.x >> 5, lane = lane_id();
   const EntSet es = stream_entries<AFF>(c.Lv);
   const VecSet<2> vs{{c.r, c.inv_d}, {4, 4}, 0u, 0u};
-  const int cmax = (int)c.ld - 1;
   float acc[1] = {0.f}, cmp[1] = {0.f};
   if (warp == kStreamWarps) {
     if (lane == 0 && !stream_produce(pl, stream_metas<AFF>(c.Lv), es, vs, full, empty)) stream_fail(st, c.cond);
@@ -612,7 +612,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
         d[t] = valid ? sv.template vec<float>(1, i) : 0.f;
         y[t] = valid ? sv.template vec<float>(0, i) : 0.f;
       }
-      staged_rows<K, W, false, AFF>(sv, md, warp, lane, cmax, Y, zero, y, bad);
+      staged_rows<K, W, false, AFF>(sv, md, warp, lane, Y, zero, y, bad);
       const bool to_z = (bwd0 >> cp.range) & 1u;
 #pragma unroll
       for (int t = 0; t < K; ++t)
@@ -660,7 +660,6 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_bwd_stream(IterCtx<T> c, 
   const bool first = st->iter == 0 || st->fresh_dir;
   const EntSet es = stream_entries<AFF>(c.Uv);
   const VecSet<3> vs{{c.Y, c.inv_d, c.p}, {4, 4, 4}, 0u, 5u};
-  const int cmax = (int)c.ld - 1;
   if (warp == kStreamWarps) {
     if (lane == 0 && !stream_produce(pl, stream_metas<AFF>(c.Uv), es, vs, full, empty)) stream_fail(st, c.cond);
   } else {
@@ -681,7 +680,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_bwd_stream(IterCtx<T> c, 
         d[t] = (valid && sweep) ? sv.template vec<float>(1, i) : 1.f;
         pold[t] = (valid && !first) ? sv.template vec<float>(2, i) : 0.f;
       }
-      if (sweep) staged_rows<K, W, false, AFF>(sv, md, warp, lane, cmax, Y, zero, z, bad);
+      if (sweep) staged_rows<K, W, false, AFF>(sv, md, warp, lane, Y, zero, z, bad);
 #pragma unroll
       for (int t = 0; t < K; ++t)
         if (lane < md[t].w) {
@@ -754,6 +753,8 @@ inline void launch_stream(void (*kernel)(KArgs...), int blocks, const StreamPlan
   switch (Srt) {                                                                   \
     case 42: { constexpr int KK = 4, WW = 2; __VA_ARGS__; } break;                 \
     case 24: { constexpr int KK = 2, WW = 4; __VA_ARGS__; } break;                 \
+    case 26: { constexpr int KK = 2, WW = 6; __VA_ARGS__; } break;                 \
+    case 27: { constexpr int KK = 2, WW = 7; __VA_ARGS__; } break;                 \
     case 28: { constexpr int KK = 2, WW = 8; __VA_ARGS__; } break;                 \
     case 18: { constexpr int KK = 1, WW = 8; __VA_ARGS__; } break;                 \
     default: throw Error(ESD_ERR_INTERNAL, "unsupported staged shape");            \
