@@ -117,9 +117,11 @@ int esd_matrix_info(const esd_matrix* A, int32_t* n, int64_t* nnz, int32_t* ncol
  * column-free copy, built at creation when every 32-row slice has at most 8 distinct
  * (column - lane) values: per slice 8 slot bases (32 bytes) and one 4-byte value per slot
  * and row, 0 where the row lacks that neighbour; 0 where the part keeps its (value, column)
- * pairs of 8 bytes. slot_entries (host, 3 int64, may be NULL): the values each copy holds
- * (slots x 32 summed over the slices; 0 without a copy). slices (host, may be NULL): the
- * number of 32-row slices. */
+ * pairs of 8 bytes. A's copy has no slot for the diagonal: the FP32 product takes the
+ * difference form s_i p_i + sum_j a_ij (p_j - p_i), in which the diagonal multiplies 0.
+ * slot_entries (host, 3 int64, may be NULL): the values each copy holds (slots x 32 summed
+ * over the slices; 0 without a copy). slices (host, may be NULL): the number of 32-row
+ * slices. */
 int esd_matrix_layout(const esd_matrix* A, int32_t* column_free, int64_t* slot_entries, int32_t* slices);
 
 /*

@@ -54,6 +54,7 @@ struct Sell {
   DevBuf abase;  // int[kAffineSlots] per slice: the slot bases
   DevBuf aval;   // float per slot entry (slots x 32 per slice)
   bool affine = false;
+  bool adiag = true;          // the diagonal has its slot (A's copy omits it: see its creation)
   int awmax = 0;              // most slots of a slice
   std::vector<int> aslots;    // slots per slice (host)
   template <typename T> SellView<T> view() const;

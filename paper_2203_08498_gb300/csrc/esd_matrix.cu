@@ -224,17 +224,23 @@ __global__ void k_fill(int nslices, int n, const int4* mA, const int4* mL, const
 }
 
 // Column-free copy, pattern: one warp per slice. The slot bases of a slice are the distinct
-// values of (column - lane) over its present entries (column < n), in increasing order; every
-// lane's columns increase, so its entries fall into increasing slots. slots[s] = their number,
-// or -1 when a slice needs more than kAffineSlots.
-__global__ void k_affine_slots(int nslices, int n, const int4* meta, const int* col, int* slots, int* abase) {
+// values of (column - lane) over its present entries (column < n; without the diagonal when
+// skip_diag), in increasing order; every lane's columns increase, so its entries fall into
+// increasing slots. slots[s] = their number, or -1 when a slice needs more than kAffineSlots.
+__global__ void k_affine_slots(int nslices, int n, const int4* meta, const int* col, int skip_diag, int* slots,
+                               int* abase) {
   const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (s >= nslices) return;
   const int4 md = meta[s];
+  const int row = md.z + lane;
   int e = 0, cnt = 0;
   auto base_at = [&](int k) {
-    const int c = k < md.y ? col[md.x + k * kSlice + lane] : n;
-    return c < n ? c - lane : INT_MAX;
+    while (true) {
+      const int c = k < md.y ? col[md.x + k * kSlice + lane] : n;
+      if (c >= n) return INT_MAX;
+      if (!(skip_diag && c == row)) return c - lane;
+      e = ++k;  // the diagonal has no slot: move past it
+    }
   };
   int cand = base_at(0);
   while (true) {
@@ -257,15 +263,16 @@ __global__ void k_affine_slots(int nslices, int n, const int4* meta, const int* 
 // Column-free copy, values: every present entry to its slot (the slots of absent entries keep
 // the zero they were allocated with).
 __global__ void k_affine_values(int nslices, int n, const int4* meta, const int* col, const double* val,
-                                const int4* ameta, const int* abase, float* aval) {
+                                int skip_diag, const int4* ameta, const int* abase, float* aval) {
   const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (s >= nslices) return;
   const int4 md = meta[s], am = ameta[s];
   const int* b = abase + (size_t)s * kAffineSlots;
+  const int row = md.z + lane;
   int k = 0;
   for (int e = 0; e < md.y; ++e) {
     const int c = col[md.x + e * kSlice + lane];
-    if (c >= n) continue;
+    if (c >= n || (skip_diag && c == row)) continue;
     while (k < am.y && b[k] + lane != c) ++k;
     if (k < am.y) aval[am.x + k * kSlice + lane] = (float)val[md.x + e * kSlice + lane];
   }
@@ -400,14 +407,15 @@ static void interleave(Sell& M, cudaStream_t s) {
 
 // Column-free FP32 copy of one part (pattern only; values come with the other FP32 copies):
 // built when every slice fits kAffineSlots slots.
-static void build_affine(Sell& part, int NS, int n, const std::vector<int2>& rows, cudaStream_t s) {
+static void build_affine(Sell& part, int NS, int n, const std::vector<int2>& rows, cudaStream_t s,
+                         bool skip_diag = false) {
   part.affine = false;
   part.awmax = 0;
   part.aslots.clear();
   if (NS == 0) return;
   DevBuf dslots(sizeof(int) * NS), dbase(sizeof(int) * (size_t)NS * kAffineSlots);
   k_affine_slots<<<(NS * 32 + 255) / 256, 256, 0, s>>>(NS, n, part.meta.as<int4>(), part.col.as<int>(),
-                                                      dslots.as<int>(), dbase.as<int>());
+                                                      skip_diag ? 1 : 0, dslots.as<int>(), dbase.as<int>());
   ESD_CUDA(cudaGetLastError());
   std::vector<int> slots(NS);
   ESD_CUDA(cudaMemcpyAsync(slots.data(), dslots.get(), dslots.bytes(), cudaMemcpyDeviceToHost, s));
@@ -429,12 +437,14 @@ static void build_affine(Sell& part, int NS, int n, const std::vector<int2>& row
   part.awmax = *std::max_element(slots.begin(), slots.end());
   part.aslots = std::move(slots);
   part.affine = true;
+  part.adiag = !skip_diag;
 }
 
 static void affine_values(const Sell& part, int NS, int n, cudaStream_t s) {
   if (!part.affine || NS == 0) return;
   k_affine_values<<<(NS * 32 + 255) / 256, 256, 0, s>>>(NS, n, part.meta.as<int4>(), part.col.as<int>(),
-                                                       part.val.as<double>(), part.ameta.as<int4>(),
+                                                       part.val.as<double>(), part.adiag ? 0 : 1,
+                                                       part.ameta.as<int4>(),
                                                        part.abase.as<int>(), part.aval.as<float>());
   ESD_CUDA(cudaGetLastError());
 }
@@ -771,7 +781,11 @@ int esd_create_matrix(int32_t n, int64_t nnz, const int32_t* rowptr, const int32
         M->A.col.as<int>(), M->A.val.as<double>(), M->L.col.as<int>(), M->L.val.as<double>(),
         M->U.col.as<int>(), M->umap.as<int>());
     ESD_CUDA(cudaGetLastError());
-    for (Sell* part : {&M->A, &M->L, &M->U}) build_affine(*part, NS, n, rows, s);
+    // A's copy serves the difference-form product, s_i p_i + sum_j a_ij (p_j - p_i), in which
+    // the diagonal multiplies p_i - p_i = 0: it gets no slot
+    build_affine(M->A, NS, n, rows, s, true);
+    build_affine(M->L, NS, n, rows, s);
+    build_affine(M->U, NS, n, rows, s);
 
     // slice flags and launch sets
     build_level_sets(M.get(), hadj);
