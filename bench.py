@@ -92,6 +92,9 @@ def parse():
     ap.add_argument("--inner-tol", dest="inner_tol", type=float, default=None,
                     help="residual reduction of each FP32 inner solve in the refinement form")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, comparison modes and CPU baseline")
+    ap.add_argument("--no-pair", dest="no_pair", action="store_true",
+                    help="c5: solve each forward system and its adjoint one after the other instead of "
+                         "pairing the adjoint of system t with the forward solve of system t + 1")
     a = ap.parse_args()
     for k, v in CONFIGS[a.config].items():
         if getattr(a, k, None) is None:
@@ -233,11 +236,24 @@ def launch_count(info, mode_is, m, fp32, its, outer):
     total = 0
     for k, o in zip(its, outer):
         if fp32:
-            total += 1 + o * (1 + start + end + 2)  # residual; per step prep, start, end, apply, residual
+            total += 2 + o * (start + end + 2)  # residual, final; per step prep, start, end, residual
         else:
             total += start + end + 1               # + true residual
         total += body * k
     return total
+
+
+def pair_launch_count(info, its, outer, paired):
+    """Kernels launched by one esd_solve_pair: per refinement step both systems' prep, start,
+    finish and residual and the three loop conditions; one body per paired iteration and
+    one per iteration that either system ran alone."""
+    nf = info["fwd_levels"] - 1
+    nb = max(info["bwd_levels"] - 1, 1)
+    body = 2 + nf + nb
+    start = 1 + 1 + nf + nb
+    end = 1
+    o = max(outer)
+    return 5 + o * (2 * (start + end + 2) + 4) + body * (sum(its) - paired)
 
 
 def gpu_arm(args):
@@ -490,13 +506,17 @@ def build_w(S, args):
 
 
 def system_arm(args, esd, torch, dev, ws, rank):
-    """One step = one system of the backward-Euler sequence: b_t = x_{t-1}/dt + s on the
-    device, the forward solve in the configured mode, then its adjoint A lambda = 2 (x_t -
-    x_target) (warm-started from lambda_{t-1}). x, lambda and W carry over from step to step;
-    the first warm-up step is system 1 (the sampling solve and the W build), so the timed
-    steps are later systems of the same sequence (continuing past its 50 systems when more
-    steps are asked for). After the timed steps, two more systems are solved once more in the
-    same mode and by plain FP64 PCG from the same b_t and x_{t-1}, timed per solve; the FP64
+    """One step = one forward solve and one adjoint solve of the backward-Euler sequence:
+    b_t = x_{t-1}/dt + s on the device, the forward solve in the configured mode, and the
+    adjoint A lambda = 2 (x - x_target) (warm-started from the previous lambda). Unpaired
+    (--no-pair, and every mode but plain FP32): system t's forward solve, then its adjoint.
+    Paired (plain FP32, the default): the adjoint of system t - 1 and the forward solve of
+    system t need only x_{t-1}, so one esd_solve_pair runs both. x, lambda and W carry over
+    from step to step; the first warm-up step is system 1 (the sampling solve and the W
+    build; paired, its adjoint goes with system 2), so the timed steps are later systems of
+    the same sequence (continuing past its 50 systems when more steps are asked for). After
+    the timed steps, two more steps are solved once more, system by system in every mode and
+    by plain FP64 PCG from the same right-hand sides and starts, timed per solve; the FP64
     comparator is resumed (esd_solve again from its own x) until its true residual
     ||b - A x|| / ||b|| recomputed in FP64 meets the tolerance."""
     p = workload(args)
@@ -508,6 +528,10 @@ def system_arm(args, esd, torch, dev, ws, rank):
     A.factor_ic0()
     S = esd.Solver(A, maxit_cap=20000, sample_cap=max(args.m, 2), precision=esd.FP32_REFINE if fp32 else esd.FP64,
                    inner_tol=args.inner_tol)
+    paired = fp32 and mode == esd.PLAIN and not args.no_pair
+    # the adjoint's solver of a pair (same matrix and factor, its own vectors and state)
+    Sa = esd.Solver(A, maxit_cap=20000, sample_cap=0, precision=esd.FP32_REFINE, inner_tol=args.inner_tol) \
+        if paired else None
     src = torch.from_numpy(p.source).to(dev)
     x = torch.zeros(n, dtype=torch.float64, device=dev)
     b = torch.empty_like(x)
@@ -559,8 +583,50 @@ def system_arm(args, esd, torch, dev, ws, rank):
                 "adjoint_outer": adj["outer_steps"], "true_relres": fwd["true_relres"],
                 "adjoint_true_relres": adj["true_relres"], "restarts": fwd["restarts"] + adj["restarts"]}
 
+    def first_forward():
+        """System 1 alone (paired steps): the sampling solve and the W build."""
+        state["t"] += 1
+        S.backward_euler_rhs(x, src, inv_dt, b)
+        S.set_mode(esd.PLAIN)
+        st, it, rr = S.solve(b, x, args.tol, 20000, args.m)
+        if st != esd.OK:
+            raise RuntimeError(f"solve of system 1 returned {st}")
+        state["cond"] = S.estimate_cond()
+        state["kept"] = build_w(S, args)
+        S.set_mode(mode)
+
+    def one_pair(marks=None, save=None):
+        """The forward solve of system t + 1 and the adjoint of system t, both from x_t, in one
+        esd_solve_pair; marks and save as one_system's (marks[1] = marks[2]: one call)."""
+        t = state["t"]
+        state["t"] += 1
+        if marks:
+            marks[0].record()
+        S.backward_euler_rhs(x, src, inv_dt, b)
+        S.backward_euler_rhs(x, neg2xt, 2.0, g)
+        if save is not None:
+            save.update(b=b.clone(), x0=x.clone(), g=g.clone(), lam0=lam.clone())
+        st, (it, _), (ita, _), npair = S.solve_pair(Sa, b, x, g, lam, args.tol, 20000)
+        if st != esd.OK:
+            raise RuntimeError(f"pair solve of system {t + 1} (adjoint of system {t}) returned {st}")
+        if marks:
+            marks[1].record()
+            marks[2].record()
+        fwd, adj = S.last_solve_info(), Sa.last_solve_info()
+        return {"system": t + 1, "adjoint_of": t, "iters": it, "adjoint_iters": ita, "paired": npair,
+                "outer": fwd["outer_steps"], "adjoint_outer": adj["outer_steps"],
+                "true_relres": fwd["true_relres"], "adjoint_true_relres": adj["true_relres"],
+                "restarts": fwd["restarts"] + adj["restarts"]}
+
+    def step(marks=None, save=None):
+        if not paired:
+            return one_system(marks, save)
+        if state["t"] == 0:
+            first_forward()
+        return one_pair(marks, save)
+
     for _ in range(args.warmup):
-        one_system()
+        step()
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
@@ -568,7 +634,7 @@ def system_arm(args, esd, torch, dev, ws, rank):
     clocks = Clocks(dev.index if dev.index is not None else 0)
     marks = [[ev(), ev(), ev()] for _ in range(args.steps)]
     t0 = time.perf_counter()
-    rows = [one_system(marks[k]) for k in range(args.steps)]
+    rows = [step(marks[k]) for k in range(args.steps)]
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
@@ -584,8 +650,12 @@ def system_arm(args, esd, torch, dev, ws, rank):
     launches = 0
     for r in rows:
         launches += 2  # right-hand sides
-        launches += launch_count(info, args.mode, args.m, fp32, [r["iters"], r["adjoint_iters"]],
-                                 [r["outer"], r["adjoint_outer"]])
+        if paired:
+            launches += pair_launch_count(info, [r["iters"], r["adjoint_iters"]], [r["outer"], r["adjoint_outer"]],
+                                          r["paired"])
+        else:
+            launches += launch_count(info, args.mode, args.m, fp32, [r["iters"], r["adjoint_iters"]],
+                                     [r["outer"], r["adjoint_outer"]])
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -593,7 +663,9 @@ def system_arm(args, esd, torch, dev, ws, rank):
         "dtype": "f64" if not fp32 else "f32 inner, f64 refinement", "data": "synthetic",
         "config": {"workload": workload_name(args, p), "config": args.config, "grid": args.grid, "n": n,
                    "nnz": p.nnz, "systems_in_sequence": args.systems,
-                   "step": "one system of the sequence: forward solve + adjoint solve",
+                   "step": ("the forward solve of system t + 1 with the adjoint of system t, paired "
+                            "(esd_solve_pair)" if paired else
+                            "one system of the sequence: forward solve + adjoint solve"),
                    "m": args.m, "m_kept": state["kept"], "mode": args.mode, "tol": args.tol,
                    "precision": args.precision, "inner_tol": args.inner_tol if fp32 else None,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
@@ -601,9 +673,11 @@ def system_arm(args, esd, torch, dev, ws, rank):
         "gpu_launches": launches,
         "clocks": clk,
         "wall_s_timed": wall,
-        "time_to_tol_ms_per_system": {"forward": float(np.mean(fwd_ms)), "adjoint": float(np.mean(adj_ms)),
-                                      "per_solve": ms_step / 2},
+        "time_to_tol_ms_per_system": ({"pair": float(np.mean(fwd_ms)), "per_solve": ms_step / 2} if paired else
+                                      {"forward": float(np.mean(fwd_ms)), "adjoint": float(np.mean(adj_ms)),
+                                       "per_solve": ms_step / 2}),
         "systems": [r["system"] for r in rows],
+        "paired_iterations": [r["paired"] for r in rows] if paired else None,
         "iterations": [r["iters"] for r in rows],
         "adjoint_iterations": [r["adjoint_iters"] for r in rows],
         "refinement_steps": [r["outer"] for r in rows] if fp32 else None,
@@ -616,9 +690,16 @@ def system_arm(args, esd, torch, dev, ws, rank):
 
     # roofline of the dominant kernel from live per-kernel times of the same kernels
     S.set_mode(mode)
-    prof = S.profile_iterations(b, x.clone(), reps=10)
     peaks = read_peaks()
-    result["roofline"], result["kernel_times_ms"] = roofline(prof, p, args, mode, esd, peaks, A.layout())
+    if paired:
+        # the kernels of the timed steps: the paired launches (b and g of the last step)
+        prof = S.profile_pair_iterations(Sa, b, x.clone(), g, lam.clone(), reps=10)
+        result["roofline"], result["kernel_times_ms"] = roofline(prof, p, args, mode, esd, peaks, A.layout(),
+                                                                 pair=True)
+        result["kernel_times_ms_unpaired"] = dict(S.profile_iterations(b, x.clone(), reps=10))
+    else:
+        prof = S.profile_iterations(b, x.clone(), reps=10)
+        result["roofline"], result["kernel_times_ms"] = roofline(prof, p, args, mode, esd, peaks, A.layout())
 
     # the next two systems: this mode (advancing the sequence), then from the same b_t and
     # x_{t-1} (and g_t, lambda_{t-1}) the other modes of this precision form with the same W,
@@ -645,13 +726,21 @@ def system_arm(args, esd, torch, dev, ws, rank):
     for _ in range(2):
         saved = {}
         mk = [ev(), ev(), ev()]
-        r = one_system(mk, save=saved)
+        r = step(mk, save=saved)
         torch.cuda.synchronize()
-        row = {"system": r["system"], "this": {"forward_ms": mk[0].elapsed_time(mk[1]),
-                                               "adjoint_ms": mk[1].elapsed_time(mk[2]),
-                                               "iters": r["iters"], "adjoint_iters": r["adjoint_iters"],
+        row = {"system": r["system"], "this": {"iters": r["iters"], "adjoint_iters": r["adjoint_iters"],
                                                "true_relres": r["true_relres"],
                                                "adjoint_true_relres": r["adjoint_true_relres"]}}
+        if paired:
+            row["adjoint_of"] = r["adjoint_of"]
+            row["this"].update(pair_ms=mk[0].elapsed_time(mk[1]), paired=r["paired"])
+            # the same two solves one after the other (esd_solve), same mode and precision
+            fms, fit, finfo = timed_solve(S, saved["b"], saved["x0"])
+            ams, ait, ainfo = timed_solve(S, saved["g"], saved["lam0"])
+            row["plain_unpaired"] = {"forward_ms": fms, "adjoint_ms": ams, "iters": fit, "adjoint_iters": ait,
+                                     "true_relres": max(finfo["true_relres"], ainfo["true_relres"])}
+        else:
+            row["this"].update(forward_ms=mk[0].elapsed_time(mk[1]), adjoint_ms=mk[1].elapsed_time(mk[2]))
         for name in others:
             S.set_mode(modes_map[name])
             fms, fit, finfo = timed_solve(S, saved["b"], saved["x0"])
@@ -676,7 +765,8 @@ def system_arm(args, esd, torch, dev, ws, rank):
             row["fp64_plain_" + name] = {"ms": e0.elapsed_time(e1), "iters": its, "resumed": resumed,
                                          "true_relres_first_stop": first_true, "true_relres": S64.true_relres()}
         cmp_rows.append(row)
-    this_ms = float(np.mean([c["this"]["forward_ms"] + c["this"]["adjoint_ms"] for c in cmp_rows]))
+    pair_ms = lambda c: c["pair_ms"] if "pair_ms" in c else c["forward_ms"] + c["adjoint_ms"]  # noqa: E731
+    this_ms = float(np.mean([pair_ms(c["this"]) for c in cmp_rows]))
     f64_ms = float(np.mean([c["fp64_plain_forward"]["ms"] + c["fp64_plain_adjoint"]["ms"] for c in cmp_rows]))
     result["vs_fp64_plain"] = {"systems": cmp_rows, "ms_per_system_this": this_ms / 2,
                                "ms_per_system_fp64_plain_to_true_tol": f64_ms / 2,
@@ -685,7 +775,7 @@ def system_arm(args, esd, torch, dev, ws, rank):
     modes_out = {args.mode: {"ms_per_solve": this_ms / 2,
                              "iters_per_solve": float(np.mean([(c["this"]["iters"] + c["this"]["adjoint_iters"]) / 2
                                                                for c in cmp_rows]))}}
-    for name in others:
+    for name in others + (["plain_unpaired"] if paired else []):
         ms_o = float(np.mean([c[name]["forward_ms"] + c[name]["adjoint_ms"] for c in cmp_rows]))
         modes_out[name] = {"ms_per_solve": ms_o / 2,
                            "iters_per_solve": float(np.mean([(c[name]["iters"] + c[name]["adjoint_iters"]) / 2
@@ -706,24 +796,29 @@ def system_arm(args, esd, torch, dev, ws, rank):
     lay = A.layout() if mode == esd.PLAIN else None
     mat = matrix_bytes(p, s_in, lay, 0) + (matrix_bytes(p, s_in, lay, 1) + matrix_bytes(p, s_in, lay, 2)
                                            if lay is not None and lay["column_free"][1] else (s_in + 4) * p.nnz)
-    model_this = mat + (4 + 12 * s_in) * n + (2 * s_in * m_eff * n + 2 * s_in * n if m_eff else 0)
+    vec_this = (4 + 12 * s_in) * n + (2 * s_in * m_eff * n + 2 * s_in * n if m_eff else 0)
+    model_this = mat + vec_this
     model_f64 = 24 * p.nnz + 100 * n
     it_this = np.mean([c["this"]["iters"] + c["this"]["adjoint_iters"] for c in cmp_rows])
     it_f64 = np.mean([c["fp64_plain_forward"]["iters"] + c["fp64_plain_adjoint"]["iters"] for c in cmp_rows])
+    # a paired iteration reads the matrix once for both systems
+    np_this = np.mean([c["this"].get("paired", 0) for c in cmp_rows])
+    bytes_this = np_this * (mat + 2 * vec_this) + (it_this - 2 * np_this) * model_this
     result["iteration_bandwidth"] = {
         "this": {"model_bytes_per_iter": model_this, "ms_per_iter": this_ms / it_this,
-                 "model_gbs": model_this / (this_ms / it_this / 1e3) / 1e9},
+                 "paired_iters": float(np_this), "model_bytes": bytes_this,
+                 "model_gbs": bytes_this / (this_ms / 1e3) / 1e9},
         "fp64_plain": {"model_bytes_per_iter": model_f64, "ms_per_iter": f64_ms / it_f64,
                        "model_gbs": model_f64 / (f64_ms / it_f64 / 1e3) / 1e9},
         "peak_gbs": peaks["hbm_gbs"], "peak_src": peaks["src"]}
-    result["e2e"] = system_e2e(esd, p, args, torch, S, x, lam, src, neg2xt)
+    result["e2e"] = system_e2e(esd, p, args, torch, S, x, lam, src, neg2xt, Sa)
     return result, None
 
 
-def system_e2e(esd, p, args, torch, S, x, lam, src, neg2xt):
+def system_e2e(esd, p, args, torch, S, x, lam, src, neg2xt, Sa=None):
     """The same step through the C ABI with host buffers: the right-hand sides and both
-    solves take pinned host arrays, so every system's inputs go in and its results come
-    back inside the timed region (the library stages the copies)."""
+    solves (or the pair solve, with Sa) take pinned host arrays, so every system's inputs go
+    in and its results come back inside the timed region (the library stages the copies)."""
     pin = lambda t: t.cpu().pin_memory()  # noqa: E731
     x_h, lam_h, src_h, n2_h = pin(x), pin(lam), pin(src), pin(neg2xt)
     b_h = torch.zeros(p.n, dtype=torch.float64).pin_memory()
@@ -731,10 +826,18 @@ def system_e2e(esd, p, args, torch, S, x, lam, src, neg2xt):
     inv_dt = 1.0 / p.dt
 
     def step():
-        S.backward_euler_rhs(x_h, src_h, inv_dt, b_h)
-        S.solve(b_h, x_h, args.tol, 20000, 0)
-        S.backward_euler_rhs(x_h, n2_h, 2.0, g_h)
-        S.solve(g_h, lam_h, args.tol, 20000, 0)
+        if Sa is not None:
+            S.backward_euler_rhs(x_h, src_h, inv_dt, b_h)
+            S.backward_euler_rhs(x_h, n2_h, 2.0, g_h)
+            st, _, _, _ = S.solve_pair(Sa, b_h, x_h, g_h, lam_h, args.tol, 20000)
+        else:
+            S.backward_euler_rhs(x_h, src_h, inv_dt, b_h)
+            st, _, _ = S.solve(b_h, x_h, args.tol, 20000, 0)
+            if st == esd.OK:
+                S.backward_euler_rhs(x_h, n2_h, 2.0, g_h)
+                st, _, _ = S.solve(g_h, lam_h, args.tol, 20000, 0)
+        if st != esd.OK:
+            raise RuntimeError(f"end-to-end step returned {st}")
 
     step()
     torch.cuda.synchronize()
@@ -746,8 +849,8 @@ def system_e2e(esd, p, args, torch, S, x, lam, src, neg2xt):
     sec = time.perf_counter() - t0
     n = p.n
     # rhs: x_prev, s in, b out; solve: b, x in, x out; adjoint rhs: x, -2 x_t in, g out;
-    # adjoint solve: g, lambda in, lambda out
-    h2d = 8 * n * 6
+    # adjoint solve: g, lambda in, lambda out (paired: the same vectors)
+    h2d = 8 * n * 8
     d2h = 8 * n * 4
     return {"value": 2 * k / sec, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "ms_per_step": sec * 1e3 / k, "steps": k}
@@ -840,9 +943,18 @@ def matrix_bytes(p, s, layout, part):
     return (s + 4) * entries
 
 
-def kernel_model(name, p, args, mode, esd, lv, layout=None):
+def kernel_model(name, p, args, mode, esd, lv, layout=None, pair=False):
     """Algorithmic bytes and FMAs of one launch, each array element counted once; value
-    size s = 8 (FP64) or 4 (FP32 inner kernels, whose SpMV also reads s = A 1)."""
+    size s = 8 (FP64) or 4 (FP32 inner kernels, whose SpMV also reads s = A 1). pair: the
+    paired launch of two systems (plain FP32), which reads the matrix, s = A 1 and 1/l_ii
+    once and every vector of each system."""
+    if pair:
+        one_b, one_f = kernel_model(name, p, args, mode, esd, lv, layout)
+        if one_b is None:
+            return None, None
+        n = p.n
+        shared = matrix_bytes(p, 4, layout, 0) + 4 * n if name == "spmv_pq" else 4 * int(lv[0][0])
+        return 2 * one_b - shared, 2 * one_f
     n, nnz = p.n, p.nnz
     s = 4 if args.precision == "fp32" else 8
     m = args.m if mode != esd.PLAIN else 0
@@ -874,12 +986,12 @@ def pad_m(m):
     return 0 if m <= 0 else next(c for c in (8, 16, 24, 32, 64) if m <= c)
 
 
-def roofline(prof, p, args, mode, esd, peaks, layout=None):
+def roofline(prof, p, args, mode, esd, peaks, layout=None, pair=False):
     lv = level_stats(p)
     times = {nm: t for nm, t in prof}
     cand = [(t, nm) for nm, t in prof if nm in ("spmv_pq", "update")]
     t_ms, name = max(cand)
-    by, fmas = kernel_model(name, p, args, mode, esd, lv, layout)
+    by, fmas = kernel_model(name, p, args, mode, esd, lv, layout, pair)
     sec = t_ms / 1e3
     gbs = by / sec / 1e9
     tflops = 2 * fmas / sec / 1e12
@@ -887,7 +999,9 @@ def roofline(prof, p, args, mode, esd, peaks, layout=None):
     alu_peak = FP32_NOMINAL_TFLOPS if args.precision == "fp32" else FP64_NOMINAL_TFLOPS
     f_alu = tflops / alu_peak
     full_size = args.grid == CONFIGS[args.config]["grid"]
-    traffic = read_traffic(TRAFFIC.get((args.config, args.precision, name))) if full_size else None
+    key = (args.config, args.precision, name + ("_pair" if pair else ""))
+    traffic = read_traffic(TRAFFIC.get(key)) if full_size else None
+    name = name + " (paired, two systems)" if pair else name
     if f_alu > f_hbm:
         roof = {"bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": f_alu, "traffic": traffic, "kernel": name,

@@ -255,6 +255,41 @@ int esd_set_mode(esd_solver* S, int32_t mode);
 int esd_solve(esd_solver* S, const double* b, double* x, double tol, int32_t maxit,
               int32_t sample_m, int32_t* iters, double* relres);
 
+/*
+ * Two systems A x_1 = b_1 and A x_2 = b_2 with the same matrix, solved together (not in the
+ * paper: a way of running two solves of a sequence that need only the same earlier solution,
+ * such as the adjoint of system t and the forward solve of system t + 1, which both need
+ * x_t). Each system runs its own refinement-form solve exactly as esd_solve does it (plain
+ * PCG with IC(0), FP32 inner runs, FP64 refinement, same tol and maxit, no sampling), with its
+ * own solver's state. In every refinement step the inner iterations of both share each pass
+ * over the matrix and its factor while both inner runs go on; the one left then goes on with
+ * the single kernels. The two trajectories equal their single runs up to the rounding of the
+ * FP32 dot products, whose per-thread partial sums cover other rows.
+ * S1, S2: two distinct solvers on the same matrix (and preconditioning matrix), both in
+ * ESD_FP32_REFINE and ESD_PLAIN with IC(0), no power method. b_k, x_k: n doubles each, host
+ * or device, x_k the start vector on input and the solution on output. iters_k, relres_k
+ * (host, may be NULL): as esd_solve's, per system; each solver's esd_last_solve_info and
+ * esd_true_relres describe its system afterwards. paired (host, may be NULL): iterations
+ * run by the paired kernels (each advanced both systems), over all refinement steps. The first call for a pair builds its graph
+ * (kept in S1 while neither solver's graphs are rebuilt).
+ * Errors: ESD_ERR_STATE when the pair cannot run these kernels (the message says why: the
+ * staged kernels are off, rows wider than 8 entries, more than 16 forward colour levels, ...);
+ * otherwise as esd_solve, the first failing system's code (the message names it).
+ */
+int esd_solve_pair(esd_solver* S1, esd_solver* S2, const double* b1, double* x1, const double* b2, double* x2,
+                   double tol, int32_t maxit, int32_t* iters1, double* relres1, int32_t* iters2, double* relres2,
+                   int32_t* paired);
+
+/*
+ * Measurement of the pair solve's kernels: reps paired iterations of the FP32 inner PCG on
+ * A d = b_1 and A d = b_2 from d = x_1, x_2 (rounded to FP32), launched one by one with CUDA
+ * events between them, as esd_profile_iterations does for one system (tolerance 0). S1, S2
+ * as esd_solve_pair asks (same errors); ms, names, cap, count as esd_profile_iterations;
+ * x_1, x_2 (device or host) receive the FP64 iterates after reps steps.
+ */
+int esd_profile_pair_iterations(esd_solver* S1, esd_solver* S2, const double* b1, double* x1, const double* b2,
+                                double* x2, int32_t reps, double* ms, char* names, int32_t cap, int32_t* count);
+
 /* ||b - A x|| / ||b|| of the last solve, recomputed in FP64 from the returned x. */
 int esd_true_relres(esd_solver* S, double* relres);
 

@@ -39,10 +39,11 @@ __all__ = [
     "esd_create_matrix", "esd_matrix_destroy", "esd_matrix_info", "esd_matrix_layout", "esd_factor_ic0",
     "esd_matrix_spmv",
     "esd_matrix_apply_ic", "esd_pattern_grad", "esd_params_default", "esd_solver_create",
-    "esd_solver_destroy", "esd_set_mode", "esd_solve", "esd_true_relres", "esd_last_solve_info",
+    "esd_solver_destroy", "esd_set_mode", "esd_solve", "esd_solve_pair", "esd_true_relres", "esd_last_solve_info",
     "esd_sample_and_build_W",
     "esd_set_W", "esd_get_W", "esd_ritz_values", "esd_estimate_cond", "esd_get_history",
-    "esd_get_samples", "esd_backward_euler_rhs", "esd_profile_iterations", "esd_last_error",
+    "esd_get_samples", "esd_backward_euler_rhs", "esd_profile_iterations", "esd_profile_pair_iterations",
+    "esd_last_error",
     "esd_lanczos_extremes_noalloc", "NOALLOC_MAX_K", "esd_matrix_set_values", "esd_fv_assemble",
     "esd_fv_grad_theta", "esd_refresh_W", "EsdFvGrid", "esd_power_start", "esd_power_estimate",
     "esd_matrix_diag_scale", "MATRIX_DIAG_SCALE", "esd_set_precision", "esd_solver_set_precond_matrix",
@@ -117,6 +118,7 @@ def lib(build_if_missing: bool = True):
             "esd_solver_destroy": (i32, [vp]),
             "esd_set_mode": (i32, [vp, i32]),
             "esd_solve": (i32, [vp, vp, vp, f64, i32, i32, P(i32), P(f64)]),
+            "esd_solve_pair": (i32, [vp, vp, vp, vp, vp, vp, f64, i32, P(i32), P(f64), P(i32), P(f64), P(i32)]),
             "esd_true_relres": (i32, [vp, P(f64)]),
             "esd_last_solve_info": (i32, [vp, P(i32), P(i32), P(i32), P(i32), P(f64), P(f64), P(i32)]),
             "esd_sample_and_build_W": (i32, [vp, f64, P(i32)]),
@@ -128,6 +130,7 @@ def lib(build_if_missing: bool = True):
             "esd_get_samples": (i32, [vp, vp, vp, i32, P(i32)]),
             "esd_backward_euler_rhs": (i32, [vp, vp, vp, f64, vp]),
             "esd_profile_iterations": (i32, [vp, vp, vp, i32, vp, vp, i32, P(i32)]),
+            "esd_profile_pair_iterations": (i32, [vp, vp, vp, vp, vp, vp, i32, vp, vp, i32, P(i32)]),
             "esd_lanczos_extremes_noalloc": (i32, [vp, vp, i32, vp, vp]),
             "esd_matrix_set_values": (i32, [vp, vp]),
             "esd_fv_assemble": (i32, [vp, P(EsdFvGrid), vp, vp]),
@@ -305,6 +308,16 @@ def esd_solve(h, b, x, tol, maxit, sample_m=0):
     return st, it.value, rr.value
 
 
+def esd_solve_pair(h1, h2, b1, x1, b2, x2, tol, maxit):
+    """Two systems with the same matrix together (both solvers in the refinement form, plain
+    mode). Returns (status, (iters1, relres1), (iters2, relres2), paired): status OK or
+    ERR_MAXIT (other errors raise), paired the iterations the paired kernels ran."""
+    i1, r1, i2, r2, pr = C.c_int32(), C.c_double(), C.c_int32(), C.c_double(), C.c_int32()
+    st = _check(lib().esd_solve_pair(h1, h2, _ptr(b1), _ptr(x1), _ptr(b2), _ptr(x2), tol, maxit, C.byref(i1),
+                                     C.byref(r1), C.byref(i2), C.byref(r2), C.byref(pr)), allow=(ERR_MAXIT,))
+    return st, (i1.value, r1.value), (i2.value, r2.value), pr.value
+
+
 def esd_true_relres(h):
     v = C.c_double()
     _check(lib().esd_true_relres(h, C.byref(v)))
@@ -410,6 +423,18 @@ def esd_profile_iterations(h, b, x, reps, cap=64):
     names = C.create_string_buffer(32 * cap)
     cnt = C.c_int32()
     _check(lib().esd_profile_iterations(h, _ptr(b), _ptr(x), reps, _ptr(ms), names, cap, C.byref(cnt)))
+    k = min(cnt.value, cap)
+    raw = names.raw
+    return [(raw[32 * j: 32 * j + 32].split(b"\0")[0].decode(), float(ms[j])) for j in range(k)]
+
+
+def esd_profile_pair_iterations(h1, h2, b1, x1, b2, x2, reps, cap=64):
+    """[(kernel name, average ms per launch)] for one paired iteration of two systems."""
+    ms = np.zeros(cap)
+    names = C.create_string_buffer(32 * cap)
+    cnt = C.c_int32()
+    _check(lib().esd_profile_pair_iterations(h1, h2, _ptr(b1), _ptr(x1), _ptr(b2), _ptr(x2), reps, _ptr(ms), names,
+                                             cap, C.byref(cnt)))
     k = min(cnt.value, cap)
     raw = names.raw
     return [(raw[32 * j: 32 * j + 32].split(b"\0")[0].decode(), float(ms[j])) for j in range(k)]
@@ -524,6 +549,10 @@ class Solver:
     def solve(self, b, x, tol=1e-8, maxit=None, sample_m=0):
         return esd_solve(self._h, b, x, tol, maxit or self.maxit_cap, sample_m)
 
+    def solve_pair(self, other, b1, x1, b2, x2, tol=1e-8, maxit=None):
+        """This solver's system and `other`'s solved together (esd_solve_pair)."""
+        return esd_solve_pair(self._h, other._h, b1, x1, b2, x2, tol, maxit or min(self.maxit_cap, other.maxit_cap))
+
     def true_relres(self):
         return esd_true_relres(self._h)
 
@@ -576,6 +605,9 @@ class Solver:
 
     def profile_iterations(self, b, x, reps=20):
         return esd_profile_iterations(self._h, b, x, reps)
+
+    def profile_pair_iterations(self, other, b1, x1, b2, x2, reps=20):
+        return esd_profile_pair_iterations(self._h, other._h, b1, x1, b2, x2, reps)
 
     def backward_euler_rhs(self, x_prev, s, inv_dt, b):
         esd_backward_euler_rhs(self._h, x_prev, s, inv_dt, b)

@@ -82,6 +82,7 @@ struct State {
   int pend_slot;    // slot to receive x at the next update (-1 = none)
   int pend_prev;    // slot_iter[pend_slot] before it was claimed (a deferred sample's undo)
   int guard;        // loop bodies started; a second, reduction-free bound on the loop
+  int paired;       // bodies of a pair's paired loop started (kept in the first system's state)
   int defer_sample; // resumed runs: a stopping run leaves its sample to the run that resumes
   int fresh_dir;    // the next direction update starts afresh (p = z) without resetting iter
   int samp_method;  // 0: sampling method A, 1: method B (relative residual levels)

@@ -1387,6 +1387,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_true_res(IterCtx<T> c, SliceSet s
 }  // namespace esd
 
 #include "esd_stream.cuh"
+#include "esd_stream_pair.cuh"
 
 namespace esd {
 

@@ -101,4 +101,10 @@ void launch_spmm(const esd_matrix* A, const double* X, double* Y, size_t ld, int
 void launch_axpby(int n, const double* x, double a, const double* sv, double* b, cudaStream_t s);
 int pad_m(int m);  // the compiled column count >= m
 
+// Two FP32 refinement-form systems with the same matrix, one PCG iteration of both per pass
+// over the matrix (plain mode, IC(0)); cond ends the paired loop once either has stopped.
+std::string pair_unsupported(const IterCtx<float>& c1, const IterCtx<float>& c2);  // "" when supported
+void launch_iteration_pair(const IterCtx<float>& c1, const IterCtx<float>& c2, unsigned long long cond,
+                           cudaStream_t s, KernelMarks* marks = nullptr);
+
 }  // namespace esd

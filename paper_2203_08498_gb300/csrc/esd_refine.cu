@@ -23,10 +23,13 @@ namespace esd {
 // longer belongs to this residual, or a step that cut the true residual by less than 10%)
 // and whether refinement goes on (stops when ||r|| <= tol ||b||, b = 0, or max_outer
 // steps are done).
+//
+// skip_done (a system of a pair): a system whose refinement has already stopped is left as it is.
 __global__ void __launch_bounds__(kBlock, 4) k_ref_residual(IterCtx<double> c, SliceSet set, double* r64,
                                                              const float* r32, RefineState* rs, State* st_in,
-                                                             unsigned long long cond) {
+                                                             unsigned long long cond, int skip_done) {
   __shared__ double red[red_size<3>()];
+  if (skip_done && rs->conv) return;
   double acc[3] = {0.0, 0.0, 0.0};
   const bool gap = st_in != nullptr;
   ESD_LOOP_SLICES(set) {
@@ -116,10 +119,15 @@ __global__ void __launch_bounds__(kBlock, 4) k_ref_residual(IterCtx<double> c, S
 
 // b32 = (float) r, x32 = 0; block 0 sets up the inner solve (fresh, or resumed) and opens
 // its loop. The inner tolerance is inner_tol relative to ||r||, but never tighter than half
-// of what the outer tolerance still asks for.
+// of what the outer tolerance still asks for. A system of a pair whose refinement has stopped
+// gets a stopped inner solve instead (the pair's inner kernels skip it).
 __global__ void __launch_bounds__(kBlock, 4) k_ref_prep(int n, const double* r64, float* b32, float* x32,
                                                          State* st_in, const RefineState* rs,
                                                          unsigned long long cond_in) {
+  if (rs->conv) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) st_in->conv = 1;
+    return;
+  }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     b32[i] = (float)r64[i];
     x32[i] = 0.0f;
@@ -145,14 +153,37 @@ __global__ void __launch_bounds__(kBlock, 4) k_ref_prep(int n, const double* r64
     st_in->maxit = rs->inner_maxit;
     st_in->lmax = rs->lmax;
     st_in->scal0 = fmax(rs->inner_tol2, 0.25 * rs->tol2bb / rs->rr);
-    cudaGraphSetConditional((cudaGraphConditionalHandle)cond_in, 1u);
+    if (cond_in) cudaGraphSetConditional((cudaGraphConditionalHandle)cond_in, 1u);
   }
 }
 
 void launch_ref_residual(const IterCtx<double>& c, double* r64, const float* r32, RefineState* rs, State* st_in,
-                         unsigned long long cond, cudaStream_t s) {
+                         unsigned long long cond, cudaStream_t s, int skip_done) {
   const SliceSet& all = c.A->all;
-  k_ref_residual<<<grid_for(k_ref_residual, all.total()), kBlock, 0, s>>>(c, all, r64, r32, rs, st_in, cond);
+  k_ref_residual<<<grid_for(k_ref_residual, all.total()), kBlock, 0, s>>>(c, all, r64, r32, rs, st_in, cond,
+                                                                         skip_done);
+  ESD_CUDA(cudaGetLastError());
+}
+
+// The loop of a pair of refinements goes on while either system has not stopped.
+__global__ void k_pair_cond(const RefineState* rs1, const RefineState* rs2, unsigned long long cond) {
+  cudaGraphSetConditional((cudaGraphConditionalHandle)cond, (rs1->conv && rs2->conv) ? 0u : 1u);
+}
+
+void launch_pair_cond(const RefineState* rs1, const RefineState* rs2, unsigned long long cond, cudaStream_t s) {
+  k_pair_cond<<<1, 1, 0, s>>>(rs1, rs2, cond);
+  ESD_CUDA(cudaGetLastError());
+}
+
+// The inner loops of a pair: the paired one runs while both inner runs go on (both = 1), a
+// single one while its system's does (st2 = NULL).
+__global__ void k_inner_cond(const State* st1, const State* st2, unsigned long long cond) {
+  const bool go = !st1->conv && (st2 == nullptr || !st2->conv);
+  cudaGraphSetConditional((cudaGraphConditionalHandle)cond, go ? 1u : 0u);
+}
+
+void launch_inner_cond(const State* st1, const State* st2, unsigned long long cond, cudaStream_t s) {
+  k_inner_cond<<<1, 1, 0, s>>>(st1, st2, cond);
   ESD_CUDA(cudaGetLastError());
 }
 

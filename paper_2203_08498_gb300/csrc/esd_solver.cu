@@ -3,6 +3,7 @@
 // Lanczos condition estimate and the C ABI of the solver.
 #include <algorithm>
 #include <cmath>
+#include <atomic>
 #include <cstring>
 #include <limits>
 #include <memory>
@@ -84,6 +85,13 @@ struct esd_solver {
   cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
   int exec_version[3] = {-1, -1, -1};
   bool exec_pw[3] = {false, false, false};
+  // the graph of a pair solve with another solver (esd_solve_pair), kept while neither
+  // solver's graphs are dropped (epoch: bumped whenever they are, as buffers may have moved)
+  unsigned long long uid = 0;
+  int epoch = 0;
+  cudaGraphExec_t pair_exec = nullptr;
+  unsigned long long pair_uid = 0;
+  int pair_epoch_self = -1, pair_epoch_other = -1;
   int last_iters = 0, last_status = 0, last_sample_m = 0, last_maxit = 0;
   double last_relres = 0.0, last_true = 0.0;
   AuxBuild aux;
@@ -91,6 +99,7 @@ struct esd_solver {
   ~esd_solver() {
     for (auto& e : exec)
       if (e) cudaGraphExecDestroy(e);
+    if (pair_exec) cudaGraphExecDestroy(pair_exec);
     if (cap) cudaStreamDestroy(cap);
     if (cap2) cudaStreamDestroy(cap2);
     if (cap3) cudaStreamDestroy(cap3);
@@ -337,6 +346,112 @@ struct esd_solver {
       exec[md] = nullptr;
       exec_version[md] = -1;
     }
+    if (pair_exec) cudaGraphExecDestroy(pair_exec);
+    pair_exec = nullptr;
+    ++epoch;
+  }
+
+  // The refinement loop of this solver's system and `o`'s, run together: FP64 residuals ->
+  // while (either has not stopped) { both inner runs prepared (a stopped one stays stopped)
+  // and started; while (both inner runs go on) { one PCG iteration of both, sharing the
+  // passes over the matrix }; while (the one left goes on) { its single iteration }; both
+  // corrected, FP64 residuals } -> x = 0 where b = 0.
+  void capture_refine_pair(cudaGraph_t g, esd_solver* o) {
+    esd_solver* sv[2] = {this, o};
+    cudaGraphConditionalHandle h_out, h_in, h_one[2];
+    ESD_CUDA(cudaGraphConditionalHandleCreate(&h_out, g, 1, cudaGraphCondAssignDefault));
+    IterCtx<double> c64[2];
+    IterCtx<float> c32[2];
+    RefineState* rs[2];
+    State* st[2];
+    for (int k = 0; k < 2; ++k) {
+      c64[k] = sv[k]->ctx(ESD_PLAIN);
+      c64[k].rowsum = A->rowsum64.as<double>();
+      c32[k] = sv[k]->ctx32(ESD_PLAIN);
+      c32[k].x_zero = 1;
+      c32[k].cond = 0;  // the paired loop is ended by the pair kernels
+      rs[k] = sv[k]->rstate.as<RefineState>();
+      st[k] = sv[k]->state_in.as<State>();
+    }
+    const int n = A->n;
+    auto inner_loop = [&](cudaGraphConditionalHandle h, auto&& body_fn) {
+      cudaGraph_t inner = add_while_node(cap2, h);
+      ESD_CUDA(cudaStreamBeginCaptureToGraph(cap3, inner, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+      try {
+        body_fn();
+      } catch (...) {
+        cudaGraph_t dummy;
+        cudaStreamEndCapture(cap3, &dummy);
+        throw;
+      }
+      ESD_CUDA(cudaStreamEndCapture(cap3, &inner));
+    };
+    ESD_CUDA(cudaStreamBeginCaptureToGraph(cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    try {
+      for (int k = 0; k < 2; ++k)
+        launch_ref_residual(c64[k], sv[k]->r64.as<double>(), sv[k]->r32.as<float>(), rs[k], nullptr, 0ull, cap, 1);
+      launch_pair_cond(rs[0], rs[1], (unsigned long long)h_out, cap);
+      cudaGraph_t body = add_while_node(cap, h_out);
+      ESD_CUDA(cudaGraphConditionalHandleCreate(&h_in, body, 0, 0));
+      for (int k = 0; k < 2; ++k) ESD_CUDA(cudaGraphConditionalHandleCreate(&h_one[k], body, 0, 0));
+      ESD_CUDA(cudaStreamBeginCaptureToGraph(cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+      try {
+        for (int k = 0; k < 2; ++k)
+          launch_ref_prep(n, sv[k]->r64.as<double>(), sv[k]->b32.as<float>(), sv[k]->x32.as<float>(), st[k], rs[k],
+                          0ull, cap2);
+        for (int k = 0; k < 2; ++k) launch_init<float>(c32[k], cap2);
+        launch_inner_cond(st[0], st[1], (unsigned long long)h_in, cap2);
+        inner_loop(h_in, [&] { launch_iteration_pair(c32[0], c32[1], (unsigned long long)h_in, cap3); });
+        for (int k = 0; k < 2; ++k) {
+          IterCtx<float> c1 = c32[k];
+          c1.cond = (unsigned long long)h_one[k];
+          launch_inner_cond(st[k], nullptr, c1.cond, cap2);
+          inner_loop(h_one[k], [&] { launch_iteration<float>(c1, cap3); });
+        }
+        for (int k = 0; k < 2; ++k) launch_finish<float>(c32[k], cap2);
+        for (int k = 0; k < 2; ++k)
+          launch_ref_residual(c64[k], sv[k]->r64.as<double>(), sv[k]->r32.as<float>(), rs[k], st[k], 0ull, cap2, 1);
+        launch_pair_cond(rs[0], rs[1], (unsigned long long)h_out, cap2);
+      } catch (...) {
+        cudaGraph_t dummy;
+        cudaStreamEndCapture(cap2, &dummy);
+        throw;
+      }
+      ESD_CUDA(cudaStreamEndCapture(cap2, &body));
+      for (int k = 0; k < 2; ++k) {
+        k_ref_final<<<max_grid_blocks(), kBlock, 0, cap>>>(n, sv[k]->vx.as<double>(), rs[k]);
+        ESD_CUDA(cudaGetLastError());
+      }
+    } catch (...) {
+      cudaGraph_t dummy;
+      cudaStreamEndCapture(cap, &dummy);
+      throw;
+    }
+    ESD_CUDA(cudaStreamEndCapture(cap, &g));
+  }
+
+  void build_pair_graph(esd_solver* o) {
+    if (pair_exec && pair_uid == o->uid && pair_epoch_self == epoch && pair_epoch_other == o->epoch) return;
+    if (pair_exec) {
+      cudaGraphExecDestroy(pair_exec);
+      pair_exec = nullptr;
+    }
+    cudaGraph_t g;
+    ESD_CUDA(cudaGraphCreate(&g, 0));
+    try {
+      capture_refine_pair(g, o);
+    } catch (...) {
+      cudaGraphDestroy(g);
+      throw;
+    }
+    cudaGraphExec_t e;
+    cudaError_t err = cudaGraphInstantiate(&e, g, 0);
+    cudaGraphDestroy(g);
+    ESD_CUDA(err);
+    pair_exec = e;
+    pair_uid = o->uid;
+    pair_epoch_self = epoch;
+    pair_epoch_other = o->epoch;
   }
 
   // FP32 slice-major copies of W and AW for the inner solves (padding lanes and columns 0)
@@ -378,10 +493,9 @@ static int smallest_lmax(int m, int maxit) {
   }
 
 // The refinement form of esd_solve (b and x already copied into vb / vx).
-static int solve_refine(esd_solver* S, double* x, double tol, int32_t maxit, int32_t sample_m, int32_t* iters,
-                        double* relres) {
-  cudaStream_t s = S->stream;
-  const int n = S->A->n;
+// The outer and refinement states of a refinement-form solve, set on the host and copied to
+// the device on stream s.
+static void refine_init(esd_solver* S, double tol, int32_t maxit, int32_t sample_m, cudaStream_t s) {
   State* h = S->hst;
   std::memset(h, 0, sizeof(State));
   h->scal0 = tol * tol;
@@ -395,11 +509,19 @@ static int solve_refine(esd_solver* S, double* x, double tol, int32_t maxit, int
   hr->inner_tol2 = S->prm.inner_tol * S->prm.inner_tol;
   hr->keep = S->prm.resume_direction ? 1 : 0;
   ESD_CUDA(cudaMemcpyAsync(S->rstate.get(), hr, sizeof(RefineState), cudaMemcpyHostToDevice, s));
-  ESD_CUDA(cudaGraphLaunch(S->exec[S->mode], s));
-  copy_out(S->vx.get(), x, sizeof(double) * n, s);
-  ESD_CUDA(cudaMemcpyAsync(hr, S->rstate.get(), sizeof(RefineState), cudaMemcpyDeviceToHost, s));
+}
+
+// After the graph: x to the caller, the refinement and inner states back to the host.
+static void refine_fetch(esd_solver* S, double* x, cudaStream_t s) {
+  copy_out(S->vx.get(), x, sizeof(double) * S->A->n, s);
+  ESD_CUDA(cudaMemcpyAsync(S->hrs, S->rstate.get(), sizeof(RefineState), cudaMemcpyDeviceToHost, s));
   ESD_CUDA(cudaMemcpyAsync(S->hst_in, S->state_in.get(), sizeof(State), cudaMemcpyDeviceToHost, s));
-  ESD_CUDA(cudaStreamSynchronize(s));
+}
+
+// The solve's outcome from the fetched states (after the stream has synchronised).
+static int refine_result(esd_solver* S, int32_t maxit, int32_t sample_m, int32_t* iters, double* relres,
+                         const char* which) {
+  const RefineState* hr = S->hrs;
   // coefficients of the whole resumed run, or of the last restarted inner solve
   S->last_iters = hr->outer > 0 ? S->hst_in->iter : 0;
   S->last_status = hr->status;
@@ -413,16 +535,27 @@ static int solve_refine(esd_solver* S, double* x, double tol, int32_t maxit, int
   if (iters) *iters = hr->inner_total;
   if (relres) *relres = S->last_relres;
   if (hr->status == ESD_ERR_MAXIT) {
-    set_last_error(hr->stalled >= 4 ? "refinement stalled: the FP64 residual stopped decreasing above the tolerance"
-                                    : "refinement did not reach the tolerance within max_outer steps or maxit");
+    set_last_error(std::string(which) +
+                   (hr->stalled >= 4 ? "refinement stalled: the FP64 residual stopped decreasing above the tolerance"
+                                     : "refinement did not reach the tolerance within max_outer steps or maxit"));
     return ESD_ERR_MAXIT;
   }
   if (hr->status == ESD_ERR_BREAKDOWN) {
-    set_last_error(hr->nonfinite ? "non-finite residual in the refinement"
-                                 : "inner CG breakdown in the refinement");
+    set_last_error(std::string(which) + (hr->nonfinite ? "non-finite residual in the refinement"
+                                                       : "inner CG breakdown in the refinement"));
     return ESD_ERR_BREAKDOWN;
   }
   return ESD_OK;
+}
+
+static int solve_refine(esd_solver* S, double* x, double tol, int32_t maxit, int32_t sample_m, int32_t* iters,
+                        double* relres) {
+  cudaStream_t s = S->stream;
+  refine_init(S, tol, maxit, sample_m, s);
+  ESD_CUDA(cudaGraphLaunch(S->exec[S->mode], s));
+  refine_fetch(S, x, s);
+  ESD_CUDA(cudaStreamSynchronize(s));
+  return refine_result(S, maxit, sample_m, iters, relres, "");
 }
 
 extern "C" {
@@ -462,6 +595,8 @@ int esd_solver_create(esd_matrix* A, const esd_params* params, esd_solver** out)
   S->A = A;
   S->prm = p;
   S->stream = A->stream;
+  static std::atomic<unsigned long long> next_uid{1};
+  S->uid = next_uid++;
   S->ld = A->vec_stride();
   const size_t vbytes = sizeof(double) * S->ld;
   for (DevBuf* b : {&S->vb, &S->vx, &S->vr, &S->vp, &S->vq, &S->vY}) {
@@ -574,6 +709,64 @@ int esd_solve(esd_solver* S, const double* b, double* x, double tol, int32_t max
     return ESD_ERR_BREAKDOWN;
   }
   return ESD_OK;
+  ESD_API_END
+}
+
+}  // extern "C"
+
+// What esd_solve_pair and esd_profile_pair_iterations ask of a pair (throws when it fails);
+// the FP32 copies of the matrix and its factor are brought up to date.
+static void check_pair(esd_solver* S1, esd_solver* S2) {
+  ESD_CHECK(S1 != S2, ESD_ERR_INVALID, "a pair needs two solvers");
+  ESD_CHECK(S1->A == S2->A && S1->P == S2->P, ESD_ERR_INVALID,
+            "the two solvers must share the matrix and the preconditioning matrix");
+  ESD_CHECK(S1->fp32 && S2->fp32, ESD_ERR_STATE, "the pair solve runs in the refinement form (ESD_FP32_REFINE)");
+  ESD_CHECK(S1->mode == ESD_PLAIN && S2->mode == ESD_PLAIN, ESD_ERR_STATE, "the pair solve runs plain PCG");
+  ESD_CHECK(S1->prm.precond == ESD_PRECOND_IC0 && S2->prm.precond == ESD_PRECOND_IC0, ESD_ERR_STATE,
+            "the pair solve runs with IC(0)");
+  ESD_CHECK(S1->PM()->factored, ESD_ERR_STATE,
+            "the IC(0) factor is missing or stale (the matrix values changed): call esd_factor_ic0");
+  ESD_CHECK(!S1->pw_on && !S2->pw_on, ESD_ERR_STATE, "the power method runs in FP64 solves");
+  S1->A->ensure_fp32();
+  if (S1->P) S1->P->ensure_fp32();
+  const std::string why = pair_unsupported(S1->ctx32(ESD_PLAIN), S2->ctx32(ESD_PLAIN));
+  ESD_CHECK(why.empty(), ESD_ERR_STATE, "pair solve: " + why);
+}
+
+extern "C" {
+
+int esd_solve_pair(esd_solver* S1, esd_solver* S2, const double* b1, double* x1, const double* b2, double* x2,
+                   double tol, int32_t maxit, int32_t* iters1, double* relres1, int32_t* iters2, double* relres2,
+                   int32_t* paired) {
+  ESD_API_BEGIN
+  ESD_CHECK(S1 && S2 && b1 && x1 && b2 && x2, ESD_ERR_INVALID, "NULL argument");
+  ESD_CHECK(tol > 0.0 && std::isfinite(tol), ESD_ERR_INVALID, "tol must be positive");
+  ESD_CHECK(maxit >= 1 && maxit <= S1->prm.maxit_cap && maxit <= S2->prm.maxit_cap, ESD_ERR_INVALID,
+            "maxit must be 1..maxit_cap of both solvers");
+  check_pair(S1, S2);
+  cudaStream_t s = S1->stream;  // one matrix, one stream
+  S1->build_pair_graph(S2);
+  const int n = S1->A->n;
+  copy_in(b1, S1->vb.get(), sizeof(double) * n, s);
+  copy_in(x1, S1->vx.get(), sizeof(double) * n, s);
+  copy_in(b2, S2->vb.get(), sizeof(double) * n, s);
+  copy_in(x2, S2->vx.get(), sizeof(double) * n, s);
+  refine_init(S1, tol, maxit, 0, s);
+  refine_init(S2, tol, maxit, 0, s);
+  ESD_CUDA(cudaMemsetAsync(&S1->state_in.as<State>()->paired, 0, sizeof(int), s));
+  ESD_CUDA(cudaGraphLaunch(S1->pair_exec, s));
+  refine_fetch(S1, x1, s);
+  refine_fetch(S2, x2, s);
+  ESD_CUDA(cudaStreamSynchronize(s));
+  if (paired) *paired = S1->hst_in->paired;
+  const int r1 = refine_result(S1, maxit, 0, iters1, relres1, "system 1: ");
+  const std::string e1 = esd_last_error();
+  const int r2 = refine_result(S2, maxit, 0, iters2, relres2, "system 2: ");
+  if (r1 != ESD_OK) {
+    set_last_error(e1);
+    return r1;
+  }
+  return r2;
   ESD_API_END
 }
 
@@ -934,6 +1127,62 @@ int esd_profile_iterations(esd_solver* S, const double* b, double* x, int32_t re
     }
   }
   copy_out(S->vx.get(), x, sizeof(double) * n, s);
+  ESD_CUDA(cudaStreamSynchronize(s));
+  const int k = (int)marks[0]->ev.size() - 1;
+  *count = k;
+  for (int j = 0; j < std::min(k, (int)cap); ++j) {
+    double tot = 0.0;
+    for (auto& mk : marks) {
+      float t = 0.f;
+      ESD_CUDA(cudaEventElapsedTime(&t, mk->ev[j], mk->ev[j + 1]));
+      tot += t;
+    }
+    ms[j] = tot / reps;
+    if (names) {
+      std::strncpy(names + 32 * j, marks[0]->names[j + 1].c_str(), 31);
+      names[32 * j + 31] = 0;
+    }
+  }
+  return ESD_OK;
+  ESD_API_END
+}
+
+int esd_profile_pair_iterations(esd_solver* S1, esd_solver* S2, const double* b1, double* x1, const double* b2,
+                                double* x2, int32_t reps, double* ms, char* names, int32_t cap, int32_t* count) {
+  ESD_API_BEGIN
+  ESD_CHECK(S1 && S2 && b1 && x1 && b2 && x2 && ms && count, ESD_ERR_INVALID, "NULL argument");
+  ESD_CHECK(reps >= 1 && reps < S1->prm.maxit_cap && reps < S2->prm.maxit_cap, ESD_ERR_INVALID,
+            "reps must be 1..maxit_cap-1 of both solvers");
+  check_pair(S1, S2);
+  cudaStream_t s = S1->stream;
+  const int n = S1->A->n;
+  esd_solver* sv[2] = {S1, S2};
+  const double* bs[2] = {b1, b2};
+  const double* xs[2] = {x1, x2};
+  IterCtx<float> c[2];
+  for (int k = 0; k < 2; ++k) {
+    esd_solver* S = sv[k];
+    copy_in(bs[k], S->vb.get(), sizeof(double) * n, s);
+    copy_in(xs[k], S->vx.get(), sizeof(double) * n, s);
+    State* h = S->hst;
+    std::memset(h, 0, sizeof(State));
+    h->scal0 = 0.0;  // tolerance 0: the iterations run for reps steps
+    h->maxit = reps + 1;
+    h->h = 1;
+    h->pend_slot = -1;
+    ESD_CUDA(cudaMemcpyAsync(S->state_in.get(), h, sizeof(State), cudaMemcpyHostToDevice, s));
+    convert_d2f(n, S->vb.as<double>(), S->b32.as<float>(), s);
+    convert_d2f(n, S->vx.as<double>(), S->x32.as<float>(), s);
+    c[k] = S->ctx32(ESD_PLAIN);
+    launch_init<float>(c[k], s);
+  }
+  std::vector<std::unique_ptr<KernelMarks>> marks;
+  for (int r = 0; r < reps; ++r) {
+    marks.emplace_back(new KernelMarks());
+    launch_iteration_pair(c[0], c[1], 0ull, s, marks.back().get());
+  }
+  copy_out(S1->vx.get(), x1, sizeof(double) * n, s);
+  copy_out(S2->vx.get(), x2, sizeof(double) * n, s);
   ESD_CUDA(cudaStreamSynchronize(s));
   const int k = (int)marks[0]->ev.size() - 1;
   *count = k;

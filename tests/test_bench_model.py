@@ -81,3 +81,23 @@ def test_gamma_model_is_the_papers_ratio():
 def test_host_info_fields():
     h = bench.host_info()
     assert h["nproc"] >= 1 and isinstance(h["cpu_model"], str) and h["machine"]
+
+
+def test_pair_models_share_the_matrix_once():
+    """The paired launches: the matrix (and s = A 1, 1/l_ii) once, each system's vectors."""
+    n, nnz = 2_097_152, 14_581_760
+    p = _problem(n, nnz)
+    n0 = n // 8
+    lv = (np.array([n0]), None, None)
+    a32 = types.SimpleNamespace(precision="fp32", m=16)
+    slices, slots_a = n // 32, 7 * n
+    lay = {"column_free": [True, True, True], "slot_entries": [slots_a, 3 * n, 3 * n], "slices": slices}
+    by, fm = bench.kernel_model("spmv_pq", p, a32, ESD.PLAIN, ESD, lv, lay, pair=True)
+    # slots and bases, s = A 1 once; p read, q written and the 4 n term per system
+    assert by == 4 * slots_a + 32 * slices + 4 * n + 2 * 12 * n
+    assert fm == 2 * (nnz + n)
+    by, fm = bench.kernel_model("update", p, a32, ESD.PLAIN, ESD, lv, lay, pair=True)
+    # per system: x read and written in FP64, p, q, r read, r written, y written on level 0;
+    # 1/l_ii of level 0 once
+    assert by == 2 * (16 * n + 16 * n + 4 * n0) + 4 * n0
+    assert fm == 2 * (3 * n + 2 * n0)

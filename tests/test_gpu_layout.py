@@ -10,8 +10,6 @@ keeps the pairs. Both must run the oracle's iteration: the FP32 CG coefficients 
 inner solve agree with the oracle's FP64 run to FP32 accuracy, the count within max(2, 5%),
 and the refined solution meets its tolerance.
 """
-import dataclasses
-
 import numpy as np
 import pytest
 
@@ -27,23 +25,10 @@ if not torch.cuda.is_available():
 import paper_2203_08498_gb300 as esd  # noqa: E402
 
 
-def shuffle_within_colours(p, seed):
-    """The same operator with the rows of every colour in a seeded random order."""
-    rng = np.random.default_rng(seed)
-    cp = np.asarray(p.colour_ptr)
-    q = np.concatenate([cp[c] + rng.permutation(cp[c + 1] - cp[c]) for c in range(len(cp) - 1)])  # new -> old
-    A = p.scipy()[q][:, q].tocsr()
-    A.sort_indices()
-    out = dataclasses.replace(p, rowptr=A.indptr.astype(np.int32), colind=A.indices.astype(np.int32),
-                              val=A.data.astype(np.float64), perm=np.asarray(p.perm)[q], name=p.name + "_shuffled")
-    out.source = np.ascontiguousarray(p.source[q])
-    return out
-
-
 @pytest.fixture(scope="module")
 def problems():
     p = wl.small_3d(24, seed=12, count=3, rmin=2, rmax=3, value=1e4)
-    return {"natural": (p, True), "shuffled": (shuffle_within_colours(p, 7), False)}
+    return {"natural": (p, True), "shuffled": (wl.shuffle_within_colours(p, 7), False)}
 
 
 @pytest.mark.parametrize("which", ["natural", "shuffled"])

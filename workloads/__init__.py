@@ -31,7 +31,7 @@ __all__ = [
     "gaussian_source", "smooth_gaussian_field", "config_c1", "config_c2", "config_c4",
     "small_3d", "random_spd_dense", "laplacian_1d", "ic0_breakdown_spd", "laplacian_2d", "csr_of_dense",
     "random_rhs", "SEED_BASE", "reorder", "wavefront_colours", "block_ids", "block_wavefront_colours",
-    "block_diagonal_part",
+    "block_diagonal_part", "shuffle_within_colours",
 ]
 
 SEED_BASE = 20220316
@@ -408,6 +408,21 @@ def small_3d(N: int, seed: int, count: int = 2, rmin: float = 1.5, rmax: float =
     coef = sphere_inclusions(N, count, rmin, rmax, value, rng) if count else np.ones((N, N, N))
     p = fv_diffusion(coef, 1.0 / N, dt, name=f"fv7_{N}cube")
     return _finish(p, gaussian_source((N, N, N)))
+
+
+def shuffle_within_colours(p: Problem, seed: int) -> Problem:
+    """The same operator with the rows of every colour in a seeded random order (still a
+    valid colouring: rows of one colour are uncoupled). Scatters the neighbours of a 32-row
+    slice, so the FP32 copy keeps (value, column) pairs instead of per-slice column bases."""
+    rng = np.random.default_rng(seed)
+    cp = np.asarray(p.colour_ptr)
+    q = np.concatenate([cp[c] + rng.permutation(cp[c + 1] - cp[c]) for c in range(len(cp) - 1)])  # new -> old
+    A = p.scipy()[q][:, q].tocsr()
+    A.sort_indices()
+    out = dataclasses.replace(p, rowptr=A.indptr.astype(np.int32), colind=A.indices.astype(np.int32),
+                              val=A.data.astype(np.float64), perm=np.asarray(p.perm)[q], name=p.name + "_shuffled")
+    out.source = np.ascontiguousarray(p.source[q])
+    return out
 
 
 def random_rhs(n: int, seed: int) -> np.ndarray:
