@@ -253,7 +253,7 @@ def pair_launch_count(info, its, outer, paired):
     start = 1 + 1 + nf + nb
     end = 1
     o = max(outer)
-    return 5 + o * (2 * (start + end + 2) + 4) + body * (sum(its) - paired)
+    return 5 + o * (2 * (start + end + 2) + 6) + body * (sum(its) - paired)
 
 
 def gpu_arm(args):

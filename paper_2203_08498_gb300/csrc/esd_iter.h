@@ -25,6 +25,9 @@ struct IterCtx {
   T* p = nullptr;   // search direction
   T* q = nullptr;   // A p
   T* Y = nullptr;   // forward then backward substitution values (y, then L^-T y)
+  // the paired kernels of two FP32 systems: (p_1, p_2) and (y_1, y_2) side by side
+  float2* p12 = nullptr;
+  float2* Y12 = nullptr;
   const T* W = nullptr;   // n x M column-major, stride ld
   const T* AW = nullptr;  // n x M column-major, stride ld
   size_t ld = 0;          // vector stride in elements
@@ -106,5 +109,7 @@ int pad_m(int m);  // the compiled column count >= m
 std::string pair_unsupported(const IterCtx<float>& c1, const IterCtx<float>& c2);  // "" when supported
 void launch_iteration_pair(const IterCtx<float>& c1, const IterCtx<float>& c2, unsigned long long cond,
                            cudaStream_t s, KernelMarks* marks = nullptr);
+// c1.p12 = (c1.p, c2.p) before the paired loop (pack = true), and back after it
+void launch_pair_pack(const IterCtx<float>& c1, const IterCtx<float>& c2, bool pack, cudaStream_t s);
 
 }  // namespace esd

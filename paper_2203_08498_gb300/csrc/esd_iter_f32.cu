@@ -17,6 +17,7 @@ std::string pair_unsupported(const IterCtx<float>& c1, const IterCtx<float>& c2)
   if (c1.A->A.wmax > kStreamWmax || !stream_sweeps<float>(P)) return "matrix rows wider than the staged kernels take";
   if (!P->upd_ok || P->fwd_sets.empty() || P->fwd_sets.size() > (size_t)kPairMaxLevels)
     return "colour levels the pair solve does not take";
+  if (!c1.p12 || !c1.Y12) return "no side-by-side vectors for the pair";
   return "";
 }
 
@@ -31,7 +32,7 @@ void launch_iteration_pair(const IterCtx<float>& c1, const IterCtx<float>& c2, u
   {
     const bool aff = A->A.affine;
     const int w = pair_width(aff ? A->A.awmax : A->A.wmax);
-    const StreamPlan pl = pair_plan(A->all, SliceSet{}, kPairChunk, aff ? A->A.awmax : A->A.wmax, aff ? 4 : 8, 3, 0,
+    const StreamPlan pl = pair_plan(A->all, SliceSet{}, kPairChunk, aff ? A->A.awmax : A->A.wmax, aff ? 4 : 8, 1, 1,
                                     aff ? kHdrAffine : kHdrPlain, &ok);
     ESD_CHECK(ok && w > 0, ESD_ERR_INTERNAL, "pair SpMV plan");
     ESD_DISPATCH_W(w, {
@@ -46,7 +47,7 @@ void launch_iteration_pair(const IterCtx<float>& c1, const IterCtx<float>& c2, u
     if (marks) marks->mark(s, "spmv_pq");
   }
   {
-    const StreamPlan pl = pair_plan(P->upd_sets[0], P->upd_sets[1], kPairUpdateChunk, 0, 0, 7, 2, kHdrPlain, &ok);
+    const StreamPlan pl = pair_plan(P->upd_sets[0], P->upd_sets[1], kPairUpdateChunk, 0, 0, 5, 3, kHdrPlain, &ok);
     ESD_CHECK(ok, ESD_ERR_INTERNAL, "pair update plan");
     auto k = k_update_pair<ESD_PRECOND_IC0>;
     launch_stream(k, stream_blocks(k, pl), pl, s, c1, c2, pl, 0, cond);
@@ -76,7 +77,7 @@ void launch_iteration_pair(const IterCtx<float>& c1, const IterCtx<float>& c2, u
     const SliceSet& el = l < P->bwd0_sets.size() ? P->bwd0_sets[l] : none;
     const bool has = l < P->bwd_sets.size();
     const int wmax = has ? (aff ? P->bwd_awmax[l] : P->bwd_wmax[l]) : 0;
-    const StreamPlan pl = pair_plan(sw, el, kPairChunk, wmax, eb, 5, 0, hdr, &ok);
+    const StreamPlan pl = pair_plan(sw, el, kPairChunk, wmax, eb, 1, 2, hdr, &ok);
     ESD_CHECK(ok, ESD_ERR_INTERNAL, "pair backward plan");
     ESD_DISPATCH_W(pair_width(wmax), {
       auto k = aff ? k_bwd_pair<WW, true> : k_bwd_pair<WW, false>;
@@ -84,6 +85,32 @@ void launch_iteration_pair(const IterCtx<float>& c1, const IterCtx<float>& c2, u
     });
     if (marks) marks->mark(s, ("bwd_" + std::to_string(l + 1)).c_str());
   }
+}
+
+// (p_1, p_2) side by side from the two systems' p before the paired loop, and back after it.
+__global__ void k_pair_pack(int n, const float* __restrict__ p1, const float* __restrict__ p2,
+                            float2* __restrict__ p12) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    p12[i] = make_float2(p1[i], p2[i]);
+}
+
+__global__ void k_pair_unpack(int n, const float2* __restrict__ p12, float* __restrict__ p1,
+                              float* __restrict__ p2) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float2 v = p12[i];
+    p1[i] = v.x;
+    p2[i] = v.y;
+  }
+}
+
+void launch_pair_pack(const IterCtx<float>& c1, const IterCtx<float>& c2, bool pack, cudaStream_t s) {
+  const int n = c1.A->n;
+  const int G = std::min(max_grid_blocks(), (n + kBlock - 1) / kBlock);
+  if (pack)
+    k_pair_pack<<<G, kBlock, 0, s>>>(n, c1.p, c2.p, c1.p12);
+  else
+    k_pair_unpack<<<G, kBlock, 0, s>>>(n, c1.p12, c1.p, c2.p);
+  ESD_CUDA(cudaGetLastError());
 }
 
 }  // namespace esd

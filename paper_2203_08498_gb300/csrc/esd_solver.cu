@@ -108,6 +108,25 @@ struct esd_solver {
     if (hrs) cudaFreeHost(hrs);
   }
 
+  // (p_1, p_2) and (y_1, y_2) side by side for the paired kernels of the pairs this solver
+  // leads, with kGuard zero pairs on each side (as p32 and Y32); allocated at its first pair
+  DevBuf pair_p12, pair_Y12;
+  void ensure_pair_vectors() {
+    if (pair_p12.get()) return;
+    const size_t bytes = sizeof(float2) * (ld + 2 * kGuard);
+    for (DevBuf* b : {&pair_p12, &pair_Y12}) {
+      b->alloc(bytes);
+      ESD_CUDA(cudaMemsetAsync(b->get(), 0, bytes, stream));
+    }
+  }
+  // this solver's plain FP32 context as a system of the pair that `lead` leads
+  IterCtx<float> pair_ctx32(const esd_solver* lead) const {
+    IterCtx<float> c = ctx32(ESD_PLAIN);
+    c.p12 = lead->pair_p12.as<float2>() ? lead->pair_p12.as<float2>() + kGuard : nullptr;
+    c.Y12 = lead->pair_Y12.as<float2>() ? lead->pair_Y12.as<float2>() + kGuard : nullptr;
+    return c;
+  }
+
   IterCtx<float> ctx32(int md) const {
     IterCtx<float> c;
     c.A = A;
@@ -367,7 +386,7 @@ struct esd_solver {
     for (int k = 0; k < 2; ++k) {
       c64[k] = sv[k]->ctx(ESD_PLAIN);
       c64[k].rowsum = A->rowsum64.as<double>();
-      c32[k] = sv[k]->ctx32(ESD_PLAIN);
+      c32[k] = sv[k]->pair_ctx32(this);
       c32[k].x_zero = 1;
       c32[k].cond = 0;  // the paired loop is ended by the pair kernels
       rs[k] = sv[k]->rstate.as<RefineState>();
@@ -400,8 +419,10 @@ struct esd_solver {
           launch_ref_prep(n, sv[k]->r64.as<double>(), sv[k]->b32.as<float>(), sv[k]->x32.as<float>(), st[k], rs[k],
                           0ull, cap2);
         for (int k = 0; k < 2; ++k) launch_init<float>(c32[k], cap2);
+        launch_pair_pack(c32[0], c32[1], true, cap2);
         launch_inner_cond(st[0], st[1], (unsigned long long)h_in, cap2);
         inner_loop(h_in, [&] { launch_iteration_pair(c32[0], c32[1], (unsigned long long)h_in, cap3); });
+        launch_pair_pack(c32[0], c32[1], false, cap2);
         for (int k = 0; k < 2; ++k) {
           IterCtx<float> c1 = c32[k];
           c1.cond = (unsigned long long)h_one[k];
@@ -729,7 +750,8 @@ static void check_pair(esd_solver* S1, esd_solver* S2) {
   ESD_CHECK(!S1->pw_on && !S2->pw_on, ESD_ERR_STATE, "the power method runs in FP64 solves");
   S1->A->ensure_fp32();
   if (S1->P) S1->P->ensure_fp32();
-  const std::string why = pair_unsupported(S1->ctx32(ESD_PLAIN), S2->ctx32(ESD_PLAIN));
+  S1->ensure_pair_vectors();
+  const std::string why = pair_unsupported(S1->pair_ctx32(S1), S2->pair_ctx32(S1));
   ESD_CHECK(why.empty(), ESD_ERR_STATE, "pair solve: " + why);
 }
 
@@ -1173,9 +1195,10 @@ int esd_profile_pair_iterations(esd_solver* S1, esd_solver* S2, const double* b1
     ESD_CUDA(cudaMemcpyAsync(S->state_in.get(), h, sizeof(State), cudaMemcpyHostToDevice, s));
     convert_d2f(n, S->vb.as<double>(), S->b32.as<float>(), s);
     convert_d2f(n, S->vx.as<double>(), S->x32.as<float>(), s);
-    c[k] = S->ctx32(ESD_PLAIN);
+    c[k] = S->pair_ctx32(S1);
     launch_init<float>(c[k], s);
   }
+  launch_pair_pack(c[0], c[1], true, s);
   std::vector<std::unique_ptr<KernelMarks>> marks;
   for (int r = 0; r < reps; ++r) {
     marks.emplace_back(new KernelMarks());

@@ -9,6 +9,11 @@
 // matrix. Two systems that need only the same earlier solution (the adjoint of system t and
 // the forward solve of system t + 1 of a time-stepping sequence both need x_t) can share both.
 //
+// The vectors the products gather, p and y, are kept for the paired loop side by side, (p_1,
+// p_2) and (y_1, y_2) in one float2 array each (IterCtx::p12, Y12), so that one 8-byte gather
+// serves both systems: k_pair_pack forms p12 from the two solvers' p before the loop and
+// k_pair_unpack gives each its p back after it; y lives only within an iteration.
+//
 // Each row's products are taken in the same order as in the single kernels, so q, y and z
 // are those of the single kernels for the same p, r and y; the dot products' per-thread
 // partial sums cover other rows (the pair launches take 16 slices per chunk for the products
@@ -58,13 +63,14 @@ inline int pair_width(int wmax) {
   }
 
 // One row of the warp's slice for both systems: acc_s += sum_e val_e (v_s[col_e] - vi_s),
-// the entries in stored order (as staged_rows), every gather of both systems issued before
-// the first FMA.
+// the entries in stored order (as staged_rows); v12 holds (v_1, v_2) side by side, so one
+// 8-byte gather serves both systems. Every gather is issued before the first FMA.
 template <int W, bool DIFF, bool AFF, int NV>
 __device__ __forceinline__ void staged_rows_pair(const StageView<NV>& sv, const int4& md, int ls, int lane,
-                                                 const float* __restrict__ v1, const float* __restrict__ v2,
-                                                 float vi1, float vi2, float& acc1, float& acc2, bool& bad) {
-  float val[W], a[W], b[W];
+                                                 const float2* __restrict__ v12, float vi1, float vi2,
+                                                 float& acc1, float& acc2, bool& bad) {
+  float val[W];
+  float2 t[W];
   bad |= md.y > W;
   const int off = (md.x - sv.x0) + lane;
   const int* sb = sv.sbase + ls * kAffineSlots;
@@ -82,14 +88,13 @@ __device__ __forceinline__ void staged_rows_pair(const StageView<NV>& sv, const 
         col = (int)pr.y;
       }
     }
-    a[e] = e < md.y ? v1[col] : 0.f;
-    b[e] = e < md.y ? v2[col] : 0.f;
+    t[e] = e < md.y ? v12[col] : make_float2(0.f, 0.f);
   }
 #pragma unroll
   for (int e = 0; e < W; ++e)
     if (e < md.y) {
-      acc1 = fmaf(val[e], DIFF ? a[e] - vi1 : a[e], acc1);
-      acc2 = fmaf(val[e], DIFF ? b[e] - vi2 : b[e], acc2);
+      acc1 = fmaf(val[e], DIFF ? t[e].x - vi1 : t[e].x, acc1);
+      acc2 = fmaf(val[e], DIFF ? t[e].y - vi2 : t[e].y, acc2);
     }
 }
 
@@ -117,7 +122,7 @@ __device__ __forceinline__ bool pair_enter(State* st1, State* st2, unsigned long
 }
 
 // q_s = A p_s (difference form) and (p_s, q_s) for both systems; the last block sets each
-// running system's alpha. Staged vectors: s = A 1, p_1, p_2.
+// running system's alpha. Staged vectors: s = A 1, (p_1, p_2).
 template <int W, bool AFF>
 __global__ void __launch_bounds__(kStreamThreads, 2)
     k_spmv_pq_pair(IterCtx<float> c1, IterCtx<float> c2, StreamPlan pl, unsigned long long cond) {
@@ -127,7 +132,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
   if (!pair_enter(c1.st, c2.st, full, empty, s_act, true, cond)) return;
   const int warp = threadIdx.x >> 5, lane = lane_id();
   const EntSet es = stream_entries<AFF>(c1.Av);
-  const VecSet<3> vs{{c1.rowsum, c1.p, c2.p}, {4, 4, 4}, 6u, 0u};
+  const VecSet<2> vs{{c1.rowsum, c1.p12}, {4, 8}, 2u, 0u};
   const bool act1 = s_act[0], act2 = s_act[1];
   float acc[2] = {0.f, 0.f}, cmp[2] = {0.f, 0.f};
   if (warp == kStreamWarps) {
@@ -137,16 +142,16 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
     }
   } else {
     bool bad = false;
-    const bool ok = stream_consume(pl, es, vs, full, empty, [&](const ChunkPos& cp, const StageView<3>& sv) {
+    const bool ok = stream_consume(pl, es, vs, full, empty, [&](const ChunkPos& cp, const StageView<2>& sv) {
       if (warp >= cp.s1 - cp.s0) return;
       const int4 md = sv.meta()[warp];
       const bool valid = lane < md.w;
       const int i = md.z + lane;
       const float si = valid ? sv.template vec<float>(0, i) : 0.f;
-      const float p1 = valid ? sv.template vec<float>(1, i) : 0.f;
-      const float p2 = valid ? sv.template vec<float>(2, i) : 0.f;
+      const float2 pp = valid ? sv.template vec<float2>(1, i) : make_float2(0.f, 0.f);
+      const float p1 = pp.x, p2 = pp.y;
       float q1 = fmaf(si, p1, 0.f), q2 = fmaf(si, p2, 0.f);
-      staged_rows_pair<W, true, AFF>(sv, md, warp, lane, c1.p, c2.p, p1, p2, q1, q2, bad);
+      staged_rows_pair<W, true, AFF>(sv, md, warp, lane, c1.p12, p1, p2, q1, q2, bad);
       if (valid) {
         if (act1) {
           c1.q[i] = q1;
@@ -191,7 +196,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
 
 // The plain update of both systems (as k_update_stream): x_s += alpha_s p_s in FP64,
 // r_s -= alpha_s q_s, ||r_s||^2 and forward level 0. Part 0: forward-level-0 rows (1/l_ii
-// staged), part 1 the others. Staged vectors: x_1, x_2, p_1, q_1, r_1, p_2, q_2, r_2, 1/l_ii.
+// staged), part 1 the others. Staged vectors: x_1, x_2, (p_1, p_2), q_1, r_1, q_2, r_2, 1/l_ii.
 template <int PRE>
 __global__ void __launch_bounds__(kStreamThreads, 2)
     k_update_pair(IterCtx<float> c1, IterCtx<float> c2, StreamPlan pl, int finalize, unsigned long long cond) {
@@ -204,8 +209,8 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
   const float al1 = (float)c1.st->alpha, al2 = (float)c2.st->alpha;
   const double ad1 = c1.st->alpha, ad2 = c2.st->alpha;
   const EntSet es{{nullptr, nullptr}, {0, 0}, 0};
-  const VecSet<9> vs{{c1.x64, c2.x64, c1.p, c1.q, c1.r, c2.p, c2.q, c2.r, c1.inv_d}, {8, 8, 4, 4, 4, 4, 4, 4, 4}, 0u,
-                     255u};
+  const VecSet<8> vs{{c1.x64, c2.x64, c1.p12, c1.q, c1.r, c2.q, c2.r, c1.inv_d}, {8, 8, 8, 4, 4, 4, 4, 4}, 0u,
+                     127u};
   float acc[4] = {0.f, 0.f, 0.f, 0.f}, cmp[4] = {0.f, 0.f, 0.f, 0.f};
   if (warp == kStreamWarps) {
     if (lane == 0 && !stream_produce(pl, c1.Av.meta, es, vs, full, empty)) {
@@ -214,38 +219,41 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
     }
   } else {
     const unsigned bwd0 = pl.set[0].bwd0;
-    const bool ok = stream_consume(pl, es, vs, full, empty, [&](const ChunkPos& cp, const StageView<9>& sv) {
+    const bool ok = stream_consume(pl, es, vs, full, empty, [&](const ChunkPos& cp, const StageView<8>& sv) {
       const bool lev0 = PRE == ESD_PRECOND_IC0 && cp.part == 0;
       const bool to_z = lev0 && ((bwd0 >> cp.range) & 1u);
       for (int ls = warp; ls < cp.s1 - cp.s0; ls += kStreamWarps) {
         const int4 md = sv.meta()[ls];
         if (lane >= md.w) continue;
         const int i = md.z + lane;
-        const float d = lev0 ? sv.template vec<float>(8, i) : 0.f;
+        const float d = lev0 ? sv.template vec<float>(7, i) : 0.f;
+        const float2 pp = sv.template vec<float2>(2, i);
+        float2 y = make_float2(0.f, 0.f);  // a stopped system's y is not used
         if (act1) {
           const double xi = sv.template vec<double>(0, i);
-          c1.x64[i] = fma(ad1, (double)sv.template vec<float>(2, i), xi);
+          c1.x64[i] = fma(ad1, (double)pp.x, xi);
           const float ri = fmaf(-al1, sv.template vec<float>(3, i), sv.template vec<float>(4, i));
           c1.r[i] = ri;
           kahan_add(acc[0], cmp[0], __fmul_rn(ri, ri));
           if (lev0) {
             const float yv = ri * d;
             kahan_add(acc[1], cmp[1], __fmul_rn(yv, yv));
-            c1.Y[i] = to_z ? yv * d : yv;
+            y.x = to_z ? yv * d : yv;
           }
         }
         if (act2) {
           const double xi = sv.template vec<double>(1, i);
-          c2.x64[i] = fma(ad2, (double)sv.template vec<float>(5, i), xi);
-          const float ri = fmaf(-al2, sv.template vec<float>(6, i), sv.template vec<float>(7, i));
+          c2.x64[i] = fma(ad2, (double)pp.y, xi);
+          const float ri = fmaf(-al2, sv.template vec<float>(5, i), sv.template vec<float>(6, i));
           c2.r[i] = ri;
           kahan_add(acc[2], cmp[2], __fmul_rn(ri, ri));
           if (lev0) {
             const float yv = ri * d;
             kahan_add(acc[3], cmp[3], __fmul_rn(yv, yv));
-            c2.Y[i] = to_z ? yv * d : yv;
+            y.y = to_z ? yv * d : yv;
           }
         }
+        if (lev0) c1.Y12[i] = y;
       }
     });
     if (!ok) {
@@ -266,6 +274,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
 
 // One forward colour level of both systems (as k_fwd_stream), each system's rho sums in its
 // own slots; the last launch sets each running system's beta. Staged vectors: r_1, r_2, 1/l_ii.
+// y goes to (y_1, y_2) side by side (a stopped system's half is not used).
 // Grids of the forward launches before the last one of a sweep (whose slots it adds up).
 constexpr int kPairMaxLevels = 16;
 struct PairGrids {
@@ -302,19 +311,13 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
       const float d = valid ? sv.template vec<float>(2, i) : 0.f;
       float y1 = valid ? sv.template vec<float>(0, i) : 0.f;
       float y2 = valid ? sv.template vec<float>(1, i) : 0.f;
-      staged_rows_pair<W, false, AFF>(sv, md, warp, lane, c1.Y, c2.Y, 0.f, 0.f, y1, y2, bad);
+      staged_rows_pair<W, false, AFF>(sv, md, warp, lane, c1.Y12, 0.f, 0.f, y1, y2, bad);
       const bool to_z = (bwd0 >> cp.range) & 1u;
       if (valid) {
-        if (act1) {
-          const float yv = y1 * d;
-          kahan_add(acc[0], cmp[0], __fmul_rn(yv, yv));
-          c1.Y[i] = to_z ? yv * d : yv;
-        }
-        if (act2) {
-          const float yv = y2 * d;
-          kahan_add(acc[1], cmp[1], __fmul_rn(yv, yv));
-          c2.Y[i] = to_z ? yv * d : yv;
-        }
+        const float yv1 = y1 * d, yv2 = y2 * d;
+        if (act1) kahan_add(acc[0], cmp[0], __fmul_rn(yv1, yv1));
+        if (act2) kahan_add(acc[1], cmp[1], __fmul_rn(yv2, yv2));
+        c1.Y12[i] = to_z ? make_float2(yv1 * d, yv2 * d) : make_float2(yv1, yv2);
       }
     });
     if (!ok || bad) {
@@ -357,8 +360,8 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
 }
 
 // One backward colour level of both systems (as k_bwd_stream): z_s, then p_s = z_s +
-// beta_s p_s. Part-1 chunks: direction update only. Staged vectors: y_1, y_2, 1/l_ii, p_1,
-// p_2 (part 1: y_1, y_2, p_1, p_2).
+// beta_s p_s. Part-1 chunks: direction update only. Staged vectors: (y_1, y_2), 1/l_ii,
+// (p_1, p_2) (part 1: (y_1, y_2), (p_1, p_2)). A stopped system's p is written back unchanged.
 template <int W, bool AFF>
 __global__ void __launch_bounds__(kStreamThreads, 2)
     k_bwd_pair(IterCtx<float> c1, IterCtx<float> c2, StreamPlan pl, unsigned long long cond) {
@@ -370,7 +373,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
   const float be1 = (float)c1.st->beta, be2 = (float)c2.st->beta;
   const bool first1 = c1.st->iter == 0 || c1.st->fresh_dir, first2 = c2.st->iter == 0 || c2.st->fresh_dir;
   const EntSet es = stream_entries<AFF>(c1.Uv);
-  const VecSet<5> vs{{c1.Y, c2.Y, c1.inv_d, c1.p, c2.p}, {4, 4, 4, 4, 4}, 0u, 27u};
+  const VecSet<3> vs{{c1.Y12, c1.inv_d, c1.p12}, {8, 4, 8}, 0u, 5u};
   if (warp == kStreamWarps) {
     if (lane == 0 && !stream_produce(pl, stream_metas<AFF>(c1.Uv), es, vs, full, empty)) {
       stream_fail(c1.st, cond);
@@ -378,30 +381,24 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
     }
   } else {
     bool bad = false;
-    const bool ok = stream_consume(pl, es, vs, full, empty, [&](const ChunkPos& cp, const StageView<5>& sv) {
+    const bool ok = stream_consume(pl, es, vs, full, empty, [&](const ChunkPos& cp, const StageView<3>& sv) {
       if (warp >= cp.s1 - cp.s0) return;
       const bool sweep = cp.part == 0;
       int4 md = sv.meta()[warp];
       if (!sweep) md.y = 0;  // rows whose z_i the forward sweep stored
       const bool valid = lane < md.w;
       const int i = md.z + lane;
-      float z1 = valid ? sv.template vec<float>(0, i) : 0.f;
-      float z2 = valid ? sv.template vec<float>(1, i) : 0.f;
-      const float d = (valid && sweep) ? sv.template vec<float>(2, i) : 1.f;
-      const float po1 = (valid && !first1) ? sv.template vec<float>(3, i) : 0.f;
-      const float po2 = (valid && !first2) ? sv.template vec<float>(4, i) : 0.f;
-      if (sweep) staged_rows_pair<W, false, AFF>(sv, md, warp, lane, c1.Y, c2.Y, 0.f, 0.f, z1, z2, bad);
+      const float2 yy = valid ? sv.template vec<float2>(0, i) : make_float2(0.f, 0.f);
+      float z1 = yy.x, z2 = yy.y;
+      const float d = (valid && sweep) ? sv.template vec<float>(1, i) : 1.f;
+      const float2 po = valid ? sv.template vec<float2>(2, i) : make_float2(0.f, 0.f);
+      if (sweep) staged_rows_pair<W, false, AFF>(sv, md, warp, lane, c1.Y12, 0.f, 0.f, z1, z2, bad);
       if (valid) {
-        if (act1) {
-          const float zi = sweep ? z1 * d : z1;
-          if (sweep) c1.Y[i] = zi;
-          c1.p[i] = first1 ? zi : fmaf(be1, po1, zi);
-        }
-        if (act2) {
-          const float zi = sweep ? z2 * d : z2;
-          if (sweep) c2.Y[i] = zi;
-          c2.p[i] = first2 ? zi : fmaf(be2, po2, zi);
-        }
+        const float zi1 = sweep ? z1 * d : z1, zi2 = sweep ? z2 * d : z2;
+        if (sweep) c1.Y12[i] = make_float2(zi1, zi2);
+        const float pn1 = act1 ? (first1 ? zi1 : fmaf(be1, po.x, zi1)) : po.x;
+        const float pn2 = act2 ? (first2 ? zi2 : fmaf(be2, po.y, zi2)) : po.y;
+        c1.p12[i] = make_float2(pn1, pn2);
       }
     });
     if (!ok || bad) {
