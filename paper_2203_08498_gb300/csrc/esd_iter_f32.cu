@@ -32,8 +32,8 @@ void launch_iteration_pair(const IterCtx<float>& c1, const IterCtx<float>& c2, u
   {
     const bool aff = A->A.affine;
     const int w = pair_width(aff ? A->A.awmax : A->A.wmax);
-    const StreamPlan pl = pair_plan(A->all, SliceSet{}, kPairChunk, aff ? A->A.awmax : A->A.wmax, aff ? 4 : 8, 1, 1,
-                                    aff ? kHdrAffine : kHdrPlain, &ok);
+    const int wmax = aff ? A->A.awmax : A->A.wmax, eb = aff ? 4 : 8, hdr = aff ? kHdrAffine : kHdrPlain;
+    const StreamPlan pl = pair_plan(A->all, SliceSet{}, pair_chunk(wmax, eb, 1, 1, hdr), wmax, eb, 1, 1, hdr, &ok);
     ESD_CHECK(ok && w > 0, ESD_ERR_INTERNAL, "pair SpMV plan");
     ESD_DISPATCH_W(w, {
       if (aff) {
@@ -59,7 +59,8 @@ void launch_iteration_pair(const IterCtx<float>& c1, const IterCtx<float>& c2, u
   const size_t nf = P->fwd_sets.size();
   for (size_t l = 0; l < nf; ++l) {
     const int wmax = aff ? P->fwd_awmax[l] : P->fwd_wmax[l];
-    const StreamPlan pl = pair_plan(P->fwd_sets[l], SliceSet{}, kPairChunk, wmax, eb, 3, 0, hdr, &ok);
+    const StreamPlan pl = pair_plan(P->fwd_sets[l], SliceSet{}, pair_chunk(wmax, eb, 3, 0, hdr), wmax, eb, 3, 0, hdr,
+                                    &ok);
     ESD_CHECK(ok, ESD_ERR_INTERNAL, "pair forward plan");
     const bool last = l + 1 == nf;
     ESD_DISPATCH_W(pair_width(wmax), {
@@ -77,7 +78,7 @@ void launch_iteration_pair(const IterCtx<float>& c1, const IterCtx<float>& c2, u
     const SliceSet& el = l < P->bwd0_sets.size() ? P->bwd0_sets[l] : none;
     const bool has = l < P->bwd_sets.size();
     const int wmax = has ? (aff ? P->bwd_awmax[l] : P->bwd_wmax[l]) : 0;
-    const StreamPlan pl = pair_plan(sw, el, kPairChunk, wmax, eb, 1, 2, hdr, &ok);
+    const StreamPlan pl = pair_plan(sw, el, pair_chunk(wmax, eb, 1, 2, hdr), wmax, eb, 1, 2, hdr, &ok);
     ESD_CHECK(ok, ESD_ERR_INTERNAL, "pair backward plan");
     ESD_DISPATCH_W(pair_width(wmax), {
       auto k = aff ? k_bwd_pair<WW, true> : k_bwd_pair<WW, false>;

@@ -16,16 +16,31 @@
 //
 // Each row's products are taken in the same order as in the single kernels, so q, y and z
 // are those of the single kernels for the same p, r and y; the dot products' per-thread
-// partial sums cover other rows (the pair launches take 16 slices per chunk for the products
-// and 32 for the update), so the two systems follow their single runs up to that rounding. The
+// partial sums cover other rows (the pair launches take their own chunks of slices), so the
+// two systems follow their single runs up to that rounding. The
 // paired loop ends when either inner run stops (the rest of that loop body skips it); the
 // other goes on with the single kernels, from the state the paired ones left.
 #pragma once
 
 namespace esd {
 
-constexpr int kPairChunk = kStreamWarps;          // slices per chunk of the pair products (K = 1)
 constexpr int kPairUpdateChunk = 2 * kStreamWarps;  // slices per chunk of the pair update
+constexpr int kPairSlices = 2;  // slices per consumer warp and chunk of the paired products, at most
+
+// Slices per chunk of a paired product launch: kStreamWarps per pass of the consumer warps,
+// up to kPairSlices passes (ESD_PAIR_SLICES = 1, 2 or 4 overrides it), as many as keep two
+// stages in the ring.
+inline int pair_chunk(int wmax, int ebytes, int nv4, int nv8, int hdr) {
+  int kmax = kPairSlices;
+  if (const char* e = std::getenv("ESD_PAIR_SLICES")) {
+    const int v = std::atoi(e);
+    if (v == 1 || v == 2 || v == 4) kmax = v;
+  }
+  for (int k = kmax; k > 1; k /= 2)
+    if (2 * stream_stage_bytes(k * kStreamWarps, wmax, ebytes, nv4, nv8, hdr) <= kStreamRingCap)
+      return k * kStreamWarps;
+  return kStreamWarps;
+}
 
 // Plan with a fixed chunk of cs slices (no shape choice); ok = false when its ring of two
 // stages does not fit kStreamRingCap.
@@ -143,23 +158,24 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
   } else {
     bool bad = false;
     const bool ok = stream_consume(pl, es, vs, full, empty, [&](const ChunkPos& cp, const StageView<2>& sv) {
-      if (warp >= cp.s1 - cp.s0) return;
-      const int4 md = sv.meta()[warp];
-      const bool valid = lane < md.w;
-      const int i = md.z + lane;
-      const float si = valid ? sv.template vec<float>(0, i) : 0.f;
-      const float2 pp = valid ? sv.template vec<float2>(1, i) : make_float2(0.f, 0.f);
-      const float p1 = pp.x, p2 = pp.y;
-      float q1 = fmaf(si, p1, 0.f), q2 = fmaf(si, p2, 0.f);
-      staged_rows_pair<W, true, AFF>(sv, md, warp, lane, c1.p12, p1, p2, q1, q2, bad);
-      if (valid) {
-        if (act1) {
-          c1.q[i] = q1;
-          kahan_add(acc[0], cmp[0], __fmul_rn(p1, q1));
-        }
-        if (act2) {
-          c2.q[i] = q2;
-          kahan_add(acc[1], cmp[1], __fmul_rn(p2, q2));
+      for (int ls = warp; ls < cp.s1 - cp.s0; ls += kStreamWarps) {
+        const int4 md = sv.meta()[ls];
+        const bool valid = lane < md.w;
+        const int i = md.z + lane;
+        const float si = valid ? sv.template vec<float>(0, i) : 0.f;
+        const float2 pp = valid ? sv.template vec<float2>(1, i) : make_float2(0.f, 0.f);
+        const float p1 = pp.x, p2 = pp.y;
+        float q1 = fmaf(si, p1, 0.f), q2 = fmaf(si, p2, 0.f);
+        staged_rows_pair<W, true, AFF>(sv, md, ls, lane, c1.p12, p1, p2, q1, q2, bad);
+        if (valid) {
+          if (act1) {
+            c1.q[i] = q1;
+            kahan_add(acc[0], cmp[0], __fmul_rn(p1, q1));
+          }
+          if (act2) {
+            c2.q[i] = q2;
+            kahan_add(acc[1], cmp[1], __fmul_rn(p2, q2));
+          }
         }
       }
     });
@@ -304,20 +320,21 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
     const unsigned bwd0 = pl.set[0].bwd0;
     bool bad = false;
     const bool ok = stream_consume(pl, es, vs, full, empty, [&](const ChunkPos& cp, const StageView<3>& sv) {
-      if (warp >= cp.s1 - cp.s0) return;
-      const int4 md = sv.meta()[warp];
-      const bool valid = lane < md.w;
-      const int i = md.z + lane;
-      const float d = valid ? sv.template vec<float>(2, i) : 0.f;
-      float y1 = valid ? sv.template vec<float>(0, i) : 0.f;
-      float y2 = valid ? sv.template vec<float>(1, i) : 0.f;
-      staged_rows_pair<W, false, AFF>(sv, md, warp, lane, c1.Y12, 0.f, 0.f, y1, y2, bad);
-      const bool to_z = (bwd0 >> cp.range) & 1u;
-      if (valid) {
-        const float yv1 = y1 * d, yv2 = y2 * d;
-        if (act1) kahan_add(acc[0], cmp[0], __fmul_rn(yv1, yv1));
-        if (act2) kahan_add(acc[1], cmp[1], __fmul_rn(yv2, yv2));
-        c1.Y12[i] = to_z ? make_float2(yv1 * d, yv2 * d) : make_float2(yv1, yv2);
+      for (int ls = warp; ls < cp.s1 - cp.s0; ls += kStreamWarps) {
+        const int4 md = sv.meta()[ls];
+        const bool valid = lane < md.w;
+        const int i = md.z + lane;
+        const float d = valid ? sv.template vec<float>(2, i) : 0.f;
+        float y1 = valid ? sv.template vec<float>(0, i) : 0.f;
+        float y2 = valid ? sv.template vec<float>(1, i) : 0.f;
+        staged_rows_pair<W, false, AFF>(sv, md, ls, lane, c1.Y12, 0.f, 0.f, y1, y2, bad);
+        const bool to_z = (bwd0 >> cp.range) & 1u;
+        if (valid) {
+          const float yv1 = y1 * d, yv2 = y2 * d;
+          if (act1) kahan_add(acc[0], cmp[0], __fmul_rn(yv1, yv1));
+          if (act2) kahan_add(acc[1], cmp[1], __fmul_rn(yv2, yv2));
+          c1.Y12[i] = to_z ? make_float2(yv1 * d, yv2 * d) : make_float2(yv1, yv2);
+        }
       }
     });
     if (!ok || bad) {
@@ -382,23 +399,24 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
   } else {
     bool bad = false;
     const bool ok = stream_consume(pl, es, vs, full, empty, [&](const ChunkPos& cp, const StageView<3>& sv) {
-      if (warp >= cp.s1 - cp.s0) return;
-      const bool sweep = cp.part == 0;
-      int4 md = sv.meta()[warp];
-      if (!sweep) md.y = 0;  // rows whose z_i the forward sweep stored
-      const bool valid = lane < md.w;
-      const int i = md.z + lane;
-      const float2 yy = valid ? sv.template vec<float2>(0, i) : make_float2(0.f, 0.f);
-      float z1 = yy.x, z2 = yy.y;
-      const float d = (valid && sweep) ? sv.template vec<float>(1, i) : 1.f;
-      const float2 po = valid ? sv.template vec<float2>(2, i) : make_float2(0.f, 0.f);
-      if (sweep) staged_rows_pair<W, false, AFF>(sv, md, warp, lane, c1.Y12, 0.f, 0.f, z1, z2, bad);
-      if (valid) {
-        const float zi1 = sweep ? z1 * d : z1, zi2 = sweep ? z2 * d : z2;
-        if (sweep) c1.Y12[i] = make_float2(zi1, zi2);
-        const float pn1 = act1 ? (first1 ? zi1 : fmaf(be1, po.x, zi1)) : po.x;
-        const float pn2 = act2 ? (first2 ? zi2 : fmaf(be2, po.y, zi2)) : po.y;
-        c1.p12[i] = make_float2(pn1, pn2);
+      for (int ls = warp; ls < cp.s1 - cp.s0; ls += kStreamWarps) {
+        const bool sweep = cp.part == 0;
+        int4 md = sv.meta()[ls];
+        if (!sweep) md.y = 0;  // rows whose z_i the forward sweep stored
+        const bool valid = lane < md.w;
+        const int i = md.z + lane;
+        const float2 yy = valid ? sv.template vec<float2>(0, i) : make_float2(0.f, 0.f);
+        float z1 = yy.x, z2 = yy.y;
+        const float d = (valid && sweep) ? sv.template vec<float>(1, i) : 1.f;
+        const float2 po = valid ? sv.template vec<float2>(2, i) : make_float2(0.f, 0.f);
+        if (sweep) staged_rows_pair<W, false, AFF>(sv, md, ls, lane, c1.Y12, 0.f, 0.f, z1, z2, bad);
+        if (valid) {
+          const float zi1 = sweep ? z1 * d : z1, zi2 = sweep ? z2 * d : z2;
+          if (sweep) c1.Y12[i] = make_float2(zi1, zi2);
+          const float pn1 = act1 ? (first1 ? zi1 : fmaf(be1, po.x, zi1)) : po.x;
+          const float pn2 = act2 ? (first2 ? zi2 : fmaf(be2, po.y, zi2)) : po.y;
+          c1.p12[i] = make_float2(pn1, pn2);
+        }
       }
     });
     if (!ok || bad) {
