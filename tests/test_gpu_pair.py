@@ -5,8 +5,12 @@ CG recurrence, scalars and vectors apart; each row's products are taken in the o
 the single kernels, only the dot products' partial sums cover other rows. So each system of
 a pair must end as it ends alone:
   stopping test   ||b - A x|| <= tol ||b||, recomputed here in FP64 from the returned x;
+  coefficients    the first CG coefficients (alpha, beta) of each system equal esd_solve's
+                  to 1e-3: the runs differ only in the rounding of the FP32 sums, which a
+                  row left out of a product or a dot product would exceed;
   iterations      the pair's inner total of each system within max(3, 5%) of esd_solve's
-                  for the same system (the runs differ only in the rounding of the sums);
+                  (25% at a contrast of 1e6, where the FP32 trajectory, its refinement
+                  restarts and so its count depend on that rounding);
   solution        within kappa-free reach of the single run: both meet the same residual
                   bound, so ||A (x_pair - x_single)|| <= 2 tol ||b||;
   independence    a system that is solved already (or has b = 0) costs nothing: the other
@@ -39,6 +43,9 @@ def _problem(which):
     return wl.small_3d(23, seed=13, count=3, rmin=2, rmax=3, value=1e6)  # ragged
 
 
+SLACK = {"natural": 0.05, "shuffled": 0.05, "ragged": 0.25}  # iteration counts (see above)
+
+
 @pytest.fixture(scope="module", params=["natural", "shuffled", "ragged"])
 def case(request):
     p = _problem(request.param)
@@ -50,7 +57,7 @@ def case(request):
     b1 = p.source.copy()
     b2 = rng.uniform(-1.0, 1.0, p.n) * float(np.abs(p.source).max())
     x2 = rng.standard_normal(p.n) * 1e-3  # a warm start for the second system
-    return dict(p=p, A=A, S=(S1, S2, S3), b1=b1, b2=b2, x2=x2, csr=p.scipy())
+    return dict(p=p, A=A, S=(S1, S2, S3), b1=b1, b2=b2, x2=x2, csr=p.scipy(), slack=SLACK[request.param])
 
 
 def relres(csr, b, x):
@@ -68,17 +75,24 @@ def test_pair_meets_the_stopping_test_and_follows_the_single_runs(case):
     S1, S2, _ = case["S"]
     csr = case["csr"]
     xs1, it_s1 = single(S1, case["b1"], np.zeros(case["p"].n))
+    h_s1 = S1.history()
     xs2, it_s2 = single(S2, case["b2"], case["x2"])
+    h_s2 = S2.history()
     x1, x2 = np.zeros(case["p"].n), case["x2"].copy()
     st, (it1, rr1), (it2, rr2), paired = S1.solve_pair(S2, case["b1"], x1, case["b2"], x2, TOL)
     assert st == esd.OK
+    for S, (a_s, b_s) in ((S1, h_s1), (S2, h_s2)):
+        a, b = S.history()
+        k = min(len(a), len(a_s), 8)
+        np.testing.assert_allclose(a[:k], a_s[:k], rtol=1e-3)
+        np.testing.assert_allclose(b[:k - 1], b_s[:k - 1], rtol=1e-3)
     # the paired loop runs while both inner runs go on: at least the shorter first inner run
     assert 0 < paired <= min(it1, it2)
     for x, b, rr in ((x1, case["b1"], rr1), (x2, case["b2"], rr2)):
         assert rr <= TOL
         assert relres(csr, b, x) <= 1.01 * TOL
     for it, it_s in ((it1, it_s1), (it2, it_s2)):
-        assert abs(it - it_s) <= max(3, int(np.ceil(0.05 * it_s))), (it, it_s)
+        assert abs(it - it_s) <= max(3, int(np.ceil(case["slack"] * it_s))), (it, it_s)
     for x, xs, b in ((x1, xs1, case["b1"]), (x2, xs2, case["b2"])):
         assert np.linalg.norm(csr @ (x - xs)) <= 2.02 * TOL * np.linalg.norm(b)
 
