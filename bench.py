@@ -1021,6 +1021,7 @@ def roofline(prof, p, args, mode, esd, peaks, layout=None, pair=False):
 TRAFFIC = {
     ("c2", "fp64", "spmv_pq"): "spmv_pq_fp64_plain_128cube_traffic.txt",
     ("c5", "fp32", "spmv_pq"): "spmv_pq_stream_colfree_fp32_256cube_traffic.txt",
+    ("c5", "fp32", "spmv_pq_pair"): "spmv_pq_pair_colfree_fp32_256cube_traffic.txt",
 }
 
 
