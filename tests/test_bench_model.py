@@ -101,3 +101,17 @@ def test_pair_models_share_the_matrix_once():
     # 1/l_ii of level 0 once
     assert by == 2 * (16 * n + 16 * n + 4 * n0) + 4 * n0
     assert fm == 2 * (3 * n + 2 * n0)
+
+
+def test_pair_launch_count():
+    """esd_solve_pair's graph: 2 residuals, the loop condition and 2 final kernels; per
+    refinement step both systems' prep, start (residual, update, 3 + 3 sweeps), finish and
+    residual, the pack and unpack of p and four loop conditions; one body (SpMV, update,
+    3 + 3 sweeps) per paired iteration and per iteration a system ran alone."""
+    info = {"fwd_levels": 4, "bwd_levels": 4}
+    start, body = 1 + 1 + 3 + 3, 2 + 3 + 3
+    per_step = 2 * (1 + start + 1 + 1) + 2 + 4
+    # 9 steps for the longer system, 1500 + 1400 iterations of which 1300 paired
+    assert bench.pair_launch_count(info, [1500, 1400], [9, 8], 1300) == 5 + 9 * per_step + body * (2900 - 1300)
+    # nothing paired: every iteration runs alone
+    assert bench.pair_launch_count(info, [10, 0], [1, 0], 0) == 5 + per_step + body * 10
