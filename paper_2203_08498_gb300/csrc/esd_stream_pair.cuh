@@ -17,9 +17,9 @@
 // Each row's products are taken in the same order as in the single kernels, so q, y and z
 // are those of the single kernels for the same p, r and y; the dot products' per-thread
 // partial sums cover other rows (the pair launches take their own chunks of slices), so the
-// two systems follow their single runs up to that rounding. The
-// paired loop ends when either inner run stops (the rest of that loop body skips it); the
-// other goes on with the single kernels, from the state the paired ones left.
+// two systems follow their single runs up to that rounding. The paired loop ends when either
+// inner run stops (the rest of that loop body skips it); the other goes on with the single
+// kernels, from the state the paired ones left.
 #pragma once
 
 namespace esd {
