@@ -3,14 +3,15 @@
 The refinement form (FP32 inner PCG in FP64 iterative refinement) stops when the FP64 true
 residual ||b - A x|| / ||b|| meets the tolerance. Its solution is compared with the oracle's
 FP64 ICCG solution of the same system, taken to a tolerance a hundred times tighter and
-refined once in FP64 by the oracle, and with the FP64 GPU solve of the same system (plain PCG stopped by its recursive residual). The
-bound the residual gives is ||x - x*|| / ||x*|| <= kappa(A) ||b - A x|| / ||b||, with kappa(A)
+refined once in FP64 by the oracle, and with the FP64 GPU solve of the same system (plain PCG
+stopped by its recursive residual). The bound the residual gives is ||x - x*|| / ||x*|| <= kappa(A) ||b - A x|| / ||b||, with kappa(A)
 up to 1e9 here; the test records the measured errors and requires 1e-5 at most.
 
 Systems: the first system of each sequence (b = s, x_0 = 0) of C2 (128^3), C3 at 64^3
 (the 27-point operator), C4 (128^3, the steady exp(theta) operator) and C5's recipe at
 128^3; with ESD_FULL_C5=1 also C5 itself at 256^3 (several minutes of oracle time).
-The errors are appended to gpurun_out/precision_errors.jsonl when that folder exists.
+The errors are appended to precision_errors.jsonl in the folder that ESD_RESULTS_DIR names,
+when it is set.
 """
 import json
 import os
@@ -49,8 +50,8 @@ CASES = _cases()
 
 
 def _record(row):
-    out = os.path.join(ROOT, "gpurun_out")
-    if os.path.isdir(out):
+    out = os.environ.get("ESD_RESULTS_DIR")
+    if out and os.path.isdir(out):
         with open(os.path.join(out, "precision_errors.jsonl"), "a") as f:
             f.write(json.dumps(row) + "\n")
 
