@@ -31,7 +31,6 @@ if not torch.cuda.is_available():
 import paper_2203_08498_gb300 as esd  # noqa: E402
 
 DEV = torch.device("cuda:0")
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _cases():
